@@ -1,0 +1,98 @@
+"""The size-regularity merge of Sec. 3.1 (Eqs. eqa:merge and condtion), re-derived with
+independent code after every phase that has merge requests: the target of each request is
+the neighbouring superpixel with the least merge energy (the Ward increase, exact rational
+arithmetic) among those whose size stays within u * InitSize; requests are accepted in
+ascending block order unless their source or target already merged in the phase."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import helpers
+import oracle
+from paper_1704_02083_gb300 import synth
+
+
+def neighbours_of(bl, a):
+    out = set()
+    m = bl == a
+    for A, B in ((bl[:, :-1], bl[:, 1:]), (bl[:-1, :], bl[1:, :])):
+        out |= set(B[(A == a) & (B != a)].tolist())
+        out |= set(A[(B == a) & (A != a)].tolist())
+    return out
+
+
+def ward_exact(s, a, n, lam_pos):
+    Na, Nn = int(s[a, 0]), int(s[n, 0])
+    ca = [Fraction(int(s[a, i]), Na) for i in range(1, 6)]
+    cn = [Fraction(int(s[n, i]), Nn) for i in range(1, 6)]
+    dc = sum((ca[i] - cn[i]) ** 2 for i in range(3))
+    dm = sum((ca[i] - cn[i]) ** 2 for i in range(3, 5))
+    return Fraction(Na * Nn, Na + Nn) * (dc + lam_pos * dm)
+
+
+@pytest.mark.parametrize("seed", [3, 7, 12])
+def test_merges_rederived(seed):
+    rgb = synth.he_image(96, 128, n_cells=10, seed=seed).rgb
+    o = oracle.Oracle(rgb, K=40, init_block=8, size_mode=2)
+    o.seed()
+    lam_pos = Fraction(o.lambda_pos())
+    total_merges = 0
+    total_requests = 0
+    for st in range(o.num_stages()):
+        if st > 0:
+            o.next_stage()
+        for sw in range(12):
+            changes = 0
+            for ph in range(9):
+                mv, nrq = o.phase_moves(ph)
+                changes += mv
+                bl = o.block_labels()
+                s, _, _ = o.stats()
+                blk, lab = o.pending_requests()
+                assert nrq == len(blk)
+                assert (np.diff(blk) > 0).all()  # ascending block order
+                total_requests += nrq
+                # expected outcome
+                targets = []
+                for b, a in zip(blk, lab):
+                    assert bl.ravel()[b] == a
+                    cands = [n for n in neighbours_of(bl, a) if 2 * (s[n, 0] + s[a, 0]) <= 3 * s[n, 6]]
+                    if not cands:
+                        targets.append(-1)
+                        continue
+                    w = {n: ward_exact(s, a, n, lam_pos) for n in cands}
+                    best = min(w.values())
+                    vals = sorted(w.values())
+                    if len(vals) > 1 and vals[1] - vals[0] <= abs(best) * Fraction(1, 10**9):
+                        targets.append(None)  # near tie: not decidable by rounding-free means
+                        continue
+                    targets.append(min(n for n in cands if w[n] == best))
+                if None in targets:
+                    mg = o.phase_merges()
+                    changes += mg
+                    continue
+                involved = set()
+                to = {}
+                for a, n in zip(lab.tolist(), targets):
+                    if n < 0 or a in involved or n in involved:
+                        continue
+                    involved |= {a, n}
+                    to[a] = n
+                exp_bl = bl.copy()
+                exp_s = s.copy()
+                for a, n in to.items():
+                    exp_bl[bl == a] = n
+                    exp_s[n, :6] += s[a, :6]
+                    exp_s[a, :6] = 0
+                mg = o.phase_merges()
+                changes += mg
+                assert mg == len(to)
+                total_merges += mg
+                np.testing.assert_array_equal(o.block_labels(), exp_bl)
+                np.testing.assert_array_equal(o.stats()[0], exp_s)
+            if changes == 0:
+                break
+    assert total_requests > 0
+    if seed == 3:
+        assert total_merges > 0
