@@ -1,0 +1,202 @@
+/* rapid.h — C ABI of the GB300 (sm_103a) implementation of the coarse-to-fine
+ * topology-preserving superpixel refinement of RAPID ("RAPID" Regions-of-Interest
+ * Detection in Big Histopathological Images, Sulimowicz & Ahmad, ICME 2017).
+ *
+ * The calls follow the paper's statement of the problem: an RGB image goes in; the label
+ * matrix L (one superpixel id per pixel) and the per-superpixel statistics S (size, mean
+ * colour, mean position; Algorithm RAPID) come out.  Every step runs in CUDA kernels on
+ * one GPU; the library owns all device memory it allocates and keeps no caller pointer
+ * after a call returns.
+ *
+ * Conventions
+ *  - Every call returns a rapid_status and never throws.  The first CUDA error is sticky:
+ *    later calls on the same context return RAPID_ECUDA until rapid_destroy.
+ *  - Work is enqueued on the context's stream (borrowed, never destroyed by the library;
+ *    0 = the legacy default stream).  Calls that return data to the host synchronise that
+ *    stream first.  A device wait that gives up (see spin_limit_ns) is reported as
+ *    RAPID_ETIMEOUT by the next synchronising call.
+ *  - Labels are int32 in [0, M).  They are stable: a superpixel merged away keeps its id
+ *    retired (size 0) and ids are never reused.
+ *  - Coordinates are 0-based full-resolution pixels; x = column, y = row.  Images are
+ *    row-major, interleaved RGB, one byte per channel.
+ *  - Floating-point energies are IEEE binary64 evaluated in a fixed operation order with
+ *    no fused multiply-add; all sums are exact int64.  Results are therefore reproducible
+ *    bit for bit.
+ */
+#ifndef RAPID_H
+#define RAPID_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rapid_status {
+  RAPID_OK = 0,
+  RAPID_EINVAL = 1,   /* bad argument (NULL pointer, size out of range, bad parameter) */
+  RAPID_ENOMEM = 2,   /* device or host allocation failed */
+  RAPID_ECUDA = 3,    /* a CUDA runtime call or kernel failed (sticky) */
+  RAPID_ESTATE = 4,   /* call out of order (e.g. refine before seeding, split after the last stage) */
+  RAPID_ETIMEOUT = 5, /* a bounded device-side wait (grid barrier) gave up; results are invalid */
+  RAPID_ERANGE = 6    /* exactness limit exceeded (an int64 sum could pass 2^53, too many stages) */
+} rapid_status;
+
+typedef struct rapid_ctx rapid_ctx; /* opaque; owns every device buffer it allocates */
+
+/* Parameters of the method.  rapid_default_params() fills the defaults listed here. */
+typedef struct rapid_params {
+  int32_t num_levels;      /* L >= 1 image levels (Sec. 2.2); level l (1 = coarsest) is the
+                              image box-summed by f_l = C^(L-l).  Default 1. */
+  int32_t ratio_C;         /* compression ratio C between levels, power of two >= 2
+                              (Eq. eq:mu).  Default 4. */
+  int32_t init_block;      /* initial block side in full-res pixels, power of two.  Default 16. */
+  int32_t final_grain;     /* final block side ("grain", Sec. 4.3), power of two.  Default 1. */
+  int32_t K;               /* requested number of superpixels (seed grid, Algorithm RAPID).
+                              Default 200. */
+  int32_t size_mode;       /* E_size handling (Sec. 3.1): 0 = none (lambda_s = 0), 1 = hard
+                              lower bound (lambda_s = inf), 2 = merge (the paper's
+                              regularity optimisation).  Default 2. */
+  double lambda_pos0;      /* position weight: lambda_pos = lambda_pos0 * M / (H*W).  Default 400. */
+  double lambda_b;         /* boundary-length weight per 4-adjacent full-res pixel pair
+                              (Eq. equa:energy1, Eq. bound).  Default 50. */
+  int32_t lo_num, lo_den;  /* lower size bound l = lo_num/lo_den (Sec. 3.1).  Default 1/4. */
+  int32_t hi_num, hi_den;  /* upper size bound u = hi_num/hi_den (Eq. condtion).  Default 3/2. */
+  int32_t predict;         /* 1: predict at level 2 and refine only boundary superpixels
+                              afterwards (Sec. 3.2, Eq. predict, Eq. new_bound).  Default 0. */
+  int32_t reuse;           /* 1: carry S across levels (Eq. eq:mu); 0: recompute S at every
+                              level entry (multi-scale baseline).  Same results.  Default 1. */
+  int32_t importance_rule; /* 0: a block is refined when its superpixel is a boundary
+                              superpixel; 1: when a 4-neighbour has a different label of the
+                              other class (Eq. new_bound read pairwise).  Default 0. */
+  int32_t max_sweeps;      /* sweeps per stage before giving up on convergence.  Default 64. */
+  int64_t h_T;             /* brightness threshold of the integer stand-in classifier
+                              h(k) = 3 h_T N_k - (R_k + G_k + B_k) (Eq. predict).  Default 150. */
+  int64_t spin_limit_ns;   /* give-up time of each device-side barrier wait; 0 gives up at
+                              once (used by tests).  Default 2e9 (2 s). */
+} rapid_params;
+
+#define RAPID_MAX_STAGES 32
+
+/* Per-superpixel statistics S (Algorithm RAPID), index = label id.  Means are sums / n. */
+typedef struct rapid_sp_stats {
+  int64_t n;          /* pixel count (0 = retired by a merge) */
+  int64_t sum_r, sum_g, sum_b;
+  int64_t sum_x, sum_y;
+  int64_t init_size;  /* InitSize: pixel count right after seeding (Sec. 3.1) */
+  int32_t y;          /* class from Eq. predict: +1 ROI, -1 non-ROI, 0 before prediction */
+  int32_t important;  /* 1 when a boundary superpixel (Eq. new_bound), else 0 */
+} rapid_sp_stats;
+
+typedef struct rapid_stage_counters {
+  int32_t level;           /* image level l of the stage */
+  int32_t block;           /* block side s in full-res pixels */
+  int32_t sweeps;          /* 9-phase sweeps run (<= max_sweeps) */
+  int32_t pad;
+  int64_t eligible;        /* block evaluations that passed the boundary / importance test */
+  int64_t evaluated;       /* ... and the topology test (energies computed) */
+  int64_t moves;           /* blocks relabelled */
+  int64_t merge_requests;  /* moves replaced by a merge request (size bound hit) */
+  int64_t merges;          /* merges accepted */
+  float kernel_ms;         /* device time of the stage's refinement launch when profiling is
+                              on (rapid_set_profiling), else -1 */
+  float pad2;
+} rapid_stage_counters;
+
+typedef struct rapid_counters {
+  int32_t num_stages;      /* stages of the schedule */
+  int32_t M;               /* label ids in use (seeded superpixels) */
+  int64_t launches;        /* kernels this context has launched since creation */
+  rapid_stage_counters stage[RAPID_MAX_STAGES];
+} rapid_counters;
+
+/* Fill *p with the defaults documented in rapid_params.  NULL-safe. */
+void rapid_default_params(rapid_params *p);
+
+/* Create a context bound to the current CUDA device.  p is copied; cuda_stream is a
+ * cudaStream_t borrowed for the context's lifetime (0 = legacy default stream).
+ * EINVAL on a bad parameter, ENOMEM, ECUDA. */
+rapid_status rapid_create(const rapid_params *p, void *cuda_stream, rapid_ctx **out);
+
+/* Copy an H x W interleaved RGB image into the context (Algorithm RAPID input I).
+ * rgb: host or device (rgb_is_device) pointer, rows row_pitch_bytes apart
+ * (>= 3*W).  The caller keeps ownership; the copy is complete when the call returns for
+ * host input and stream-ordered for device input.  Allocates the per-image buffers;
+ * resets the context to "image set, not seeded".  EINVAL (H or W < 1, H*W >= 2^31, or
+ * H*W*max(H,W) >= 2^53, which would break exact double conversion of position sums),
+ * ENOMEM, ECUDA. */
+rapid_status rapid_set_image(rapid_ctx *ctx, const uint8_t *rgb, int32_t H, int32_t W,
+                             int64_t row_pitch_bytes, int32_t rgb_is_device);
+
+/* Build the level images (exact box sums, Sec. 2.2) and seed the regular grid of
+ * superpixels (Algorithm RAPID, "initialize superpixels to be regular grids"): gx =
+ * round(sqrt(K W / H)), gy = round(K / gx), clamped to the first stage's block grid;
+ * compute S and InitSize.  *M_out (may be NULL) receives gx*gy.  ESTATE without an image. */
+rapid_status rapid_seed_grid(rapid_ctx *ctx, int32_t *M_out);
+
+/* Refine the current stage (Sec. 2.1 and Algorithm RAPID's queue loop): 9-phase sweeps of
+ * boundary-block relabelling (Eq. operation) under the topology constraint, with the size
+ * term of size_mode, until a sweep changes nothing or max_sweeps.  Out-pointers may be
+ * NULL; when any is non-NULL the call synchronises and fills them.  ESTATE before
+ * seeding; ETIMEOUT / ECUDA as above. */
+rapid_status rapid_refine_stage(rapid_ctx *ctx, int32_t *sweeps_out, int64_t *moves_out,
+                                int64_t *merges_out);
+
+/* Advance to the next stage: predict on entering level 2 (when enabled), split every block
+ * into 2x2 blocks that keep its label (Algorithm RAPID, "map superpixels' labels"), and
+ * with reuse off recompute S from the new level.  ESTATE before seeding or after the last
+ * stage. */
+rapid_status rapid_split(rapid_ctx *ctx);
+
+/* The whole schedule on the context's image: level images, seeding, then refine / split
+ * through every stage.  Enqueue only; a later synchronising call reports errors. */
+rapid_status rapid_run(rapid_ctx *ctx);
+
+/* Current position in the schedule: stage index (-1 before seeding), its level and block
+ * side, and M.  Host-side only (no synchronisation).  Any pointer may be NULL. */
+rapid_status rapid_get_state(rapid_ctx *ctx, int32_t *stage, int32_t *level, int32_t *block,
+                             int32_t *M);
+
+/* Full-resolution label map (H x W int32, rows row_pitch_bytes apart, >= 4*W) into a host
+ * or device (dst_is_device) buffer owned by the caller.  Synchronises.  ESTATE before
+ * seeding. */
+rapid_status rapid_read_labels(rapid_ctx *ctx, int32_t *dst, int64_t row_pitch_bytes,
+                               int32_t dst_is_device);
+
+/* The current stage's block-resolution label map (nby x nbx int32, row-major, nbx =
+ * ceil(W/s), nby = ceil(H/s)) into a host buffer of `capacity` elements.  *nbx_out and
+ * *nby_out may be NULL.  Synchronises.  EINVAL when the buffer is too small. */
+rapid_status rapid_read_block_labels(rapid_ctx *ctx, int32_t *dst, int64_t capacity,
+                                     int32_t *nbx_out, int32_t *nby_out);
+
+/* Statistics S of every label id (host buffer of `capacity` entries).  *M_out (may be
+ * NULL) receives M.  Synchronises.  EINVAL when capacity < M. */
+rapid_status rapid_read_stats(rapid_ctx *ctx, rapid_sp_stats *dst, int64_t capacity,
+                              int64_t *M_out);
+
+/* Per-stage counters of the current run (host struct).  Synchronises. */
+rapid_status rapid_read_counters(rapid_ctx *ctx, rapid_counters *dst);
+
+/* Time each stage's refinement launch with CUDA events (0 = off, the default). */
+rapid_status rapid_set_profiling(rapid_ctx *ctx, int32_t on);
+
+/* Synchronise the context's stream and return the context's status (ETIMEOUT if a device
+ * wait gave up, ECUDA on a CUDA error). */
+rapid_status rapid_sync(rapid_ctx *ctx);
+
+/* Topology test table computed by the device code: out[m] = 1 when removing a block whose
+ * 3x3 neighbourhood mask is m keeps its superpixel connected (E_topo, Eq. equa:energy1).
+ * Bit i of m is neighbour i in the order NW, N, NE, E, SE, S, SW, W (1 = same label).
+ * Host buffer of 256 bytes; runs a kernel on the current device and synchronises. */
+rapid_status rapid_simple_table(uint8_t *out256);
+
+/* Human-readable name of a status.  Never NULL. */
+const char *rapid_status_string(rapid_status s);
+
+/* Free everything the context owns.  NULL-safe.  Synchronises its stream first. */
+void rapid_destroy(rapid_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAPID_H */

@@ -106,3 +106,18 @@ def test_importance_prunes_work_at_later_levels():
     rule1 = oracle.Oracle(rgb, **{**P3, "importance_rule": 1}).run().counters()
     assert (rule1[:2] == off[:2]).all()
     assert rule1[2:, 3].sum() < off[2:, 3].sum()
+
+
+def test_prediction_tie_is_roi():
+    """Eq. predict: h >= 0 gives y = 1; a superpixel of mean brightness exactly T has h = 0."""
+    H, W = 64, 128
+    rgb = synth.two_colour_image(H, W, 64, left=(150, 150, 150), right=(200, 200, 200))
+    o = oracle.Oracle(rgb, num_levels=2, ratio_C=4, init_block=16, K=2, predict=1)
+    o.seed()
+    o.refine_stage()
+    while o.grid()["level"] < 2:
+        o.next_stage()
+    s, y, imp = o.stats()
+    assert s[0, 1:4].sum() == 3 * 150 * s[0, 0]
+    assert y.tolist() == [1, -1]
+    assert imp.tolist() == [1, 1]

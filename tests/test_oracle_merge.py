@@ -31,10 +31,12 @@ def ward_exact(s, a, n, lam_pos):
     return Fraction(Na * Nn, Na + Nn) * (dc + lam_pos * dm)
 
 
-@pytest.mark.parametrize("seed", [3, 7, 12])
-def test_merges_rederived(seed):
-    rgb = synth.he_image(96, 128, n_cells=10, seed=seed).rgb
-    o = oracle.Oracle(rgb, K=40, init_block=8, size_mode=2)
+@pytest.mark.parametrize("H,W,cells,K,seed", [(96, 128, 10, 40, 3), (96, 128, 10, 40, 7),
+                                              (96, 128, 10, 40, 12), (160, 200, 12, 200, 6)])
+def test_merges_rederived(H, W, cells, K, seed):
+    """(160 x 200, K 200, seed 6) contains a phase where two requests pick the same target."""
+    rgb = synth.he_image(H, W, n_cells=cells, seed=seed).rgb
+    o = oracle.Oracle(rgb, K=K, init_block=8, size_mode=2)
     o.seed()
     lam_pos = Fraction(o.lambda_pos())
     total_merges = 0
