@@ -1,0 +1,316 @@
+"""GB300 (sm_103a) implementation of the coarse-to-fine topology-preserving superpixel
+refinement of RAPID (Sulimowicz & Ahmad, ICME 2017).
+
+This module is the thin Python binding of the C ABI declared in include/rapid.h: the
+functions below have the C names and only marshal arguments.  Every step of the method
+runs in the CUDA kernels of ``_build/librapid.so``; there is no CPU path, and importing
+the binding fails loudly when the library is missing.  PyTorch is used only for device
+memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librapid.so")
+
+RAPID_OK, RAPID_EINVAL, RAPID_ENOMEM, RAPID_ECUDA, RAPID_ESTATE, RAPID_ETIMEOUT, RAPID_ERANGE = range(7)
+RAPID_MAX_STAGES = 32
+
+
+class RapidError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {rapid_status_string(status)}")
+
+
+class rapid_params(C.Structure):
+    _fields_ = [
+        ("num_levels", C.c_int32), ("ratio_C", C.c_int32), ("init_block", C.c_int32),
+        ("final_grain", C.c_int32), ("K", C.c_int32), ("size_mode", C.c_int32),
+        ("lambda_pos0", C.c_double), ("lambda_b", C.c_double),
+        ("lo_num", C.c_int32), ("lo_den", C.c_int32), ("hi_num", C.c_int32), ("hi_den", C.c_int32),
+        ("predict", C.c_int32), ("reuse", C.c_int32), ("importance_rule", C.c_int32),
+        ("max_sweeps", C.c_int32), ("h_T", C.c_int64), ("spin_limit_ns", C.c_int64),
+    ]
+
+
+class rapid_sp_stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sum_r", C.c_int64), ("sum_g", C.c_int64), ("sum_b", C.c_int64),
+                ("sum_x", C.c_int64), ("sum_y", C.c_int64), ("init_size", C.c_int64),
+                ("y", C.c_int32), ("important", C.c_int32)]
+
+
+class rapid_stage_counters(C.Structure):
+    _fields_ = [("level", C.c_int32), ("block", C.c_int32), ("sweeps", C.c_int32), ("pad", C.c_int32),
+                ("eligible", C.c_int64), ("evaluated", C.c_int64), ("moves", C.c_int64),
+                ("merge_requests", C.c_int64), ("merges", C.c_int64), ("kernel_ms", C.c_float),
+                ("pad2", C.c_float)]
+
+
+class rapid_counters(C.Structure):
+    _fields_ = [("num_stages", C.c_int32), ("M", C.c_int32), ("launches", C.c_int64),
+                ("stage", rapid_stage_counters * RAPID_MAX_STAGES)]
+
+
+# numpy view of rapid_sp_stats (same layout)
+SP_STATS_DTYPE = np.dtype([("n", "<i8"), ("sum_r", "<i8"), ("sum_g", "<i8"), ("sum_b", "<i8"),
+                           ("sum_x", "<i8"), ("sum_y", "<i8"), ("init_size", "<i8"), ("y", "<i4"),
+                           ("important", "<i4")])
+assert SP_STATS_DTYPE.itemsize == C.sizeof(rapid_sp_stats)
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load librapid.so (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_1704_02083_gb300.build.build() first "
+                          "(there is no CPU fallback)")
+    L = C.CDLL(LIB_PATH)
+    P, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    pi32, pi64 = C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+    sig = {
+        "rapid_default_params": (None, [C.POINTER(rapid_params)]),
+        "rapid_create": (i32, [C.POINTER(rapid_params), P, C.POINTER(P)]),
+        "rapid_set_image": (i32, [P, P, i32, i32, i64, i32]),
+        "rapid_seed_grid": (i32, [P, pi32]),
+        "rapid_refine_stage": (i32, [P, pi32, pi64, pi64]),
+        "rapid_split": (i32, [P]),
+        "rapid_run": (i32, [P]),
+        "rapid_get_state": (i32, [P, pi32, pi32, pi32, pi32]),
+        "rapid_read_labels": (i32, [P, P, i64, i32]),
+        "rapid_read_block_labels": (i32, [P, P, i64, pi32, pi32]),
+        "rapid_read_stats": (i32, [P, P, i64, pi64]),
+        "rapid_read_counters": (i32, [P, C.POINTER(rapid_counters)]),
+        "rapid_set_profiling": (i32, [P, i32]),
+        "rapid_sync": (i32, [P]),
+        "rapid_simple_table": (i32, [P]),
+        "rapid_status_string": (C.c_char_p, [i32]),
+        "rapid_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int, what: str):
+    if status != RAPID_OK:
+        raise RapidError(status, what)
+
+
+# ------------------------------------------------------------------ C-named functions
+def rapid_status_string(status: int) -> str:
+    return lib().rapid_status_string(status).decode()
+
+
+def rapid_default_params(**overrides) -> rapid_params:
+    p = rapid_params()
+    lib().rapid_default_params(C.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def rapid_create(params: rapid_params, cuda_stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check(lib().rapid_create(C.byref(params), C.c_void_p(cuda_stream), C.byref(h)), "rapid_create")
+    return h.value
+
+
+def rapid_set_image(ctx: int, rgb_ptr: int, H: int, W: int, row_pitch_bytes: int, rgb_is_device: int):
+    _check(lib().rapid_set_image(ctx, rgb_ptr, H, W, row_pitch_bytes, rgb_is_device), "rapid_set_image")
+
+
+def rapid_seed_grid(ctx: int) -> int:
+    M = C.c_int32()
+    _check(lib().rapid_seed_grid(ctx, C.byref(M)), "rapid_seed_grid")
+    return M.value
+
+
+def rapid_refine_stage(ctx: int, sync: bool = False):
+    if not sync:
+        _check(lib().rapid_refine_stage(ctx, None, None, None), "rapid_refine_stage")
+        return None
+    s, m, g = C.c_int32(), C.c_int64(), C.c_int64()
+    _check(lib().rapid_refine_stage(ctx, C.byref(s), C.byref(m), C.byref(g)), "rapid_refine_stage")
+    return s.value, m.value, g.value
+
+
+def rapid_split(ctx: int):
+    _check(lib().rapid_split(ctx), "rapid_split")
+
+
+def rapid_run(ctx: int):
+    _check(lib().rapid_run(ctx), "rapid_run")
+
+
+def rapid_get_state(ctx: int):
+    v = [C.c_int32() for _ in range(4)]
+    _check(lib().rapid_get_state(ctx, *[C.byref(x) for x in v]), "rapid_get_state")
+    return dict(zip(("stage", "level", "block", "M"), [x.value for x in v]))
+
+
+def rapid_read_labels(ctx: int, dst_ptr: int, row_pitch_bytes: int, dst_is_device: int):
+    _check(lib().rapid_read_labels(ctx, dst_ptr, row_pitch_bytes, dst_is_device), "rapid_read_labels")
+
+
+def rapid_read_block_labels(ctx: int, dst_ptr: int, capacity: int):
+    nbx, nby = C.c_int32(), C.c_int32()
+    _check(lib().rapid_read_block_labels(ctx, dst_ptr, capacity, C.byref(nbx), C.byref(nby)),
+           "rapid_read_block_labels")
+    return nbx.value, nby.value
+
+
+def rapid_read_stats(ctx: int, dst_ptr: int, capacity: int) -> int:
+    M = C.c_int64()
+    _check(lib().rapid_read_stats(ctx, dst_ptr, capacity, C.byref(M)), "rapid_read_stats")
+    return M.value
+
+
+def rapid_read_counters(ctx: int) -> rapid_counters:
+    c = rapid_counters()
+    _check(lib().rapid_read_counters(ctx, C.byref(c)), "rapid_read_counters")
+    return c
+
+
+def rapid_set_profiling(ctx: int, on: bool):
+    _check(lib().rapid_set_profiling(ctx, 1 if on else 0), "rapid_set_profiling")
+
+
+def rapid_sync(ctx: int):
+    _check(lib().rapid_sync(ctx), "rapid_sync")
+
+
+def rapid_simple_table() -> np.ndarray:
+    out = np.zeros(256, np.uint8)
+    _check(lib().rapid_simple_table(out.ctypes.data), "rapid_simple_table")
+    return out
+
+
+def rapid_destroy(ctx: int):
+    if ctx:
+        lib().rapid_destroy(ctx)
+
+
+# ------------------------------------------------------------------ convenience wrapper
+class Context:
+    """One rapid_ctx bound to the current CUDA device and a torch stream.
+
+    ``Context(params).set_image(rgb)`` accepts a numpy H x W x 3 uint8 array (host copy) or
+    a CUDA torch tensor of that shape (device copy).  ``labels()`` returns a host int32
+    H x W array (or writes into a CUDA int32 tensor with ``labels(out=t)``).
+    """
+
+    def __init__(self, params: rapid_params | None = None, stream=None, **overrides):
+        if params is None:
+            params = rapid_default_params(**overrides)
+        elif overrides:
+            for k, v in overrides.items():
+                setattr(params, k, v)
+        self.params = params
+        self._stream = stream
+        handle = 0
+        if stream is not None:
+            handle = int(getattr(stream, "cuda_stream", stream))
+        self.h = rapid_create(params, handle)
+        self.H = self.W = 0
+
+    def close(self):
+        if getattr(self, "h", 0):
+            rapid_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_image(self, rgb):
+        if isinstance(rgb, np.ndarray):
+            rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
+            if rgb.ndim != 3 or rgb.shape[2] != 3:
+                raise ValueError("expected H x W x 3 uint8")
+            H, W = rgb.shape[:2]
+            rapid_set_image(self.h, rgb.ctypes.data, H, W, rgb.strides[0], 0)
+        else:  # torch CUDA tensor, uint8, H x W x 3 with contiguous rows
+            if str(rgb.dtype) != "torch.uint8" or rgb.dim() != 3 or rgb.shape[2] != 3 or not rgb.is_cuda:
+                raise ValueError("expected a CUDA uint8 tensor of shape H x W x 3")
+            if rgb.stride(2) != 1 or rgb.stride(1) != 3:
+                raise ValueError("rows must be interleaved RGB (stride(1) == 3, stride(2) == 1)")
+            H, W = int(rgb.shape[0]), int(rgb.shape[1])
+            rapid_set_image(self.h, rgb.data_ptr(), H, W, rgb.stride(0), 1)
+        self.H, self.W = int(H), int(W)
+        return self
+
+    def seed(self) -> int:
+        return rapid_seed_grid(self.h)
+
+    def refine_stage(self, sync: bool = True):
+        return rapid_refine_stage(self.h, sync)
+
+    def split(self):
+        rapid_split(self.h)
+
+    def run(self):
+        rapid_run(self.h)
+        return self
+
+    def state(self):
+        return rapid_get_state(self.h)
+
+    def labels(self, out=None):
+        if out is None:
+            a = np.empty((self.H, self.W), np.int32)
+            rapid_read_labels(self.h, a.ctypes.data, a.strides[0], 0)
+            return a
+        rapid_read_labels(self.h, out.data_ptr(), out.stride(0) * 4, 1)
+        return out
+
+    def block_labels(self):
+        st = self.state()
+        s = st["block"]
+        nbx, nby = -(-self.W // s), -(-self.H // s)
+        a = np.empty((nby, nbx), np.int32)
+        rapid_read_block_labels(self.h, a.ctypes.data, a.size)
+        return a
+
+    def stats(self) -> np.ndarray:
+        M = self.state()["M"]
+        a = np.zeros(max(M, 1), SP_STATS_DTYPE)
+        rapid_read_stats(self.h, a.ctypes.data, a.size)
+        return a[:M]
+
+    def counters(self) -> rapid_counters:
+        return rapid_read_counters(self.h)
+
+    def counters_array(self) -> np.ndarray:
+        """num_stages x 8 int64: level, block, sweeps, eligible, evaluated, moves, merge
+        requests, merges (the oracle's counter layout)."""
+        c = self.counters()
+        rows = []
+        for i in range(c.num_stages):
+            s = c.stage[i]
+            rows.append([s.level, s.block, s.sweeps, s.eligible, s.evaluated, s.moves, s.merge_requests, s.merges])
+        return np.array(rows, np.int64).reshape(-1, 8)
+
+    def set_profiling(self, on: bool = True):
+        rapid_set_profiling(self.h, on)
+
+    def sync(self):
+        rapid_sync(self.h)

@@ -1,0 +1,232 @@
+// k_prep.cu — the non-sweep kernels: level images (box sums), seeding, stage split,
+// prediction, statistics recomputation and the readers.
+#include <climits>
+
+#include "../../include/rapid.h"
+#include "rapid_dev.cuh"
+
+namespace rapid {
+
+static inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// Level image of factor f (Sec. 2.2): coarse cell (X, Y) holds the exact R, G, B sums of
+// full-res [fX, min(fX + f, W)) x [fY, min(fY + f, H)).
+__global__ void pyramid_kernel(const unsigned char *img, long long pitch, int H, int W, int f, int Wl, int Hl,
+                               int4 *out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)Wl * Hl) return;
+  const int X = (int)(i % Wl), Y = (int)(i / Wl);
+  const int x0 = X * f, y0 = Y * f, x1 = min(x0 + f, W), y1 = min(y0 + f, H);
+  int r = 0, g = 0, b = 0;
+  for (int y = y0; y < y1; y++) {
+    const unsigned char *row = img + (long long)y * pitch + 3ll * x0;
+    for (int x = 0; x < x1 - x0; x++) {
+      r += row[3 * x];
+      g += row[3 * x + 1];
+      b += row[3 * x + 2];
+    }
+  }
+  out[i] = make_int4(r, g, b, 0);
+}
+
+cudaError_t launch_pyramid(const unsigned char *img, long long pitch, int H, int W, int f, int Wl, int Hl,
+                           int4 *out, cudaStream_t s) {
+  const long long n = (long long)Wl * Hl;
+  pyramid_kernel<<<blocks_for(n, 256), 256, 0, s>>>(img, pitch, H, W, f, Wl, Hl, out);
+  return cudaGetLastError();
+}
+
+// Regular seed grid (Algorithm RAPID): block (bx, by) of the first stage gets label
+// floor(by gy / nby) gx + floor(bx gx / nbx); its sums go to S and its rectangle to the
+// label's bounding box.
+__global__ void seed_kernel(StageArgs a, int gx, int gy) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)a.nbx * a.nby) return;
+  const int bx = (int)(i % a.nbx), by = (int)(i / a.nbx);
+  const int lbl = (int)(((long long)by * gy / a.nby) * gx + ((long long)bx * gx / a.nbx));
+  a.lab[i] = lbl;
+  const BlockSums bs = block_sums(a, bx, by);
+  atomic_add_i64(&a.st.N[lbl], bs.w);
+  atomic_add_i64(&a.st.R[lbl], bs.r);
+  atomic_add_i64(&a.st.G[lbl], bs.g);
+  atomic_add_i64(&a.st.B[lbl], bs.b);
+  atomic_add_i64(&a.st.X[lbl], bs.x);
+  atomic_add_i64(&a.st.Y[lbl], bs.y);
+  const int x0 = bx * a.side, y0 = by * a.side;
+  atomicMin(&a.st.bbox[lbl].x, x0);
+  atomicMin(&a.st.bbox[lbl].y, y0);
+  atomicMax(&a.st.bbox[lbl].z, x0 + bs.bw - 1);
+  atomicMax(&a.st.bbox[lbl].w, y0 + bs.bh - 1);
+}
+
+__global__ void reset_labels_kernel(DevStats st, DevMerge mg) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= st.M) return;
+  st.N[k] = st.R[k] = st.G[k] = st.B[k] = st.X[k] = st.Y[k] = st.init[k] = 0;
+  st.dN[k] = st.dR[k] = st.dG[k] = st.dB[k] = st.dX[k] = st.dY[k] = 0;
+  st.dirty[k] = 0;
+  st.y[k] = 0;
+  st.imp[k] = 0;
+  st.bbox[k] = make_int4(INT_MAX, INT_MAX, INT_MIN, INT_MIN);
+  mg.req_min[k] = INT_MAX;
+  mg.req_flag[k] = 0;
+  mg.target[k] = -1;
+  mg.involved[k] = 0;
+}
+
+__global__ void init_size_kernel(DevStats st) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < st.M) st.init[k] = st.N[k];
+}
+
+cudaError_t launch_seed(const StageArgs &a, int gx, int gy, cudaStream_t s, int *launches) {
+  reset_labels_kernel<<<blocks_for(a.st.M, 256), 256, 0, s>>>(a.st, a.mg);
+  const long long n = (long long)a.nbx * a.nby;
+  seed_kernel<<<blocks_for(n, 256), 256, 0, s>>>(a, gx, gy);
+  init_size_kernel<<<blocks_for(a.st.M, 256), 256, 0, s>>>(a.st);
+  *launches += 3;
+  return cudaGetLastError();
+}
+
+// S recomputed from the label map at the current stage's level (the multi-scale
+// baseline's per-level statistics; identical to the carried S).
+__global__ void zero_stats_kernel(DevStats st) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < st.M) st.N[k] = st.R[k] = st.G[k] = st.B[k] = st.X[k] = st.Y[k] = 0;
+}
+
+__global__ void accumulate_stats_kernel(StageArgs a) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)a.nbx * a.nby) return;
+  const int bx = (int)(i % a.nbx), by = (int)(i / a.nbx);
+  const int lbl = a.lab[i];
+  const BlockSums bs = block_sums(a, bx, by);
+  atomic_add_i64(&a.st.N[lbl], bs.w);
+  atomic_add_i64(&a.st.R[lbl], bs.r);
+  atomic_add_i64(&a.st.G[lbl], bs.g);
+  atomic_add_i64(&a.st.B[lbl], bs.b);
+  atomic_add_i64(&a.st.X[lbl], bs.x);
+  atomic_add_i64(&a.st.Y[lbl], bs.y);
+}
+
+cudaError_t launch_recompute(const StageArgs &a, cudaStream_t s, int *launches) {
+  zero_stats_kernel<<<blocks_for(a.st.M, 256), 256, 0, s>>>(a.st);
+  accumulate_stats_kernel<<<blocks_for((long long)a.nbx * a.nby, 256), 256, 0, s>>>(a);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+// Stage split: each block becomes 2x2 blocks with its label ("map superpixels' labels").
+__global__ void split_kernel(const int *src, int snbx, int *dst, int dnbx, int dnby) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)dnbx * dnby) return;
+  const int cx = (int)(i % dnbx), cy = (int)(i / dnbx);
+  dst[i] = src[(long long)(cy >> 1) * snbx + (cx >> 1)];
+}
+
+cudaError_t launch_split(const int *src, int snbx, int *dst, int dnbx, int dnby, cudaStream_t s) {
+  split_kernel<<<blocks_for((long long)dnbx * dnby, 256), 256, 0, s>>>(src, snbx, dst, dnbx, dnby);
+  return cudaGetLastError();
+}
+
+// Prediction at the start of level 2 (Eq. predict) with the integer stand-in classifier
+// h(k) = 3 T N_k - (R_k + G_k + B_k); y = 1 when h >= 0.
+__global__ void classify_kernel(DevStats st, long long hT) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= st.M) return;
+  const long long h = 3 * hT * st.N[k] - (st.R[k] + st.G[k] + st.B[k]);
+  st.y[k] = h >= 0 ? 1 : -1;
+  st.imp[k] = 0;
+}
+
+// Boundary superpixels (Eq. new_bound): labels 4-adjacent to a label of the other class.
+__global__ void importance_kernel(const int *lab, int nbx, int nby, DevStats st) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)nbx * nby) return;
+  const int bx = (int)(i % nbx), by = (int)(i / nbx);
+  const int a = lab[i];
+  if (bx + 1 < nbx) {
+    const int e = lab[i + 1];
+    if (e != a && st.y[e] != st.y[a]) {
+      st.imp[a] = 1;
+      st.imp[e] = 1;
+    }
+  }
+  if (by + 1 < nby) {
+    const int b = lab[i + nbx];
+    if (b != a && st.y[b] != st.y[a]) {
+      st.imp[a] = 1;
+      st.imp[b] = 1;
+    }
+  }
+}
+
+cudaError_t launch_predict(const int *lab, int nbx, int nby, const DevStats &st, long long hT, cudaStream_t s,
+                           int *launches) {
+  classify_kernel<<<blocks_for(st.M, 256), 256, 0, s>>>(st, hT);
+  importance_kernel<<<blocks_for((long long)nbx * nby, 256), 256, 0, s>>>(lab, nbx, nby, st);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+// Full-resolution label map from a block-resolution one.
+__global__ void upsample_kernel(const int *lab, int nbx, int side, int H, int W, int *dst, long long pitch_elems) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)H * W) return;
+  const int x = (int)(i % W), y = (int)(i / W);
+  dst[(long long)y * pitch_elems + x] = lab[(long long)(y / side) * nbx + x / side];
+}
+
+cudaError_t launch_upsample(const int *lab, int nbx, int side, int H, int W, int *dst, long long pitch_elems,
+                            cudaStream_t s) {
+  upsample_kernel<<<blocks_for((long long)H * W, 256), 256, 0, s>>>(lab, nbx, side, H, W, dst, pitch_elems);
+  return cudaGetLastError();
+}
+
+__global__ void pack_stats_kernel(DevStats st, rapid_sp_stats *out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= st.M) return;
+  rapid_sp_stats v;
+  v.n = st.N[k];
+  v.sum_r = st.R[k];
+  v.sum_g = st.G[k];
+  v.sum_b = st.B[k];
+  v.sum_x = st.X[k];
+  v.sum_y = st.Y[k];
+  v.init_size = st.init[k];
+  v.y = st.y[k];
+  v.important = st.imp[k];
+  out[k] = v;
+}
+
+cudaError_t launch_pack_stats(const DevStats &st, rapid_sp_stats *out, cudaStream_t s) {
+  pack_stats_kernel<<<blocks_for(st.M, 256), 256, 0, s>>>(st, out);
+  return cudaGetLastError();
+}
+
+__global__ void init_counters_kernel(long long *cnt, Schedule sch) {
+  const int i = threadIdx.x;
+  if (i >= RAPID_MAX_STAGES) return;
+  for (int j = 0; j < CNT_N; j++) cnt[i * CNT_N + j] = 0;
+  if (i < sch.n) {
+    cnt[i * CNT_N + CNT_LEVEL] = sch.level[i];
+    cnt[i * CNT_N + CNT_SIDE] = sch.side[i];
+  }
+}
+
+cudaError_t launch_init_counters(long long *cnt, const Schedule &sch, cudaStream_t s) {
+  init_counters_kernel<<<1, RAPID_MAX_STAGES, 0, s>>>(cnt, sch);
+  return cudaGetLastError();
+}
+
+__global__ void simple_table_kernel(unsigned char *out) {
+  const unsigned m = threadIdx.x;
+  out[m] = simple_mask(m) ? 1 : 0;
+}
+
+cudaError_t launch_simple_table(unsigned char *out, cudaStream_t s) {
+  simple_table_kernel<<<1, 256, 0, s>>>(out);
+  return cudaGetLastError();
+}
+
+}  // namespace rapid

@@ -1,0 +1,265 @@
+// rapid_dev.cuh — device-side data layout and helpers shared by the kernels of the
+// coarse-to-fine topology-preserving superpixel refinement (RAPID, ICME 2017).
+//
+// Layout in HBM (all row-major):
+//   image   H x W interleaved RGB bytes, rows img_pitch bytes apart (multiple of 16)
+//   level   for each image level with factor f > 1: ceil(H/f) x ceil(W/f) int4 = exact
+//           (R, G, B, 0) sums of the f x f full-res footprint (Sec. 2.2, box "resize")
+//   labels  two int32 maps sized for the finest stage; the current stage uses nby x nbx
+//   S       structure of arrays over label ids: count, R, G, B, x, y, InitSize (int64),
+//           phase deltas of the first six (int64), snapshot means (5 doubles), class y
+//           (int8), boundary-superpixel flag (uint8), conservative bounding box (int4)
+// Position sums of a block are not stored: a block is an axis-aligned rectangle of
+// full-res pixels, so its count and x/y sums follow from its corners.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rapid {
+
+enum { CNT_LEVEL = 0, CNT_SIDE, CNT_SWEEPS, CNT_ELIG, CNT_EVAL, CNT_MOVES, CNT_REQ, CNT_MERGES, CNT_N };
+
+// Device error word values (0 = fine).
+enum { DERR_TIMEOUT = 1, DERR_MERGE_OVERFLOW = 2 };
+
+struct DevStats {
+  long long *N, *R, *G, *B, *X, *Y, *init;
+  long long *dN, *dR, *dG, *dB, *dX, *dY;
+  double *mR, *mG, *mB, *mX, *mY;
+  unsigned char *dirty;
+  signed char *y;
+  unsigned char *imp;
+  int4 *bbox;  // inclusive full-res pixel box: x0, y0, x1, y1
+  int M;
+};
+
+struct DevMerge {
+  int *req_count;   // requests (distinct labels) of the phase
+  int *req_list;    // [M] requested label ids
+  int *req_min;     // [M] smallest requesting block index per label (INT_MAX = none)
+  int *req_flag;    // [M] 1 when the label is in req_list
+  int *target;      // [M] chosen merge target (or -1)
+  int *order;       // [M] scratch: requests sorted by req_min
+  int2 *acc;        // [M] accepted (source, target) pairs of the phase
+  int *acc_count;
+  unsigned char *involved;  // [M]
+};
+
+struct DevCtl {
+  unsigned int *bar;             // [0] arrivals, [1] generation
+  int *err;                      // first device error (0 = none)
+  long long spin_ns;             // give-up time of one barrier wait
+  unsigned long long *changes;   // [3] moves + merges of the sweep, rotating slots
+  long long *cnt;                // this stage's counters [CNT_N]
+};
+
+struct StageArgs {
+  int H, W;           // full-res image
+  int side;           // block side s (full-res px)
+  int nbx, nby;       // block grid ceil(W/s) x ceil(H/s)
+  int level, f, k;    // level, its factor, coarse cells per block side (s / f)
+  int Wl, Hl;         // level dims
+  const unsigned char *img;
+  long long img_pitch;
+  const int4 *pyr;    // level sums (f > 1), else unused
+  int *lab;           // nby x nbx labels
+  DevStats st;
+  DevMerge mg;
+  DevCtl ctl;
+  int imp_on, imp_rule;
+  double lam_pos, lam_b2;
+  int size_mode, lo_num, lo_den, hi_num, hi_den;
+  int max_sweeps;
+};
+
+// Stage schedule handed to the counter initialiser (by value).
+struct Schedule {
+  int n;
+  int level[32];
+  int side[32];
+};
+
+#ifdef __CUDACC__
+
+// ---------------------------------------------------------------- topology test
+// Removing the centre from its label keeps the label 4-connected iff the label's ring
+// cells that are 4-neighbours of the centre all lie in one 4-connected arc of the 3x3
+// ring (E_topo of Eq. equa:energy1).  Ring order NW, N, NE, E, SE, S, SW, W: consecutive
+// ring cells are 4-adjacent and no others are, so the ring's 4-components are the cyclic
+// runs of set bits; a run without a 4-neighbour bit is an isolated corner.
+__host__ __device__ inline int popc8(unsigned v) {
+  v &= 0xFFu;
+  v = v - ((v >> 1) & 0x55u);
+  v = (v & 0x33u) + ((v >> 2) & 0x33u);
+  return (int)((v + (v >> 4)) & 0x0Fu);
+}
+
+__host__ __device__ inline bool simple_mask(unsigned m) {
+  m &= 0xFFu;
+  if ((m & 0xAAu) == 0) return false;  // no 4-neighbour keeps the label
+  if (m == 0xFFu) return true;
+  unsigned prev = ((m << 1) | (m >> 7)) & 0xFFu;  // bit i holds ring bit i-1
+  unsigned next = ((m >> 1) | (m << 7)) & 0xFFu;  // bit i holds ring bit i+1
+  int runs = popc8(m & ~prev);
+  int lone_corners = popc8(m & 0x55u & ~prev & ~next);
+  return runs - lone_corners == 1;
+}
+
+// ---------------------------------------------------------------- grid barrier
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(const volatile int *)p; }
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
+  return *(const volatile unsigned long long *)p;
+}
+
+// All CTAs of a co-resident (cooperative) grid meet here.  Thread 0 of each CTA arrives
+// on a counter; the last arrival resets it and bumps the generation.  Every wait is
+// bounded by ctl.spin_ns (and an iteration cap); on give-up the CTA records
+// DERR_TIMEOUT and the whole grid returns false, so no kernel can hang.
+__device__ inline bool grid_sync(const DevCtl &c) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int good = 1;
+    unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+    unsigned gen = ld_acquire_u32(&c.bar[1]);
+    __threadfence();
+    unsigned arrived = atomicAdd(&c.bar[0], 1u);
+    if (arrived == nb - 1) {
+      atomicExch(&c.bar[0], 0u);
+      __threadfence();
+      atomicAdd(&c.bar[1], 1u);
+    } else {
+      unsigned long long t0 = global_ns();
+      long long iters = 0;
+      while (ld_acquire_u32(&c.bar[1]) == gen) {
+        if (ld_volatile_i32(c.err) != 0) { good = 0; break; }
+        if ((long long)(global_ns() - t0) > c.spin_ns || ++iters > (1ll << 26)) {
+          atomicCAS(c.err, 0, (int)DERR_TIMEOUT);
+          good = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// ---------------------------------------------------------------- block sums
+struct BlockSums {
+  long long w, r, g, b, x, y;
+  int bw, bh;
+};
+
+// Sums of block (bx, by) at the current stage: colour from the level's coarse cells
+// (or the image at f = 1), count and position from the block rectangle
+// [s bx, min(s bx + s, W)) x [s by, min(s by + s, H)).
+__device__ inline BlockSums block_sums(const StageArgs &a, int bx, int by) {
+  BlockSums o;
+  int x0 = bx * a.side, y0 = by * a.side;
+  int x1 = min(x0 + a.side, a.W), y1 = min(y0 + a.side, a.H);
+  o.bw = x1 - x0;
+  o.bh = y1 - y0;
+  o.w = (long long)o.bw * o.bh;
+  o.x = (long long)o.bh * (((long long)(x0 + x1 - 1) * o.bw) >> 1);
+  o.y = (long long)o.bw * (((long long)(y0 + y1 - 1) * o.bh) >> 1);
+  long long r = 0, g = 0, b = 0;
+  if (a.f == 1) {
+    for (int yy = y0; yy < y1; yy++) {
+      const unsigned char *row = a.img + (long long)yy * a.img_pitch + 3ll * x0;
+      for (int xx = 0; xx < o.bw; xx++) {
+        r += row[3 * xx];
+        g += row[3 * xx + 1];
+        b += row[3 * xx + 2];
+      }
+    }
+  } else {
+    int X0 = bx * a.k, Y0 = by * a.k;
+    int X1 = min(X0 + a.k, a.Wl), Y1 = min(Y0 + a.k, a.Hl);
+    for (int Y = Y0; Y < Y1; Y++)
+      for (int X = X0; X < X1; X++) {
+        int4 c = a.pyr[(long long)Y * a.Wl + X];
+        r += c.x;
+        g += c.y;
+        b += c.z;
+      }
+  }
+  o.r = r;
+  o.g = g;
+  o.b = b;
+  return o;
+}
+
+// ---------------------------------------------------------------- energies (binary64)
+// Block energy under label means (c, mu), up to a label-independent constant
+// (Eq. equa:energy1 summed over the block's pixels):
+//   sum_ch [(w c) c - (2 S) c] + lambda_pos sum_d [(w mu) mu - (2 P) mu] + 2 lambda_b B
+// evaluated with explicitly rounded operations in exactly this order (never fused).
+__device__ __forceinline__ double blk_energy(double w, double r2, double g2, double b2, double x2,
+                                             double y2, double cR, double cG, double cB, double mX,
+                                             double mY, double Bk, double lam_pos, double lam_b2) {
+  double eR = __dsub_rn(__dmul_rn(__dmul_rn(w, cR), cR), __dmul_rn(r2, cR));
+  double eG = __dsub_rn(__dmul_rn(__dmul_rn(w, cG), cG), __dmul_rn(g2, cG));
+  double eB = __dsub_rn(__dmul_rn(__dmul_rn(w, cB), cB), __dmul_rn(b2, cB));
+  double ec = __dadd_rn(__dadd_rn(eR, eG), eB);
+  double ex = __dsub_rn(__dmul_rn(__dmul_rn(w, mX), mX), __dmul_rn(x2, mX));
+  double ey = __dsub_rn(__dmul_rn(__dmul_rn(w, mY), mY), __dmul_rn(y2, mY));
+  double ep = __dadd_rn(ex, ey);
+  return __dadd_rn(__dadd_rn(ec, __dmul_rn(lam_pos, ep)), __dmul_rn(lam_b2, Bk));
+}
+
+// Snapshot means of label k from its exact sums: c = S / N (IEEE division).
+__device__ __forceinline__ void set_means(const DevStats &s, int k) {
+  long long n = s.N[k];
+  if (n > 0) {
+    double dn = __ll2double_rn(n);
+    s.mR[k] = __ddiv_rn(__ll2double_rn(s.R[k]), dn);
+    s.mG[k] = __ddiv_rn(__ll2double_rn(s.G[k]), dn);
+    s.mB[k] = __ddiv_rn(__ll2double_rn(s.B[k]), dn);
+    s.mX[k] = __ddiv_rn(__ll2double_rn(s.X[k]), dn);
+    s.mY[k] = __ddiv_rn(__ll2double_rn(s.Y[k]), dn);
+  } else {
+    s.mR[k] = s.mG[k] = s.mB[k] = s.mX[k] = s.mY[k] = 0.0;
+  }
+}
+
+// Merge cost of labels a and n (Sec. 3.1): the Ward increase of the colour and position
+// energy, Na Nn / (Na + Nn) * (|ca - cn|^2 + lambda_pos |mua - mun|^2).
+__device__ __forceinline__ double ward_cost(const DevStats &s, int a, int n, double lam_pos) {
+  double t = __ddiv_rn(__dmul_rn(__ll2double_rn(s.N[a]), __ll2double_rn(s.N[n])),
+                       __ll2double_rn(s.N[a] + s.N[n]));
+  double d0 = __dsub_rn(s.mR[a], s.mR[n]);
+  double d1 = __dsub_rn(s.mG[a], s.mG[n]);
+  double d2 = __dsub_rn(s.mB[a], s.mB[n]);
+  double dc = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+  double e0 = __dsub_rn(s.mX[a], s.mX[n]);
+  double e1 = __dsub_rn(s.mY[a], s.mY[n]);
+  double dm = __dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1));
+  return __dmul_rn(t, __dadd_rn(dc, __dmul_rn(lam_pos, dm)));
+}
+
+__device__ __forceinline__ void atomic_add_i64(long long *p, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
+}
+
+#endif  // __CUDACC__
+
+// Host-side launchers (defined in the .cu files).
+cudaError_t launch_stage(const StageArgs &a, int grid, int block, cudaStream_t s);
+int stage_block_threads();
+const void *stage_kernel_ptr();
+
+}  // namespace rapid

@@ -1,0 +1,47 @@
+"""Shared helpers of the GPU tests: run the CUDA path through the C ABI and the CPU
+oracle on the same seeded input, and compare."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+STAT_FIELDS = ("n", "sum_r", "sum_g", "sum_b", "sum_x", "sum_y", "init_size")
+
+
+def gpu_run(rgb: np.ndarray, device_input: bool = True, **params):
+    import torch
+
+    import paper_1704_02083_gb300 as pkg
+
+    stream = torch.cuda.current_stream()
+    with pkg.Context(stream=stream, **params) as ctx:
+        if device_input:
+            ctx.set_image(torch.from_numpy(np.ascontiguousarray(rgb)).cuda())
+        else:
+            ctx.set_image(rgb)
+        ctx.run()
+        lab = ctx.labels()
+        st = ctx.stats()
+        cnt = ctx.counters_array()
+    stats = np.stack([st[f] for f in STAT_FIELDS], 1)
+    return lab, stats, st["y"].astype(np.int8), st["important"].astype(np.uint8), cnt
+
+
+def oracle_run(rgb: np.ndarray, **params):
+    p = {k: v for k, v in params.items() if k != "spin_limit_ns"}
+    return oracle.run(rgb, **p)
+
+
+def assert_parity(rgb, **params):
+    lab, st, y, imp, cnt = gpu_run(rgb, **params)
+    rlab, rst, ry, rimp, rcnt = oracle_run(rgb, **params)
+    assert lab.shape == rlab.shape
+    diff = np.argwhere(lab != rlab)
+    assert diff.size == 0, f"{len(diff)} labels differ, first at {diff[:3].tolist()}"
+    np.testing.assert_array_equal(st, rst)
+    if params.get("predict", 0):
+        np.testing.assert_array_equal(y, ry)
+        np.testing.assert_array_equal(imp, rimp)
+    np.testing.assert_array_equal(cnt, rcnt)
+    return lab, st, cnt
