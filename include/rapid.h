@@ -100,6 +100,9 @@ typedef struct rapid_stage_counters {
   int64_t merges;          /* merges accepted */
   float kernel_ms;         /* device time of the stage's refinement launch when profiling is
                               on (rapid_set_profiling), else -1 */
+  float section_ms[5];     /* with profiling on, as seen by the launch's first CTA: block
+                              evaluation, wait after it, statistics commit, wait after it,
+                              merge resolution (with its waits); else 0 */
   float pad2;
 } rapid_stage_counters;
 

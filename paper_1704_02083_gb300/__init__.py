@@ -48,7 +48,7 @@ class rapid_stage_counters(C.Structure):
     _fields_ = [("level", C.c_int32), ("block", C.c_int32), ("sweeps", C.c_int32), ("pad", C.c_int32),
                 ("eligible", C.c_int64), ("evaluated", C.c_int64), ("moves", C.c_int64),
                 ("merge_requests", C.c_int64), ("merges", C.c_int64), ("kernel_ms", C.c_float),
-                ("pad2", C.c_float)]
+                ("section_ms", C.c_float * 5), ("pad2", C.c_float)]
 
 
 class rapid_counters(C.Structure):

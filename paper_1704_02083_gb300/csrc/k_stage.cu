@@ -309,18 +309,39 @@ __device__ void merge_relabel(const StageArgs &a, int nacc) {
   }
 }
 
+// Section timer of the first CTA (profiling only).
+struct Timer {
+  long long *prof;
+  unsigned long long t;
+  __device__ Timer(long long *p) : prof((blockIdx.x == 0 && threadIdx.x == 0) ? p : nullptr), t(0) {
+    if (prof) t = global_ns();
+  }
+  __device__ __forceinline__ void lap(int section) {
+    if (prof) {
+      const unsigned long long n = global_ns();
+      prof[section] += (long long)(n - t);
+      t = n;
+    }
+  }
+};
+
 __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs a) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.st.M; k += gridDim.x * blockDim.x) set_means(a.st, k);
   if (!grid_sync(a.ctl)) return;
+  Timer tm(a.ctl.prof);
   for (int sweep = 0; sweep < a.max_sweeps; sweep++) {
     unsigned long long *changes = &a.ctl.changes[sweep % 3];
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl.changes[(sweep + 1) % 3] = 0;
     for (int ph = 0; ph < 9; ph++) {
       eval_phase(a, ph, changes);
+      tm.lap(PROF_EVAL);
       if (!grid_sync(a.ctl)) return;
+      tm.lap(PROF_SYNC1);
       const int rq = ld_volatile_i32(a.mg.req_count);
       commit_phase(a);
+      tm.lap(PROF_COMMIT);
       if (!grid_sync(a.ctl)) return;
+      tm.lap(PROF_SYNC2);
       if (rq > 0) {
         merge_targets(a, rq);
         if (!grid_sync(a.ctl)) return;
@@ -328,6 +349,7 @@ __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs a) {
         if (!grid_sync(a.ctl)) return;
         merge_relabel(a, ld_volatile_i32(a.mg.acc_count));
         if (!grid_sync(a.ctl)) return;
+        tm.lap(PROF_MERGE);
       }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl.cnt[CNT_SWEEPS] += 1;

@@ -65,6 +65,7 @@ struct rapid_ctx {
   int imp_on;
   long long launches;
   int profiling;
+  long long *prof;  // [RAPID_MAX_STAGES][PROF_N] section times (ns)
   cudaEvent_t ev[RAPID_MAX_STAGES][2];
   int ev_ok[RAPID_MAX_STAGES];
 };
@@ -150,7 +151,7 @@ extern "C" rapid_status rapid_create(const rapid_params *p, void *cuda_stream, r
   ctx->coop_grid = ctx->nsm * per_sm;
   // control block: barrier (2 u32), error (i32), request/accept counts, sweep changes
   // (3 u64), counters.
-  size_t ctl_bytes = 64 + sizeof(long long) * CNT_N * RAPID_MAX_STAGES;
+  size_t ctl_bytes = 64 + sizeof(long long) * (CNT_N + PROF_N) * RAPID_MAX_STAGES;
   if (cudaMalloc(&ctx->d_ctl_block, ctl_bytes) != cudaSuccess) {
     delete ctx;
     return RAPID_ENOMEM;
@@ -162,6 +163,7 @@ extern "C" rapid_status rapid_create(const rapid_params *p, void *cuda_stream, r
   ctx->mg.acc_count = (int *)(b + 16);
   ctx->ctl.changes = (unsigned long long *)(b + 24);
   ctx->ctl.cnt = (long long *)(b + 64);
+  ctx->prof = (long long *)(b + 64 + sizeof(long long) * CNT_N * RAPID_MAX_STAGES);
   ctx->ctl.spin_ns = p->spin_limit_ns;
   if (cudaMemsetAsync(ctx->d_ctl_block, 0, ctl_bytes, ctx->stream) != cudaSuccess) {
     cudaFree(ctx->d_ctl_block);
@@ -317,6 +319,7 @@ static StageArgs stage_args(rapid_ctx *ctx) {
   a.mg = ctx->mg;
   a.ctl = ctx->ctl;
   a.ctl.cnt = ctx->ctl.cnt + (long long)CNT_N * ctx->cur;
+  a.ctl.prof = ctx->profiling ? ctx->prof + (long long)PROF_N * ctx->cur : nullptr;
   a.imp_on = ctx->imp_on;
   a.imp_rule = ctx->p.importance_rule;
   a.lam_pos = ctx->lam_pos;
@@ -425,6 +428,7 @@ extern "C" rapid_status rapid_seed_grid(rapid_ctx *ctx, int32_t *M_out) {
     sch.side[i] = ctx->st_side[i];
   }
   CK(launch_init_counters(ctx->ctl.cnt, sch, ctx->stream));
+  CK(cudaMemsetAsync(ctx->prof, 0, sizeof(long long) * PROF_N * RAPID_MAX_STAGES, ctx->stream));
   CK(cudaMemsetAsync(ctx->mg.req_count, 0, 2 * sizeof(int), ctx->stream));
   int nl = 1;
   StageArgs a = stage_args(ctx);
@@ -606,6 +610,8 @@ extern "C" rapid_status rapid_read_counters(rapid_ctx *ctx, rapid_counters *dst)
   if (rs != RAPID_OK) return rs;
   long long c[CNT_N * RAPID_MAX_STAGES];
   CK(cudaMemcpy(c, ctx->ctl.cnt, sizeof c, cudaMemcpyDeviceToHost));
+  long long pr[PROF_N * RAPID_MAX_STAGES];
+  CK(cudaMemcpy(pr, ctx->prof, sizeof pr, cudaMemcpyDeviceToHost));
   dst->num_stages = ctx->cur >= 0 ? ctx->nstages : 0;
   dst->M = ctx->cur >= 0 ? ctx->M : 0;
   dst->launches = ctx->launches;
@@ -621,6 +627,7 @@ extern "C" rapid_status rapid_read_counters(rapid_ctx *ctx, rapid_counters *dst)
     o.merge_requests = ci[CNT_REQ];
     o.merges = ci[CNT_MERGES];
     o.kernel_ms = -1.0f;
+    for (int j = 0; j < PROF_N; j++) o.section_ms[j] = ctx->profiling ? (float)(pr[i * PROF_N + j] * 1e-6) : 0.0f;
     if (ctx->profiling && ctx->ev_ok[i] && i <= ctx->cur) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, ctx->ev[i][0], ctx->ev[i][1]) == cudaSuccess) o.kernel_ms = ms;

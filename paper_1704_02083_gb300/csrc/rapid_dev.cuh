@@ -19,6 +19,9 @@ namespace rapid {
 
 enum { CNT_LEVEL = 0, CNT_SIDE, CNT_SWEEPS, CNT_ELIG, CNT_EVAL, CNT_MOVES, CNT_REQ, CNT_MERGES, CNT_N };
 
+// Sections timed by the first CTA when profiling is on.
+enum { PROF_EVAL = 0, PROF_SYNC1, PROF_COMMIT, PROF_SYNC2, PROF_MERGE, PROF_N };
+
 // Device error word values (0 = fine).
 enum { DERR_TIMEOUT = 1, DERR_MERGE_OVERFLOW = 2 };
 
@@ -51,6 +54,7 @@ struct DevCtl {
   long long spin_ns;             // give-up time of one barrier wait
   unsigned long long *changes;   // [3] moves + merges of the sweep, rotating slots
   long long *cnt;                // this stage's counters [CNT_N]
+  long long *prof;               // this stage's section times [PROF_N] in ns, or null
 };
 
 struct StageArgs {

@@ -41,7 +41,7 @@ def test_invalid_arguments(pkg):
     with pytest.raises(pkg.RapidError) as e:
         pkg.rapid_create(pkg.rapid_default_params(num_levels=2, ratio_C=3))
     assert e.value.status == pkg.RAPID_EINVAL
-    with pkg.Context() as ctx:
+    with pkg.Context(K=16, init_block=2) as ctx:
         rgb = np.zeros((8, 8, 3), np.uint8)
         for H, W, pitch in ((0, 8, 24), (8, 0, 24), (8, 8, 23)):
             with pytest.raises(pkg.RapidError) as e:
