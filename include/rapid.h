@@ -193,6 +193,37 @@ rapid_status rapid_sync(rapid_ctx *ctx);
  * Host buffer of 256 bytes; runs a kernel on the current device and synchronises. */
 rapid_status rapid_simple_table(uint8_t *out256);
 
+/* Whole refinement of one small image without allocating any GPU memory.  The paper has
+ * no counterpart: this entry point exists for callers that cannot call cudaMalloc, such as
+ * services whose device memory is fully reserved up front by their own pool allocator, or
+ * latency-critical paths where cudaMalloc / cudaFree (which can synchronise the device)
+ * are not allowed.  It runs the same kernels as rapid_run (same results, bit for bit), but
+ * every byte of working memory comes from one fixed 16 MiB __device__ array inside the
+ * library; every GPU that loads the library holds that array until the process exits.
+ *
+ * p: parameters as for rapid_create.  rgb_dev: H x W interleaved RGB in device memory, rows
+ * rgb_pitch_bytes apart (>= 3*W), read only.  labels_dev: device H x W int32 output, rows
+ * labels_pitch_bytes apart (>= 4*W, multiple of 4).  stats_dev: device output of
+ * stats_capacity entries (>= M), index = label id.  *M_out (host, may be NULL) receives M.
+ * cuda_stream: the stream to run on (0 = legacy default).  All buffers belong to the
+ * caller.  The call synchronises the stream before returning.
+ *
+ * Limits: H*W <= RAPID_STATIC_MAX_PIXELS and M <= RAPID_STATIC_MAX_LABELS, and the image's
+ * level sums, label maps and per-label arrays must fit the fixed array; otherwise
+ * RAPID_ERANGE, with nothing launched.  EINVAL on a bad argument, ECUDA, ETIMEOUT as above.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and caches it for that device, so make the first call on each device before capturing
+ * any stream work.  All calls on a device share the array and it keeps the last call's
+ * contents; each call re-initialises what must start at zero.  Calls whose GPU work
+ * overlaps in time (other streams or host threads) race on the array: serialise them. */
+#define RAPID_STATIC_MAX_PIXELS (1 << 19)
+#define RAPID_STATIC_MAX_LABELS (1 << 13)
+rapid_status rapid_run_static(const rapid_params *p, const uint8_t *rgb_dev, int32_t H, int32_t W,
+                              int64_t rgb_pitch_bytes, int32_t *labels_dev, int64_t labels_pitch_bytes,
+                              rapid_sp_stats *stats_dev, int64_t stats_capacity, int32_t *M_out,
+                              void *cuda_stream);
+
 /* Human-readable name of a status.  Never NULL. */
 const char *rapid_status_string(rapid_status s);
 

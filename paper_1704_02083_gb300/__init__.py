@@ -92,6 +92,7 @@ def lib() -> C.CDLL:
         "rapid_set_profiling": (i32, [P, i32]),
         "rapid_sync": (i32, [P]),
         "rapid_simple_table": (i32, [P]),
+        "rapid_run_static": (i32, [C.POINTER(rapid_params), P, i32, i32, i64, P, i64, P, i64, pi32, P]),
         "rapid_status_string": (C.c_char_p, [i32]),
         "rapid_destroy": (None, [P]),
     }
@@ -202,6 +203,22 @@ def rapid_simple_table() -> np.ndarray:
 def rapid_destroy(ctx: int):
     if ctx:
         lib().rapid_destroy(ctx)
+
+
+RAPID_STATIC_MAX_PIXELS = 1 << 19
+RAPID_STATIC_MAX_LABELS = 1 << 13
+
+
+def rapid_run_static(params: rapid_params, rgb_dev_ptr: int, H: int, W: int, rgb_pitch_bytes: int,
+                     labels_dev_ptr: int, labels_pitch_bytes: int, stats_dev_ptr: int, stats_capacity: int,
+                     cuda_stream: int = 0) -> int:
+    """Whole refinement without any GPU allocation (for callers that cannot call cudaMalloc);
+    all buffers are the caller's device memory.  Returns M."""
+    M = C.c_int32()
+    _check(lib().rapid_run_static(C.byref(params), rgb_dev_ptr, H, W, rgb_pitch_bytes, labels_dev_ptr,
+                                  labels_pitch_bytes, stats_dev_ptr, stats_capacity, C.byref(M),
+                                  C.c_void_p(cuda_stream)), "rapid_run_static")
+    return M.value
 
 
 # ------------------------------------------------------------------ convenience wrapper

@@ -1,0 +1,286 @@
+// rapid_static.cu — rapid_run_static: the whole refinement of one small image with every
+// byte of working memory taken from one fixed device array, for callers that must not
+// allocate GPU memory.
+//
+// Who needs it: services whose device memory is fully reserved up front by another
+// allocator (a framework memory pool, a multi-tenant inference server), so a library
+// cudaMalloc would fail or steal from their budget; and latency-critical pipelines that
+// forbid cudaMalloc / cudaFree because those calls can synchronise the device.  Such
+// callers pass their input image and output buffers (device memory they already own);
+// this entry point never calls cudaMalloc, cudaFree or any allocating library routine.
+//
+// The working memory is g_scratch below: a file-scope __device__ array of
+// kStaticScratchBytes (16 MiB).  Every GPU that loads this library holds that array until
+// the process exits.  All calls on one device share it, and it keeps the last call's
+// contents, so each call re-initialises everything that must start at zero; two calls
+// whose GPU work overlaps in time (different streams or host threads) race on it and
+// must be serialised by the caller.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/rapid.h"
+#include "rapid_dev.cuh"
+
+namespace rapid {
+cudaError_t launch_pyramid(const unsigned char *img, long long pitch, int H, int W, int f, int Wl, int Hl,
+                           int4 *out, cudaStream_t s);
+cudaError_t launch_seed(const StageArgs &a, int gx, int gy, cudaStream_t s, int *launches);
+cudaError_t launch_recompute(const StageArgs &a, cudaStream_t s, int *launches);
+cudaError_t launch_split(const int *src, int snbx, int *dst, int dnbx, int dnby, cudaStream_t s);
+cudaError_t launch_predict(const int *lab, int nbx, int nby, const DevStats &st, long long hT, cudaStream_t s,
+                           int *launches);
+cudaError_t launch_upsample(const int *lab, int nbx, int side, int H, int W, int *dst, long long pitch_elems,
+                            cudaStream_t s);
+cudaError_t launch_pack_stats(const DevStats &st, rapid_sp_stats *out, cudaStream_t s);
+cudaError_t launch_init_counters(long long *cnt, const Schedule &sch, cudaStream_t s);
+}  // namespace rapid
+
+using namespace rapid;
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;
+constexpr int kMaxDevices = 64;
+constexpr int kMaxLevelsStatic = 8;
+
+__device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
+
+std::mutex g_setup_mutex;
+unsigned char *g_scratch_addr[kMaxDevices];  // device address of g_scratch per device
+
+// Device address of g_scratch on the current device, looked up once per device.  In host
+// code the name g_scratch is only a host-side stand-in, never a device address.
+rapid_status scratch_on_current_device(unsigned char **out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RAPID_ECUDA;
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (!g_scratch_addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || p == nullptr) return RAPID_ECUDA;
+    g_scratch_addr[dev] = (unsigned char *)p;
+  }
+  *out = g_scratch_addr[dev];
+  return RAPID_OK;
+}
+
+// Bump allocator over the fixed array (256-byte aligned pieces).
+struct Carve {
+  unsigned char *base;
+  size_t used, cap;
+  void *take(size_t n) {
+    n = (n + 255) / 256 * 256;
+    if (n > cap - used) return nullptr;
+    void *r = base + used;
+    used += n;
+    return r;
+  }
+};
+
+bool pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *rgb_dev, int32_t H, int32_t W,
+                                         int64_t rgb_pitch_bytes, int32_t *labels_dev, int64_t labels_pitch_bytes,
+                                         rapid_sp_stats *stats_dev, int64_t stats_capacity, int32_t *M_out,
+                                         void *cuda_stream) {
+  if (!p || !rgb_dev || !labels_dev || !stats_dev) return RAPID_EINVAL;
+  if (H < 1 || W < 1 || rgb_pitch_bytes < 3ll * W || labels_pitch_bytes < 4ll * W || labels_pitch_bytes % 4)
+    return RAPID_EINVAL;
+  if (p->num_levels < 1 || p->num_levels > kMaxLevelsStatic) return RAPID_EINVAL;
+  if (p->num_levels > 1 && (!pow2(p->ratio_C) || p->ratio_C < 2)) return RAPID_EINVAL;
+  if (!pow2(p->init_block) || !pow2(p->final_grain) || p->init_block > (1 << 20)) return RAPID_EINVAL;
+  if (p->K < 1 || p->size_mode < 0 || p->size_mode > 2 || p->max_sweeps < 1) return RAPID_EINVAL;
+  if (p->lo_den <= 0 || p->hi_den <= 0 || p->lo_num < 0 || p->hi_num < 0) return RAPID_EINVAL;
+  if (!std::isfinite(p->lambda_pos0) || !std::isfinite(p->lambda_b)) return RAPID_EINVAL;
+  if ((p->predict | p->reuse | p->importance_rule) & ~1) return RAPID_EINVAL;
+  if (p->spin_limit_ns < 0 || p->h_T < 0 || p->h_T > (1ll << 40)) return RAPID_EINVAL;
+  if ((long long)H * W > RAPID_STATIC_MAX_PIXELS) return RAPID_ERANGE;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+
+  // Levels and stages (same schedule as rapid_run).
+  const int L = p->num_levels;
+  int f[kMaxLevelsStatic + 1], Wl[kMaxLevelsStatic + 1], Hl[kMaxLevelsStatic + 1];
+  for (int l = 1; l <= L; l++) {
+    long long ff = 1;
+    for (int i = 0; i < L - l; i++) ff *= p->ratio_C;
+    if (ff > (1 << 20)) return RAPID_EINVAL;
+    f[l] = (int)ff;
+    Wl[l] = cdiv(W, f[l]);
+    Hl[l] = cdiv(H, f[l]);
+  }
+  int nst = 0, lev[RAPID_MAX_STAGES], side[RAPID_MAX_STAGES];
+  int s = p->init_block < f[1] ? f[1] : p->init_block;
+  while (s >= 1 && s >= p->final_grain) {
+    int lv = 0;
+    for (int l = 1; l <= L; l++)
+      if (f[l] <= s) {
+        lv = l;
+        break;
+      }
+    if (lv == 0) break;
+    if (nst >= RAPID_MAX_STAGES) return RAPID_ERANGE;
+    lev[nst] = lv;
+    side[nst] = s;
+    nst++;
+    s /= 2;
+  }
+  if (nst == 0) {
+    lev[0] = 1;
+    side[0] = p->init_block < f[1] ? f[1] : p->init_block;
+    nst = 1;
+  }
+  const int nbx0 = cdiv(W, side[0]), nby0 = cdiv(H, side[0]);
+  int gx = (int)std::floor(std::sqrt((double)p->K * (double)W / (double)H) + 0.5);
+  if (gx < 1) gx = 1;
+  int gy = (int)std::floor((double)p->K / (double)gx + 0.5);
+  if (gy < 1) gy = 1;
+  if (gx > nbx0) gx = nbx0;
+  if (gy > nby0) gy = nby0;
+  const int M = gx * gy;
+  if (M > RAPID_STATIC_MAX_LABELS) return RAPID_ERANGE;
+  if (stats_capacity < M) return RAPID_EINVAL;
+
+  // Carve the fixed array.
+  unsigned char *base = nullptr;
+  rapid_status rs = scratch_on_current_device(&base);
+  if (rs != RAPID_OK) return rs;
+  Carve cv{base, 0, kStaticScratchBytes};
+  const size_t ctl_bytes = 64 + sizeof(long long) * CNT_N * RAPID_MAX_STAGES;
+  unsigned char *ctl = (unsigned char *)cv.take(ctl_bytes);
+  int4 *pyr[kMaxLevelsStatic + 1] = {nullptr};
+  for (int l = 1; l <= L; l++)
+    if (f[l] > 1) pyr[l] = (int4 *)cv.take((size_t)Wl[l] * Hl[l] * sizeof(int4));
+  const long long cap = (long long)cdiv(W, side[nst - 1]) * cdiv(H, side[nst - 1]);
+  int *lab[2] = {(int *)cv.take(cap * sizeof(int)), (int *)cv.take(cap * sizeof(int))};
+  const size_t m = (size_t)M;
+  DevStats st;
+  DevMerge mg;
+  std::memset(&st, 0, sizeof st);
+  std::memset(&mg, 0, sizeof mg);
+  long long **i64[] = {&st.N, &st.R, &st.G, &st.B, &st.X, &st.Y, &st.init, &st.dN, &st.dR, &st.dG, &st.dB, &st.dX, &st.dY};
+  for (long long **q : i64) *q = (long long *)cv.take(m * 8);
+  double **f64[] = {&st.mR, &st.mG, &st.mB, &st.mX, &st.mY};
+  for (double **q : f64) *q = (double *)cv.take(m * 8);
+  st.bbox = (int4 *)cv.take(m * 16);
+  mg.acc = (int2 *)cv.take(m * 8);
+  int **i32[] = {&mg.req_list, &mg.req_min, &mg.req_flag, &mg.target, &mg.order};
+  for (int **q : i32) *q = (int *)cv.take(m * 4);
+  st.dirty = (unsigned char *)cv.take(m);
+  st.y = (signed char *)cv.take(m);
+  st.imp = (unsigned char *)cv.take(m);
+  mg.involved = (unsigned char *)cv.take(m);
+  bool ok = ctl && lab[0] && lab[1] && st.bbox && mg.acc && st.dirty && st.y && st.imp && mg.involved;
+  for (long long **q : i64) ok = ok && *q;
+  for (double **q : f64) ok = ok && *q;
+  for (int **q : i32) ok = ok && *q;
+  for (int l = 1; l <= L; l++) ok = ok && (f[l] == 1 || pyr[l]);
+  if (!ok) return RAPID_ERANGE;  // this image and parameter set need more than the fixed array
+  st.M = M;
+  DevCtl c;
+  c.bar = (unsigned *)(ctl + 0);
+  c.err = (int *)(ctl + 8);
+  mg.req_count = (int *)(ctl + 12);
+  mg.acc_count = (int *)(ctl + 16);
+  c.changes = (unsigned long long *)(ctl + 24);
+  c.cnt = (long long *)(ctl + 64);
+  c.prof = nullptr;
+  c.spin_ns = p->spin_limit_ns;
+
+  // Cooperative grid size for the stage kernel (no allocation involved).
+  int dev = 0, nsm = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_ptr(), stage_block_threads(), 0) !=
+          cudaSuccess ||
+      per_sm < 1)
+    return RAPID_ECUDA;
+
+#define CKS(call)                                   \
+  do {                                              \
+    if ((call) != cudaSuccess) return RAPID_ECUDA; \
+  } while (0)
+
+  // Start from a clean control block: barrier, error word, request counts, counters.
+  CKS(cudaMemsetAsync(ctl, 0, ctl_bytes, stream));
+  for (int l = 1; l <= L; l++)
+    if (f[l] > 1) CKS(launch_pyramid(rgb_dev, rgb_pitch_bytes, H, W, f[l], Wl[l], Hl[l], pyr[l], stream));
+  Schedule sch;
+  std::memset(&sch, 0, sizeof sch);
+  sch.n = nst;
+  for (int i = 0; i < nst; i++) {
+    sch.level[i] = lev[i];
+    sch.side[i] = side[i];
+  }
+  CKS(launch_init_counters(c.cnt, sch, stream));
+
+  StageArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.H = H;
+  a.W = W;
+  a.img = rgb_dev;
+  a.img_pitch = rgb_pitch_bytes;
+  a.st = st;
+  a.mg = mg;
+  a.lam_pos = p->lambda_pos0 * ((double)M / ((double)H * (double)W));
+  a.lam_b2 = 2.0 * p->lambda_b;
+  a.imp_rule = p->importance_rule;
+  a.size_mode = p->size_mode;
+  a.lo_num = p->lo_num;
+  a.lo_den = p->lo_den;
+  a.hi_num = p->hi_num;
+  a.hi_den = p->hi_den;
+  a.max_sweeps = p->max_sweeps;
+  int buf = 0, nbx = nbx0, nby = nby0, launches = 0;
+  auto set_stage = [&](int i) {
+    a.side = side[i];
+    a.nbx = nbx;
+    a.nby = nby;
+    a.level = lev[i];
+    a.f = f[a.level];
+    a.k = a.side / a.f;
+    a.Wl = Wl[a.level];
+    a.Hl = Hl[a.level];
+    a.pyr = pyr[a.level];
+    a.lab = lab[buf];
+    a.ctl = c;
+    a.ctl.cnt = c.cnt + (long long)CNT_N * i;
+  };
+  set_stage(0);
+  CKS(launch_seed(a, gx, gy, stream, &launches));
+  for (int i = 0; i < nst; i++) {
+    if (i > 0) {
+      if (p->predict && lev[i] >= 2 && lev[i - 1] < 2) {
+        CKS(launch_predict(lab[buf], nbx, nby, st, p->h_T, stream, &launches));
+        a.imp_on = 1;
+      }
+      const int dnbx = cdiv(W, side[i]), dnby = cdiv(H, side[i]);
+      CKS(launch_split(lab[buf], nbx, lab[buf ^ 1], dnbx, dnby, stream));
+      buf ^= 1;
+      nbx = dnbx;
+      nby = dnby;
+      set_stage(i);
+      if (!p->reuse && lev[i] != lev[i - 1]) CKS(launch_recompute(a, stream, &launches));
+    }
+    CKS(cudaMemsetAsync(c.bar, 0, 8, stream));
+    CKS(cudaMemsetAsync(c.changes, 0, 3 * sizeof(unsigned long long), stream));
+    CKS(launch_stage(a, nsm * per_sm, stage_block_threads(), stream));
+  }
+  // Outputs into the caller's buffers.
+  const int sl = side[nst - 1];
+  if (sl == 1)
+    CKS(cudaMemcpy2DAsync(labels_dev, labels_pitch_bytes, lab[buf], 4ull * W, 4ull * W, H,
+                          cudaMemcpyDeviceToDevice, stream));
+  else
+    CKS(launch_upsample(lab[buf], nbx, sl, H, W, labels_dev, labels_pitch_bytes / 4, stream));
+  CKS(launch_pack_stats(st, stats_dev, stream));
+  int err = 0;
+  CKS(cudaMemcpyAsync(&err, c.err, sizeof err, cudaMemcpyDeviceToHost, stream));
+  CKS(cudaStreamSynchronize(stream));
+#undef CKS
+  if (M_out) *M_out = M;
+  return err ? RAPID_ETIMEOUT : RAPID_OK;
+}
