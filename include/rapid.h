@@ -74,6 +74,14 @@ typedef struct rapid_params {
                               h(k) = 3 h_T N_k - (R_k + G_k + B_k) (Eq. predict).  Default 150. */
   int64_t spin_limit_ns;   /* give-up time of each device-side barrier wait; 0 gives up at
                               once (used by tests).  Default 2e9 (2 s). */
+  int32_t use_filter;      /* 1: decide blocks in single precision with a certified error
+                              bound and fall back to binary64 when it cannot decide (same
+                              results as 0, faster).  Default 1. */
+  int32_t skip_tiles;      /* 1: skip tiles none of whose labels changed since their last scan
+                              (same results and counters as 0, faster).  Default 1. */
+  int32_t verify_filter;   /* 1: also decide every block in binary64 and count disagreements
+                              with the single-precision decisions (testing).  Default 0. */
+  int32_t pad;
 } rapid_params;
 
 #define RAPID_MAX_STAGES 32
@@ -98,6 +106,13 @@ typedef struct rapid_stage_counters {
   int64_t moves;           /* blocks relabelled */
   int64_t merge_requests;  /* moves replaced by a merge request (size bound hit) */
   int64_t merges;          /* merges accepted */
+  int64_t fp64_fallbacks;  /* evaluations the single-precision bound could not decide */
+  int64_t filter_mismatches; /* with verify_filter: single-precision decisions that differ
+                              from binary64 (must be 0) */
+  int64_t tiles_scanned;   /* tile-phase scans performed ... */
+  int64_t tiles_skipped;   /* ... and skipped because nothing they depend on changed */
+  int64_t merge_searches;  /* merge-target searches that scanned the label map ... */
+  int64_t merge_cache_hits; /* ... and requests answered by a still-valid earlier failure */
   float kernel_ms;         /* device time of the stage's refinement launch when profiling is
                               on (rapid_set_profiling), else -1 */
   float section_ms[5];     /* with profiling on, as seen by the launch's first CTA: block

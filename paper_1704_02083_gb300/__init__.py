@@ -35,6 +35,7 @@ class rapid_params(C.Structure):
         ("lo_num", C.c_int32), ("lo_den", C.c_int32), ("hi_num", C.c_int32), ("hi_den", C.c_int32),
         ("predict", C.c_int32), ("reuse", C.c_int32), ("importance_rule", C.c_int32),
         ("max_sweeps", C.c_int32), ("h_T", C.c_int64), ("spin_limit_ns", C.c_int64),
+        ("use_filter", C.c_int32), ("skip_tiles", C.c_int32), ("verify_filter", C.c_int32), ("pad", C.c_int32),
     ]
 
 
@@ -47,7 +48,10 @@ class rapid_sp_stats(C.Structure):
 class rapid_stage_counters(C.Structure):
     _fields_ = [("level", C.c_int32), ("block", C.c_int32), ("sweeps", C.c_int32), ("pad", C.c_int32),
                 ("eligible", C.c_int64), ("evaluated", C.c_int64), ("moves", C.c_int64),
-                ("merge_requests", C.c_int64), ("merges", C.c_int64), ("kernel_ms", C.c_float),
+                ("merge_requests", C.c_int64), ("merges", C.c_int64), ("fp64_fallbacks", C.c_int64),
+                ("filter_mismatches", C.c_int64), ("tiles_scanned", C.c_int64), ("tiles_skipped", C.c_int64),
+                ("merge_searches", C.c_int64), ("merge_cache_hits", C.c_int64),
+                ("kernel_ms", C.c_float),
                 ("section_ms", C.c_float * 5), ("pad2", C.c_float)]
 
 

@@ -1,0 +1,415 @@
+// eval_tile.cuh — block decisions of one phase, one warp per tile (included by k_stage.cu).
+//
+// A warp takes a 32 x 16-block tile, stages its labels with a 1-block halo in its own
+// shared window (34 x 18 int32) and gives each lane the tile's blocks of the phase class
+// (at most 11 x 6).  Warps never wait for each other inside a phase, so the SM hides the
+// global-memory latency of one warp's tile behind the work of the others.
+//
+// A tile is skipped when its record says that no label present in its window (halo
+// included) has changed since its last scan in this phase class and that scan issued no
+// merge request: every block would decide exactly as before, i.e. not move, so the
+// recorded eligible / evaluated counts are replayed.
+#pragma once
+
+// (included inside namespace rapid)
+static constexpr int kWinW = kTileW + 2, kWinH = kTileH + 2;
+
+struct WarpTile {
+  int win[kWinW * kWinH];
+  int hkey[32];             // labels of the window: open-addressing table (-1 = empty)
+  int hval[32];             // 1 when hkey[i] changed since the tile's previous scan
+  unsigned prevreq[3];      // blocks that requested a merge at the previous scan
+  unsigned req[3];          // blocks that request one now
+  int items[96];            // phase-class blocks (index j) that need a decision
+  int hcount, over;         // labels in the table; more than kTileLabels (or table full)
+};
+
+__device__ __forceinline__ int tab_slot(int v) { return (int)(((unsigned)v * 0x9E3779B1u) >> 27); }
+
+// Insert label v into the warp's table (lanes may insert concurrently).
+__device__ __forceinline__ void tab_insert(WarpTile &W, int v) {
+  int h = tab_slot(v);
+  for (int p = 0; p < 32; p++) {
+    int cur = ((volatile int *)W.hkey)[h];
+    if (cur == v) return;
+    if (cur == -1) {
+      cur = atomicCAS(&W.hkey[h], -1, v);
+      if (cur == -1) {
+        if (atomicAdd(&W.hcount, 1) >= kTileLabels) W.over = 1;
+        return;
+      }
+      if (cur == v) return;
+    }
+    h = (h + 1) & 31;
+  }
+  W.over = 1;
+}
+
+// 1 when label k may have changed since the previous scan (labels not in the table count
+// as changed).
+__device__ __forceinline__ bool win_label_changed(const WarpTile &W, int k) {
+  int h = tab_slot(k);
+  for (int p = 0; p < 32; p++) {
+    const int cur = W.hkey[h];
+    if (cur == k) return W.hval[h] != 0;
+    if (cur == -1) return true;
+    h = (h + 1) & 31;
+  }
+  return true;
+}
+
+// Decide a block: the target label, or -1 for no decrease (Eq. operation; ties to the
+// smaller label, a move only on a strict decrease).  The candidates are visited once,
+// keeping the best one's interval, the smallest lower bound among the others and the
+// largest magnitude seen.
+__device__ __forceinline__ int decide(const StageArgs &a, const BlockIn &in, Local &lc) {
+  if (!a.use_filter) return decide_f64(a, in);
+  const DevStats &s = a.st;
+  const BlockSums &bs = in.bs;
+  const int lbl = in.lbl;
+  const float wf = (float)bs.w;  // exact: blocks have < 2^24 pixels when the filter is on
+  const float r2f = (float)(2 * bs.r), g2f = (float)(2 * bs.g), b2f = (float)(2 * bs.b);
+  const float x2f = (float)(2 * bs.x), y2f = (float)(2 * bs.y);
+  const float pbx = (float)in.x0 + 0.5f * (float)(bs.bw - 1);  // P_x / w, exact
+  const float pby = (float)in.y0 + 0.5f * (float)(bs.bh - 1);
+  const float lamf = a.lam_pos_f, lamb2f = a.lam_b2_f;
+  const float rlam = 1.0001f * kU * lamf, rlamb = 1.0001f * kU * lamb2f;  // |float - binary64| weights
+  const float4 ha = s.fhi[lbl], la = s.flo[lbl];
+  const float2 ya = s.fy[lbl];
+  int Ba = 0;
+  if (in.nb[0] >= 0 && in.nb[0] != lbl) Ba += bs.bw;
+  if (in.nb[1] >= 0 && in.nb[1] != lbl) Ba += bs.bh;
+  if (in.nb[2] >= 0 && in.nb[2] != lbl) Ba += bs.bh;
+  if (in.nb[3] >= 0 && in.nb[3] != lbl) Ba += bs.bw;
+  const float eps_a = eps64(ha, ya, wf, r2f, g2f, b2f, x2f, y2f, lamf, lamb2f, (float)Ba);
+
+  int bk = -1;
+  float bD = 0.f, bLo = 0.f, bHi = 0.f;
+  float minLoOther = INFINITY, minLoAll = INFINITY, maxAbs = 0.f;
+#pragma unroll 1
+  for (int j = 0; j < 4; j++) {
+    const int k = in.nb[j];
+    if (k < 0 || k == lbl) continue;
+    bool dup = false;
+    for (int i = 0; i < j; i++) dup |= (in.nb[i] == k);
+    if (dup) continue;
+    int Bk = 0;
+    if (in.nb[0] >= 0 && in.nb[0] != k) Bk += bs.bw;
+    if (in.nb[1] >= 0 && in.nb[1] != k) Bk += bs.bh;
+    if (in.nb[2] >= 0 && in.nb[2] != k) Bk += bs.bh;
+    if (in.nb[3] >= 0 && in.nb[3] != k) Bk += bs.bw;
+    const float4 hk = s.fhi[k], lk = s.flo[k];
+    const float2 yk = s.fy[k];
+    const Fr col = add_fr(add_fr(colour_term(hk.x, lk.x, ha.x, la.x, wf, r2f, kU * r2f),
+                                 colour_term(hk.y, lk.y, ha.y, la.y, wf, g2f, kU * g2f)),
+                          colour_term(hk.z, lk.z, ha.z, la.z, wf, b2f, kU * b2f));
+    const Fr pos =
+        add_fr(position_term(hk.w, lk.w, ha.w, la.w, pbx, wf), position_term(yk.x, yk.y, ya.x, ya.y, pby, wf));
+    const float lp = lamf * pos.v;
+    const Fr lpos = {lp, lamf * pos.r + fabsf(pos.v) * rlam + rlam * pos.r + kU * fabsf(lp)};
+    const float dB = (float)(Bk - Ba);  // exact small integer
+    const float bb = lamb2f * dB;
+    const Fr bnd = {bb, fabsf(dB) * rlamb + kU * fabsf(bb)};
+    const Fr d = add_fr(add_fr(col, lpos), bnd);
+    const float eps_k = eps64(hk, yk, wf, r2f, g2f, b2f, x2f, y2f, lamf, lamb2f, (float)Bk);
+    const float R = __fmul_ru(__fadd_ru(__fadd_ru(d.r, eps_k), eps_a), 1.01f);
+    const float lo = __fsub_rd(d.v, R), hi = __fadd_ru(d.v, R);
+    minLoAll = fminf(minLoAll, lo);
+    maxAbs = fmaxf(maxAbs, fmaxf(fabsf(lo), fabsf(hi)));
+    if (bk < 0 || d.v < bD || (d.v == bD && k < bk)) {
+      if (bk >= 0) minLoOther = fminf(minLoOther, bLo);
+      bk = k;
+      bD = d.v;
+      bLo = lo;
+      bHi = hi;
+    } else {
+      minLoOther = fminf(minLoOther, lo);
+    }
+  }
+  if (bk < 0) return -1;
+  int result = -2;  // undecided
+  if (minLoAll >= 0.f) {
+    result = -1;  // every binary64 difference is >= 0: no move
+  } else if (bHi < 0.f) {
+    // strict lead of the best candidate that survives the final binary64 rounding of the
+    // differences (margin 2^-50 of four times the largest magnitude)
+    const float thr = __fmul_ru(maxAbs, 3.5527137e-15f);
+    if (minLoOther == INFINITY || __fsub_rd(minLoOther, bHi) > thr) result = bk;
+  }
+  if (result == -2) {
+    lc.fallback++;
+    return decide_f64(a, in);
+  }
+  if (a.verify_filter) {
+    const int ref = decide_f64(a, in);
+    if (ref != result) {
+      lc.mismatch++;
+      return ref;
+    }
+  }
+  return result;
+}
+
+// ---------------------------------------------------------------- one block, two passes
+// Pass 1 (every phase-class block of the tile, one lane each): the cheap tests from the
+// shared window -- boundary (Eq. bound), boundary superpixel (Eq. new_bound), topology
+// (E_topo) -- and the counters.  Returns true when the block needs an energy decision: it
+// passed the tests and, when block_skip holds (the tile was scanned before in this phase
+// class and its label set is complete), its label or a neighbour label changed since, or
+// it requested a merge then.  Otherwise it decides as at the previous scan: no move.
+__device__ __forceinline__ bool block_needs_decision(const StageArgs &a, const WarpTile &W, int c, int j,
+                                                     bool block_skip, Local &lc) {
+  const int *win = W.win;
+  const int lbl = win[c];
+  const int nN = win[c - kWinW], nW = win[c - 1], nE = win[c + 1], nS = win[c + kWinW];
+  const bool boundary = (nN >= 0 && nN != lbl) || (nW >= 0 && nW != lbl) || (nE >= 0 && nE != lbl) ||
+                        (nS >= 0 && nS != lbl);
+  if (!boundary) return false;
+  const DevStats &s = a.st;
+  if (a.imp_on) {
+    if (a.imp_rule == 0) {
+      if (!s.imp[lbl]) return false;
+    } else {
+      const signed char ya = s.y[lbl];
+      const bool any = (nN >= 0 && nN != lbl && s.y[nN] != ya) || (nW >= 0 && nW != lbl && s.y[nW] != ya) ||
+                       (nE >= 0 && nE != lbl && s.y[nE] != ya) || (nS >= 0 && nS != lbl && s.y[nS] != ya);
+      if (!any) return false;
+    }
+  }
+  lc.elig++;
+  const int nNW = win[c - kWinW - 1], nNE = win[c - kWinW + 1], nSE = win[c + kWinW + 1], nSW = win[c + kWinW - 1];
+  const unsigned m = (unsigned)(nNW == lbl) | ((unsigned)(nN == lbl) << 1) | ((unsigned)(nNE == lbl) << 2) |
+                     ((unsigned)(nE == lbl) << 3) | ((unsigned)(nSE == lbl) << 4) | ((unsigned)(nS == lbl) << 5) |
+                     ((unsigned)(nSW == lbl) << 6) | ((unsigned)(nW == lbl) << 7);
+  if (!simple_mask(m)) return false;
+  lc.eval++;
+  if (block_skip && !((W.prevreq[j >> 5] >> (j & 31)) & 1u) && !win_label_changed(W, lbl) &&
+      (nN < 0 || !win_label_changed(W, nN)) && (nW < 0 || !win_label_changed(W, nW)) &&
+      (nE < 0 || !win_label_changed(W, nE)) && (nS < 0 || !win_label_changed(W, nS)))
+    return false;
+  return true;
+}
+
+// Pass 2 (one compacted block per lane): block sums, the decision (Eq. operation), the size
+// term (Sec. 3.1) and the move.
+__device__ __forceinline__ void decide_block(const StageArgs &a, WarpTile &W, int c, int j, int bx, int by, int g,
+                                             Local &lc) {
+  const int *win = W.win;
+  const DevStats &s = a.st;
+  BlockIn in;
+  in.lbl = win[c];
+  in.nb[0] = win[c - kWinW];
+  in.nb[1] = win[c - 1];
+  in.nb[2] = win[c + 1];
+  in.nb[3] = win[c + kWinW];
+  in.bs = block_sums(a, bx, by);
+  in.x0 = bx * a.side;
+  in.y0 = by * a.side;
+  const int lbl = in.lbl;
+  const int k = decide(a, in, lc);
+  if (k < 0) return;
+  const long long idx = (long long)by * a.nbx + bx;
+  if (a.size_mode != 0 && (long long)a.lo_den * (s.N[lbl] - in.bs.w) < (long long)a.lo_num * s.init[lbl]) {
+    if (a.size_mode == 2) {
+      lc.req++;
+      atomicOr(&W.req[j >> 5], 1u << (j & 31));
+      atomicMin(&a.mg.req_min[lbl], (int)idx);
+      if (atomicExch(&a.mg.req_flag[lbl], 1) == 0) {
+        const int slot = atomicAdd(a.mg.req_count + (g & 1), 1);
+        a.mg.req_list[slot] = lbl;
+      }
+    }
+    return;
+  }
+  // Move: relabel in place, accumulate the exact deltas of both labels.
+  const BlockSums &bs = in.bs;
+  a.lab[idx] = k;
+  atomic_add_i64(&s.dN[lbl], -bs.w);
+  atomic_add_i64(&s.dR[lbl], -bs.r);
+  atomic_add_i64(&s.dG[lbl], -bs.g);
+  atomic_add_i64(&s.dB[lbl], -bs.b);
+  atomic_add_i64(&s.dX[lbl], -bs.x);
+  atomic_add_i64(&s.dY[lbl], -bs.y);
+  atomic_add_i64(&s.dN[k], bs.w);
+  atomic_add_i64(&s.dR[k], bs.r);
+  atomic_add_i64(&s.dG[k], bs.g);
+  atomic_add_i64(&s.dB[k], bs.b);
+  atomic_add_i64(&s.dX[k], bs.x);
+  atomic_add_i64(&s.dY[k], bs.y);
+  s.dirty[lbl] = 1;
+  s.dirty[k] = 1;
+  // the adjacency of the block's old and new labels and of its 4-neighbours' labels may
+  // have changed (every writer of this phase stores the same stamp)
+  s.adj[lbl] = 2 * g;
+  s.adj[k] = 2 * g;
+  for (int q = 0; q < 4; q++)
+    if (in.nb[q] >= 0) s.adj[in.nb[q]] = 2 * g;
+  atomicMin(&s.bbox[k].x, in.x0);
+  atomicMin(&s.bbox[k].y, in.y0);
+  atomicMax(&s.bbox[k].z, in.x0 + bs.bw - 1);
+  atomicMax(&s.bbox[k].w, in.y0 + bs.bh - 1);
+  lc.moves++;
+}
+
+__device__ inline int warp_sum(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Insert v into a shared append-only set of `cap` slots initialised to -1; sets *over when
+// the set is full.
+__device__ __forceinline__ void set_insert(int *set, int cap, int v, int *over) {
+  for (int j = 0; j < cap; j++) {
+    int cur = ((volatile int *)set)[j];
+    if (cur == v) return;
+    if (cur == -1) {
+      cur = atomicCAS(&set[j], -1, v);
+      if (cur == -1 || cur == v) return;
+    }
+  }
+  *over = 1;
+}
+
+// ---------------------------------------------------------------- one phase
+// g: 1-based phase number within the launch.
+// CTA b owns the tiles b, b + grid, b + 2 grid, ... (spread over the image); its warps draw
+// them one at a time from a shared-memory counter, the next draw issued before the current
+// tile is processed.
+__device__ void eval_phase(const StageArgs &a, WarpTile *wts, int *s_draw, int phase, int g,
+                           unsigned long long *changes) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  WarpTile &W = wts[warp];
+  const int py = phase / 3, px = phase % 3;
+  const int ntiles = a.ntx * a.nty;
+  if (threadIdx.x == 0) *s_draw = 0;
+  __syncthreads();
+  int draw = 0;
+  if (lane == 0) draw = atomicAdd(s_draw, 1);
+  draw = __shfl_sync(0xffffffffu, draw, 0);
+  Local lc = {0, 0, 0, 0, 0, 0};
+  int scanned = 0, skipped = 0;
+  for (;;) {
+    const long long tt = (long long)blockIdx.x + (long long)draw * gridDim.x;
+    if (tt >= ntiles) break;
+    const int t = (int)tt;
+    int nxt = 0;
+    if (lane == 0) nxt = atomicAdd(s_draw, 1);
+    draw = __shfl_sync(0xffffffffu, nxt, 0);  // used by the next iteration
+    const int tx = t % a.ntx, ty = t / a.ntx;
+    const int bx0 = tx * kTileW, by0 = ty * kTileH;
+    int *rec = a.trec + ((long long)t * 9 + phase) * kRecInts;
+    const int rv = lane < kRecInts ? rec[lane] : 0;
+    const int stamp = __shfl_sync(0xffffffffu, rv, 0), nlab = __shfl_sync(0xffffffffu, rv, 1);
+    const unsigned pm0 = (unsigned)__shfl_sync(0xffffffffu, rv, 4 + kTileLabels);
+    const unsigned pm1 = (unsigned)__shfl_sync(0xffffffffu, rv, 5 + kTileLabels);
+    const unsigned pm2 = (unsigned)__shfl_sync(0xffffffffu, rv, 6 + kTileLabels);
+    const bool can = a.skip_tiles && stamp > 0 && nlab >= 0 && (pm0 | pm1 | pm2) == 0u;
+    const int myl = __shfl_sync(0xffffffffu, rv, (4 + lane) & 31);
+    const bool changed = __any_sync(0xffffffffu, can && lane < nlab && a.st.chg[myl] >= 2 * stamp);
+    if (can && !changed) {
+      const int re = __shfl_sync(0xffffffffu, rv, 2), rvv = __shfl_sync(0xffffffffu, rv, 3);
+      if (lane == 0) {
+        lc.elig += re;
+        lc.eval += rvv;
+        skipped++;
+      }
+      continue;
+    }
+    if (lane == 0) scanned++;
+    W.hkey[lane] = -1;
+    if (lane == 0) {
+      W.over = 0;
+      W.hcount = 0;
+      W.req[0] = W.req[1] = W.req[2] = 0u;
+      W.prevreq[0] = stamp > 0 ? pm0 : 0u;
+      W.prevreq[1] = stamp > 0 ? pm1 : 0u;
+      W.prevreq[2] = stamp > 0 ? pm2 : 0u;
+    }
+    __syncwarp();
+    // window: lane = column (lanes 0 and 1 also take columns 32 and 33); the label of each
+    // run of equal labels down a column goes into the table
+    for (int col = lane; col < kWinW; col += 32) {
+      const int gx = bx0 - 1 + col;
+      const bool inx = gx >= 0 && gx < a.nbx;
+      int vals[kWinH];
+#pragma unroll
+      for (int wy = 0; wy < kWinH; wy++) {
+        const int gy = by0 - 1 + wy;
+        vals[wy] = (inx && gy >= 0 && gy < a.nby) ? a.lab[(long long)gy * a.nbx + gx] : -1;
+      }
+      int prev = -2;
+#pragma unroll
+      for (int wy = 0; wy < kWinH; wy++) {
+        const int v = vals[wy];
+        W.win[wy * kWinW + col] = v;
+        if (v != prev && v >= 0) tab_insert(W, v);
+        prev = v;
+      }
+    }
+    // the tile's blocks of this phase class
+    const int lx0 = ((px - bx0) % 3 + 3) % 3, ly0 = ((py - by0) % 3 + 3) % 3;
+    const int tw = min(kTileW, a.nbx - bx0), th = min(kTileH, a.nby - by0);
+    const int nx = tw > lx0 ? (tw - lx0 + 2) / 3 : 0, ny = th > ly0 ? (th - ly0 + 2) / 3 : 0;
+    __syncwarp();
+    // which of the window's labels changed since the previous scan of this tile and class
+    const int key = W.hkey[lane];
+    W.hval[lane] = (key >= 0 && stamp > 0) ? (a.st.chg[key] >= 2 * stamp) : 1;
+    __syncwarp();
+    const bool block_skip = a.skip_tiles && stamp > 0 && !W.over;
+    const int e0 = lc.elig, v0 = lc.eval;
+    // pass 1: tests; the blocks that need a decision are compacted into W.items
+    int nitems = 0;
+    for (int j0 = 0; j0 < nx * ny; j0 += 32) {
+      const int j = j0 + lane;
+      bool need = false;
+      if (j < nx * ny) {
+        const int lx = lx0 + 3 * (j % nx), ly = ly0 + 3 * (j / nx);
+        need = block_needs_decision(a, W, (ly + 1) * kWinW + (lx + 1), j, block_skip, lc);
+      }
+      const unsigned ball = __ballot_sync(0xffffffffu, need);
+      if (need) W.items[nitems + __popc(ball & ((1u << lane) - 1u))] = j;
+      nitems += __popc(ball);
+    }
+    __syncwarp();
+    // pass 2: decisions, one compacted block per lane
+    for (int it = lane; it < nitems; it += 32) {
+      const int j = W.items[it];
+      const int lx = lx0 + 3 * (j % nx), ly = ly0 + 3 * (j / nx);
+      decide_block(a, W, (ly + 1) * kWinW + (lx + 1), j, bx0 + lx, by0 + ly, g, lc);
+    }
+    const int de = warp_sum(lc.elig - e0), dv = warp_sum(lc.eval - v0);
+    __syncwarp();
+    // record: the table's labels (when at most kTileLabels), counts, request mask
+    const unsigned present = __ballot_sync(0xffffffffu, key >= 0);
+    const int pos = __popc(present & ((1u << lane) - 1u));
+    if (key >= 0 && pos < kTileLabels) rec[4 + pos] = key;
+    if (lane == 0) {
+      rec[0] = g;
+      rec[2] = (int)de;
+      rec[3] = (int)dv;
+      rec[1] = W.over ? -1 : __popc(present);
+      rec[4 + kTileLabels] = (int)W.req[0];
+      rec[5 + kTileLabels] = (int)W.req[1];
+      rec[6 + kTileLabels] = (int)W.req[2];
+    }
+    __syncwarp();
+  }
+  const int e = warp_sum(lc.elig), v = warp_sum(lc.eval), m = warp_sum(lc.moves), r = warp_sum(lc.req);
+  const int fb = warp_sum(lc.fallback), mm = warp_sum(lc.mismatch);
+  const int sc = warp_sum(scanned), sk = warp_sum(skipped);
+
+  if (lane == 0) {
+    if (e) atomic_add_i64(&a.ctl.cnt[CNT_ELIG], e);
+    if (v) atomic_add_i64(&a.ctl.cnt[CNT_EVAL], v);
+    if (m) {
+      atomic_add_i64(&a.ctl.cnt[CNT_MOVES], m);
+      atomicAdd(changes, (unsigned long long)m);
+    }
+    if (r) atomic_add_i64(&a.ctl.cnt[CNT_REQ], r);
+    if (fb) atomic_add_i64(&a.ctl.cnt[CNT_FALLBACK], fb);
+    if (mm) atomic_add_i64(&a.ctl.cnt[CNT_MISMATCH], mm);
+    if (sc) atomic_add_i64(&a.ctl.cnt[CNT_SCANNED], sc);
+    if (sk) atomic_add_i64(&a.ctl.cnt[CNT_SKIPPED], sk);
+  }
+}

@@ -230,3 +230,57 @@ cudaError_t launch_simple_table(unsigned char *out, cudaStream_t s) {
 }
 
 }  // namespace rapid
+
+namespace rapid {
+
+// Per-label arrays, each in its own 256-byte aligned piece.
+static size_t carve_impl(char *base, size_t cap, int M, DevStats *st, DevMerge *mg) {
+  const size_t m = (size_t)M;
+  size_t used = 0;
+  bool ok = true;
+  auto take = [&](size_t n) -> void * {
+    n = (n + 255) / 256 * 256;
+    if (used + n > cap) {
+      ok = false;
+      return nullptr;
+    }
+    void *r = base ? base + used : nullptr;
+    used += n;
+    return r;
+  };
+  long long **i64[] = {&st->N, &st->R, &st->G, &st->B, &st->X, &st->Y, &st->init,
+                       &st->dN, &st->dR, &st->dG, &st->dB, &st->dX, &st->dY};
+  for (long long **q : i64) *q = (long long *)take(m * 8);
+  double **f64[] = {&st->mR, &st->mG, &st->mB, &st->mX, &st->mY};
+  for (double **q : f64) *q = (double *)take(m * 8);
+  st->fhi = (float4 *)take(m * 16);
+  st->flo = (float4 *)take(m * 16);
+  st->fy = (float2 *)take(m * 8);
+  st->bbox = (int4 *)take(m * 16);
+  st->chg = (int *)take(m * 4);
+  st->adj = (int *)take(m * 4);
+  mg->acc = (int2 *)take(m * 8);
+  int **i32[] = {&mg->req_list, &mg->req_min, &mg->req_flag, &mg->target, &mg->order, &mg->cache_stamp, &mg->cache_n};
+  for (int **q : i32) *q = (int *)take(m * 4);
+  mg->cache_nb = (int *)take(m * 4 * kCacheLabels);
+  mg->found = (int *)take(m * 4);
+
+  st->dirty = (unsigned char *)take(m);
+  st->y = (signed char *)take(m);
+  st->imp = (unsigned char *)take(m);
+  mg->involved = (unsigned char *)take(m);
+  st->M = M;
+  return ok ? used : 0;
+}
+
+size_t label_arrays_bytes(int M) {
+  DevStats st;
+  DevMerge mg;
+  return carve_impl(nullptr, (size_t)-1, M, &st, &mg);
+}
+
+size_t carve_label_arrays(void *base, size_t cap, int M, DevStats *st, DevMerge *mg) {
+  return carve_impl((char *)base, cap, M, st, mg);
+}
+
+}  // namespace rapid

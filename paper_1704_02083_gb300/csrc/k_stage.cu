@@ -9,82 +9,74 @@
 // in place and accumulate exact int64 deltas that are folded into S after the phase.
 // Merge requests of the phase (size bound hit, Sec. 3.1) are then resolved against the
 // post-move state.
+//
+// Work layout: a CTA takes 64 x 32-block tiles, stages the tile's labels (with a 1-block
+// halo) in shared memory and gives each thread one block of the phase class.  A tile is
+// skipped when no label present in it has changed since its last scan in this phase class
+// and that scan issued no merge request: its blocks would decide exactly as before (no
+// move), so the recorded counts are replayed instead.
+//
+// Decisions: the energy difference of each candidate label k against the block's label a
+// is first computed in single precision in the well-conditioned form
+//   dE_k = sum_ch (c_k - c_a)(w (c_k + c_a) - 2 S_ch)
+//          + lambda_pos w sum_d (mu_k - mu_a)((mu_k - pbar_d) + (mu_a - pbar_d))
+//          + 2 lambda_b (B_k - B_a)          (pbar = block centre = P / w)
+// (algebraically e(k) - e(a) of the binary64 block energy) together with a rigorous bound
+// on its rounding error, widened by the rounding error of the binary64 evaluation itself.
+// When the resulting intervals fix the sign of the best candidate and its strict lead over
+// the others, that is exactly the binary64 decision; otherwise the block is decided in
+// binary64 with the oracle's operation order.  Results are bit-identical to an
+// all-binary64 evaluation.
 #include <climits>
 
 #include "rapid_dev.cuh"
 
 namespace rapid {
 
-static constexpr int kThreads = 256;
+static constexpr int kThreads = 1024;
+static_assert((kThreads & (kThreads - 1)) == 0, "block reductions assume a power-of-two CTA size");
+
+static constexpr int kMergeSet = 64;
 
 struct Local {
-  long long elig, eval, moves, req;
+  int elig, eval, moves, req, fallback, mismatch;  // per thread and phase: fit in 32 bits
+
 };
 
-// Decide one block (Eq. bound, E_topo, Eq. operation, size term) and apply its move.
-__device__ __forceinline__ void eval_block(const StageArgs &a, int bx, int by, Local &lc,
-                                           unsigned long long *changes) {
-  const int nbx = a.nbx, nby = a.nby;
-  const int *L = a.lab;
-  const long long idx = (long long)by * nbx + bx;
-  const int lbl = L[idx];
-  const bool hasN = by > 0, hasS = by + 1 < nby, hasW = bx > 0, hasE = bx + 1 < nbx;
-  const int nN = hasN ? L[idx - nbx] : -1;
-  const int nW = hasW ? L[idx - 1] : -1;
-  const int nE = hasE ? L[idx + 1] : -1;
-  const int nS = hasS ? L[idx + nbx] : -1;
-  const bool boundary = (nN >= 0 && nN != lbl) || (nW >= 0 && nW != lbl) || (nE >= 0 && nE != lbl) ||
-                        (nS >= 0 && nS != lbl);
-  if (!boundary) return;
-  if (a.imp_on) {
-    if (a.imp_rule == 0) {
-      if (!a.st.imp[lbl]) return;
-    } else {
-      const signed char ya = a.st.y[lbl];
-      bool any = (nN >= 0 && nN != lbl && a.st.y[nN] != ya) || (nW >= 0 && nW != lbl && a.st.y[nW] != ya) ||
-                 (nE >= 0 && nE != lbl && a.st.y[nE] != ya) || (nS >= 0 && nS != lbl && a.st.y[nS] != ya);
-      if (!any) return;
-    }
-  }
-  lc.elig++;
-  const int nNW = (hasN && hasW) ? L[idx - nbx - 1] : -1;
-  const int nNE = (hasN && hasE) ? L[idx - nbx + 1] : -1;
-  const int nSE = (hasS && hasE) ? L[idx + nbx + 1] : -1;
-  const int nSW = (hasS && hasW) ? L[idx + nbx - 1] : -1;
-  unsigned m = (unsigned)(nNW == lbl) | ((unsigned)(nN == lbl) << 1) | ((unsigned)(nNE == lbl) << 2) |
-               ((unsigned)(nE == lbl) << 3) | ((unsigned)(nSE == lbl) << 4) | ((unsigned)(nS == lbl) << 5) |
-               ((unsigned)(nSW == lbl) << 6) | ((unsigned)(nW == lbl) << 7);
-  if (!simple_mask(m)) return;
-  lc.eval++;
+struct BlockIn {
+  BlockSums bs;
+  int x0, y0;  // block origin (full-res px)
+  int lbl;
+  int nb[4];   // N, W, E, S neighbour labels (-1 outside the grid)
+};
 
-  const BlockSums bs = block_sums(a, bx, by);
+// ---------------------------------------------------------------- binary64 decision
+// Exactly the oracle's evaluation: e(a), then e(k) - e(a) per distinct neighbour label,
+// least value (ties to the smaller label).  Returns the best label or -1 (no decrease).
+__device__ __noinline__ int decide_f64(const StageArgs &a, const BlockIn &in) {
+  const DevStats &s = a.st;
+  const BlockSums &bs = in.bs;
   const double w = __ll2double_rn(bs.w);
   const double r2 = __ll2double_rn(2 * bs.r), g2 = __ll2double_rn(2 * bs.g), b2 = __ll2double_rn(2 * bs.b);
   const double x2 = __ll2double_rn(2 * bs.x), y2 = __ll2double_rn(2 * bs.y);
-  const int nb[4] = {nN, nW, nE, nS};
   const int len[4] = {bs.bw, bs.bh, bs.bh, bs.bw};
-  const DevStats &s = a.st;
-
+  const int lbl = in.lbl;
   long long Ba = 0;
-#pragma unroll
   for (int j = 0; j < 4; j++)
-    if (nb[j] >= 0 && nb[j] != lbl) Ba += len[j];
+    if (in.nb[j] >= 0 && in.nb[j] != lbl) Ba += len[j];
   const double ea = blk_energy(w, r2, g2, b2, x2, y2, s.mR[lbl], s.mG[lbl], s.mB[lbl], s.mX[lbl], s.mY[lbl],
                                __ll2double_rn(Ba), a.lam_pos, a.lam_b2);
   int bestk = -1;
   double best = 0.0;
-#pragma unroll
   for (int j = 0; j < 4; j++) {
-    const int k = nb[j];
+    const int k = in.nb[j];
     if (k < 0 || k == lbl) continue;
     bool dup = false;
-#pragma unroll
-    for (int i = 0; i < j; i++) dup |= (nb[i] == k);
+    for (int i = 0; i < j; i++) dup |= (in.nb[i] == k);
     if (dup) continue;
     long long Bk = 0;
-#pragma unroll
     for (int i = 0; i < 4; i++)
-      if (nb[i] >= 0 && nb[i] != k) Bk += len[i];
+      if (in.nb[i] >= 0 && in.nb[i] != k) Bk += len[i];
     const double ek = blk_energy(w, r2, g2, b2, x2, y2, s.mR[k], s.mG[k], s.mB[k], s.mX[k], s.mY[k],
                                  __ll2double_rn(Bk), a.lam_pos, a.lam_b2);
     const double dE = __dsub_rn(ek, ea);
@@ -93,78 +85,77 @@ __device__ __forceinline__ void eval_block(const StageArgs &a, int bx, int by, L
       bestk = k;
     }
   }
-  if (bestk < 0 || !(best < 0.0)) return;
-  if (a.size_mode != 0 && (long long)a.lo_den * (s.N[lbl] - bs.w) < (long long)a.lo_num * s.init[lbl]) {
-    if (a.size_mode == 2) {
-      lc.req++;
-      atomicMin(&a.mg.req_min[lbl], (int)idx);
-      if (atomicExch(&a.mg.req_flag[lbl], 1) == 0) {
-        const int slot = atomicAdd(a.mg.req_count, 1);
-        a.mg.req_list[slot] = lbl;
-      }
-    }
-    return;
-  }
-  // Move: relabel in place, accumulate the exact deltas of both labels.
-  a.lab[idx] = bestk;
-  atomic_add_i64(&s.dN[lbl], -bs.w);
-  atomic_add_i64(&s.dR[lbl], -bs.r);
-  atomic_add_i64(&s.dG[lbl], -bs.g);
-  atomic_add_i64(&s.dB[lbl], -bs.b);
-  atomic_add_i64(&s.dX[lbl], -bs.x);
-  atomic_add_i64(&s.dY[lbl], -bs.y);
-  atomic_add_i64(&s.dN[bestk], bs.w);
-  atomic_add_i64(&s.dR[bestk], bs.r);
-  atomic_add_i64(&s.dG[bestk], bs.g);
-  atomic_add_i64(&s.dB[bestk], bs.b);
-  atomic_add_i64(&s.dX[bestk], bs.x);
-  atomic_add_i64(&s.dY[bestk], bs.y);
-  s.dirty[lbl] = 1;
-  s.dirty[bestk] = 1;
-  const int x0 = bx * a.side, y0 = by * a.side;
-  atomicMin(&s.bbox[bestk].x, x0);
-  atomicMin(&s.bbox[bestk].y, y0);
-  atomicMax(&s.bbox[bestk].z, x0 + bs.bw - 1);
-  atomicMax(&s.bbox[bestk].w, y0 + bs.bh - 1);
-  lc.moves++;
-  (void)changes;
+  return (bestk >= 0 && best < 0.0) ? bestk : -1;
 }
 
-__device__ inline long long warp_sum(long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
+// ---------------------------------------------------------------- single-precision filter
+// Running error analysis: each quantity carries a radius r with |computed - exact| <= r,
+// "exact" being real arithmetic on the binary64 snapshot means.  kU = 2^-24 is the unit
+// roundoff of float; kSplit = 2^-46 bounds |c - (hi + lo)| / |hi| for the hi/lo split of a
+// binary64 mean (|c - hi - lo| <= 2^-48 |c|).  The radius arithmetic itself is evaluated in
+// float; its own relative rounding (< 40 operations of 2^-24) is covered by the final 1%
+// widening.
+static constexpr float kU = 5.9604645e-08f;
+static constexpr float kSplit = 1.4210855e-14f;
+
+struct Fr {
+  float v, r;
+};
+
+__device__ __forceinline__ Fr diff_hl(float hk, float lk, float ha, float la) {
+  const float d1 = hk - ha, d2 = lk - la, d = d1 + d2;
+  return {d, kU * (fabsf(d1) + fabsf(d2) + fabsf(d)) + kSplit * (fabsf(hk) + fabsf(ha))};
 }
 
-__device__ void eval_phase(const StageArgs &a, int phase, unsigned long long *changes) {
-  const int py = phase / 3, px = phase % 3;
-  Local lc = {0, 0, 0, 0};
-  if (a.nbx > px && a.nby > py) {
-    const long long nphx = (a.nbx - px + 2) / 3, nphy = (a.nby - py + 2) / 3;
-    const long long total = nphx * nphy;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-      const int bx = px + 3 * (int)(i % nphx);
-      const int by = py + 3 * (int)(i / nphx);
-      eval_block(a, bx, by, lc, changes);
-    }
-  }
-  const long long e = warp_sum(lc.elig), v = warp_sum(lc.eval), m = warp_sum(lc.moves), r = warp_sum(lc.req);
-  if ((threadIdx.x & 31) == 0) {
-    if (e) atomic_add_i64(&a.ctl.cnt[CNT_ELIG], e);
-    if (v) atomic_add_i64(&a.ctl.cnt[CNT_EVAL], v);
-    if (m) {
-      atomic_add_i64(&a.ctl.cnt[CNT_MOVES], m);
-      atomicAdd(changes, (unsigned long long)m);
-    }
-    if (r) atomic_add_i64(&a.ctl.cnt[CNT_REQ], r);
-  }
+// (c_k - c_a)(w (c_k + c_a) - 2 S) for one colour channel.  s2f = float(2 S), rs2 = its error.
+__device__ __forceinline__ Fr colour_term(float hk, float lk, float ha, float la, float wf, float s2f, float rs2) {
+  const Fr d = diff_hl(hk, lk, ha, la);
+  const float s1 = hk + ha, s2 = lk + la, sm = s1 + s2;
+  const float rs = kU * (fabsf(s1) + fabsf(s2) + fabsf(sm)) + kSplit * (fabsf(hk) + fabsf(ha));
+  const float ws = wf * sm;
+  const float rws = wf * rs + kU * fabsf(ws);
+  const float m = ws - s2f;
+  const float rm = rws + rs2 + kU * fabsf(m);
+  const float t = d.v * m;
+  return {t, fabsf(d.v) * rm + fabsf(m) * d.r + d.r * rm + kU * fabsf(t)};
 }
 
-// Fold the phase's deltas into S and refresh the snapshot means of changed labels.
-__device__ void commit_phase(const StageArgs &a) {
+// w (mu_k - mu_a)((mu_k - pb) + (mu_a - pb)) for one position dimension; pb exact in float.
+__device__ __forceinline__ Fr position_term(float hk, float lk, float ha, float la, float pb, float wf) {
+  const Fr d = diff_hl(hk, lk, ha, la);
+  const float e1 = hk - pb, e2 = ha - pb, e12 = e1 + e2, l12 = lk + la, e = e12 + l12;
+  const float re =
+      kU * (fabsf(e1) + fabsf(e2) + fabsf(e12) + fabsf(l12) + fabsf(e)) + kSplit * (fabsf(hk) + fabsf(ha));
+  const float t = d.v * e;
+  const float rt = fabsf(d.v) * re + fabsf(e) * d.r + d.r * re + kU * fabsf(t);
+  const float tw = wf * t;
+  return {tw, wf * rt + kU * fabsf(tw)};
+}
+
+__device__ __forceinline__ Fr add_fr(Fr x, Fr y) {
+  const float v = x.v + y.v;
+  return {v, x.r + y.r + kU * fabsf(v)};
+}
+
+// Bound on |binary64 e(j) - exact e(j)|: at most 7 u64 times the sum of the absolute terms
+// of the energy (u64 = 2^-53; each term passes through at most 7 roundings), taken as
+// 16 u64 and widened 1% for the float evaluation of the sum.
+__device__ __forceinline__ float eps64(const float4 &h, const float2 &hy, float wf, float r2f, float g2f,
+                                       float b2f, float x2f, float y2f, float lamf, float lamb2f, float Bj) {
+  const float col = (wf * h.x * h.x + r2f * h.x) + (wf * h.y * h.y + g2f * h.y) + (wf * h.z * h.z + b2f * h.z);
+  const float pos = (wf * h.w * h.w + x2f * h.w) + (wf * hy.x * hy.x + y2f * hy.x);
+  const float T = col + lamf * pos + lamb2f * Bj;
+  return T * (1.7763568e-15f * 1.01f);
+}
+
+#include "eval_tile.cuh"
+
+// Fold the phase's deltas into S, refresh the snapshot means of changed labels and stamp
+// them (2g).
+__device__ void commit_phase(const StageArgs &a, int g) {
   const DevStats &s = a.st;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < s.M; k += gridDim.x * blockDim.x) {
+  // label k goes to CTA k % grid: the divisions of set_means spread over every SM
+  for (int k = blockIdx.x + gridDim.x * threadIdx.x; k < s.M; k += gridDim.x * blockDim.x) {
     if (!s.dirty[k]) continue;
     s.dirty[k] = 0;
     s.N[k] += s.dN[k];
@@ -175,36 +166,93 @@ __device__ void commit_phase(const StageArgs &a) {
     s.Y[k] += s.dY[k];
     s.dN[k] = s.dR[k] = s.dG[k] = s.dB[k] = s.dX[k] = s.dY[k] = 0;
     set_means(s, k);
+    s.chg[k] = 2 * g;
   }
 }
 
 // Merge targets (Eqs. eqa:merge, condtion), one CTA per requested label: over the labels
-// 4-adjacent to it (found by scanning its bounding box, which always contains it), the
-// least merge cost among those that stay within u * InitSize; ties to the smaller id.
-__device__ void merge_targets(const StageArgs &a, int rq) {
+// 4-adjacent to it (gathered by scanning its bounding box, which always contains it), the
+// least merge cost among those that stay within u * InitSize; ties to the smaller id.  A
+// search that found no target is remembered with its neighbour labels; while neither the
+// label nor any of them has changed since, the answer is the same and the scan is skipped.
+__device__ void merge_targets(const StageArgs &a, int rq, int g) {
   __shared__ double sw[kThreads];
   __shared__ int sn[kThreads];
+  __shared__ int nset[kMergeSet];
+  __shared__ int s_over, s_hit;
+  __shared__ int s_ext[4];
   const DevStats &s = a.st;
+  const DevMerge &mg = a.mg;
   for (int j = blockIdx.x; j < rq; j += gridDim.x) {
-    const int al = a.mg.req_list[j];
+    const int al = mg.req_list[j];
+    // A cached failure still holds when the neighbour set is provably the same (no move of
+    // or next to a block of al, no merge since) and every cached neighbour still fails the
+    // size condition with the current counts.
+    if (threadIdx.x < 32) {
+      const int cs = mg.cache_stamp[al], cn = mg.cache_n[al];
+      const bool can = cs > 0 && cn >= 0 && s.adj[al] <= cs && ld_volatile_i32(a.ctl.last_merge) <= cs;
+      bool fits = false;
+      if (can && (int)threadIdx.x < cn) {
+        const int n = mg.cache_nb[(long long)al * kCacheLabels + threadIdx.x];
+        fits = (long long)a.hi_den * (s.N[n] + s.N[al]) <= (long long)a.hi_num * s.init[n];
+      }
+      fits = __any_sync(0xffffffffu, fits);
+      if (threadIdx.x == 0) {
+        s_hit = can && !fits;
+        atomic_add_i64(&a.ctl.cnt[s_hit ? CNT_CACHE_HITS : CNT_SEARCHES], 1);
+        s_over = 0;
+        s_ext[0] = s_ext[1] = INT_MAX;
+        s_ext[2] = s_ext[3] = -1;
+      }
+    }
+    if (threadIdx.x < kMergeSet) nset[threadIdx.x] = -1;
+    __syncthreads();
+    if (s_hit) {
+      if (threadIdx.x == 0) {  // no target: the request is finished here
+        mg.target[al] = -1;
+        mg.req_flag[al] = 0;
+        mg.req_min[al] = INT_MAX;
+      }
+      __syncthreads();
+      continue;
+    }
+    // gather the distinct neighbour labels of al, and its exact extent (which replaces the
+    // conservative bounding box: later moves only widen it again)
     const int4 bb = s.bbox[al];
     const int bx0 = bb.x / a.side, bx1 = bb.z / a.side, by0 = bb.y / a.side, by1 = bb.w / a.side;
     const int bw = bx1 - bx0 + 1;
     const long long total = (long long)bw * (by1 - by0 + 1);
-    double best = 0.0;
-    int bestn = INT_MAX;
+    int mnx = INT_MAX, mny = INT_MAX, mxx = -1, mxy = -1;
     for (long long t = threadIdx.x; t < total; t += blockDim.x) {
       const int cx = bx0 + (int)(t % bw), cy = by0 + (int)(t / bw);
       const long long idx = (long long)cy * a.nbx + cx;
       if (a.lab[idx] != al) continue;
-      int nbv[4];
-      nbv[0] = cy > 0 ? a.lab[idx - a.nbx] : -1;
-      nbv[1] = cx > 0 ? a.lab[idx - 1] : -1;
-      nbv[2] = cx + 1 < a.nbx ? a.lab[idx + 1] : -1;
-      nbv[3] = cy + 1 < a.nby ? a.lab[idx + a.nbx] : -1;
-      for (int q = 0; q < 4; q++) {
-        const int n = nbv[q];
-        if (n < 0 || n == al) continue;
+      mnx = min(mnx, cx);
+      mxx = max(mxx, cx);
+      mny = min(mny, cy);
+      mxy = max(mxy, cy);
+      const int q[4] = {cy > 0 ? a.lab[idx - a.nbx] : -1, cx > 0 ? a.lab[idx - 1] : -1,
+                        cx + 1 < a.nbx ? a.lab[idx + 1] : -1, cy + 1 < a.nby ? a.lab[idx + a.nbx] : -1};
+      for (int i = 0; i < 4; i++)
+        if (q[i] >= 0 && q[i] != al) set_insert(nset, kMergeSet, q[i], &s_over);
+    }
+    if (mxx >= 0) {
+      atomicMin(&s_ext[0], mnx);
+      atomicMin(&s_ext[1], mny);
+      atomicMax(&s_ext[2], mxx);
+      atomicMax(&s_ext[3], mxy);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_ext[2] >= 0) {
+      s.bbox[al] = make_int4(s_ext[0] * a.side, s_ext[1] * a.side, min((s_ext[2] + 1) * a.side, a.W) - 1,
+                             min((s_ext[3] + 1) * a.side, a.H) - 1);
+    }
+    double best = 0.0;
+    int bestn = INT_MAX;
+    if (!s_over) {
+      for (int i = threadIdx.x; i < kMergeSet; i += blockDim.x) {
+        const int n = nset[i];
+        if (n < 0) continue;
         if ((long long)a.hi_den * (s.N[n] + s.N[al]) > (long long)a.hi_num * s.init[n]) continue;
         const double wv = ward_cost(s, al, n, a.lam_pos);
         if (bestn == INT_MAX || wv < best || (wv == best && n < bestn)) {
@@ -212,12 +260,30 @@ __device__ void merge_targets(const StageArgs &a, int rq) {
           bestn = n;
         }
       }
+    } else {  // more neighbours than the set holds: evaluate every adjacency directly
+      for (long long t = threadIdx.x; t < total; t += blockDim.x) {
+        const int cx = bx0 + (int)(t % bw), cy = by0 + (int)(t / bw);
+        const long long idx = (long long)cy * a.nbx + cx;
+        if (a.lab[idx] != al) continue;
+        const int q[4] = {cy > 0 ? a.lab[idx - a.nbx] : -1, cx > 0 ? a.lab[idx - 1] : -1,
+                          cx + 1 < a.nbx ? a.lab[idx + 1] : -1, cy + 1 < a.nby ? a.lab[idx + a.nbx] : -1};
+        for (int i = 0; i < 4; i++) {
+          const int n = q[i];
+          if (n < 0 || n == al) continue;
+          if ((long long)a.hi_den * (s.N[n] + s.N[al]) > (long long)a.hi_num * s.init[n]) continue;
+          const double wv = ward_cost(s, al, n, a.lam_pos);
+          if (bestn == INT_MAX || wv < best || (wv == best && n < bestn)) {
+            best = wv;
+            bestn = n;
+          }
+        }
+      }
     }
     sw[threadIdx.x] = best;
     sn[threadIdx.x] = bestn;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) {
+      if ((int)threadIdx.x < o) {
         const double w2 = sw[threadIdx.x + o];
         const int n2 = sn[threadIdx.x + o];
         const int n1 = sn[threadIdx.x];
@@ -228,33 +294,116 @@ __device__ void merge_targets(const StageArgs &a, int rq) {
       }
       __syncthreads();
     }
-    if (threadIdx.x == 0) a.mg.target[al] = sn[0] == INT_MAX ? -1 : sn[0];
+    if (threadIdx.x == 0) {
+      const int tgt = sn[0] == INT_MAX ? -1 : sn[0];
+      mg.target[al] = tgt;
+      if (tgt >= 0) {  // goes on to the acceptance walk
+        mg.found[atomicAdd(mg.found_count + (g & 1), 1)] = al;
+      } else {  // no target: the request is finished here
+        mg.req_flag[al] = 0;
+        mg.req_min[al] = INT_MAX;
+      }
+      if (tgt < 0) {  // remember the failure with its neighbour set
+        int n = 0;
+        while (!s_over && n < kMergeSet && nset[n] >= 0) n++;
+        if (!s_over && n <= kCacheLabels) {
+          for (int i = 0; i < n; i++) mg.cache_nb[(long long)al * kCacheLabels + i] = nset[i];
+          mg.cache_n[al] = n;
+          mg.cache_stamp[al] = 2 * g;
+        } else {
+          mg.cache_n[al] = -1;
+        }
+      }
+    }
     __syncthreads();
   }
 }
 
-// Accept requests in ascending order of their first requesting block; skip those whose
-// source or target already merged in this phase; fold S.  Runs on CTA 0 only.
-__device__ void merge_accept(const StageArgs &a, int rq, unsigned long long *changes) {
-  const DevStats &s = a.st;
-  const DevMerge &g = a.mg;
-  for (int j = threadIdx.x; j < rq; j += blockDim.x) {
-    const int key = g.req_min[g.req_list[j]];
-    int rank = 0;
-    for (int i = 0; i < rq; i++) rank += g.req_min[g.req_list[i]] < key;
-    g.order[rank] = g.req_list[j];
+// Acceptance of the requests whose search found a target (Sec. 3.1): in ascending order of
+// their first requesting block, skipping those whose source or target already merged in
+// this phase.  With up to kAcceptSmem such requests every CTA runs the same (cheap) walk in
+// shared memory, so each knows the accepted list without another grid barrier; above that
+// CTA 0 walks in global memory and the grid waits once more.  CTA b then applies merges
+// b, b + grid, ...: S_n += S_a, S_a = 0, stamps, bounding box, and relabels a -> n over a's
+// bounding box.  No two accepted merges share a label, so they apply independently.
+static constexpr int kAcceptSmem = 512;
+
+// Walk of up to kAcceptSmem found requests in shared memory; returns the accepted count.
+__device__ int merge_walk_small(const StageArgs &a, int nf, int2 *s_acc) {
+  __shared__ int s_key[kAcceptSmem], s_lab[kAcceptSmem], s_tgt[kAcceptSmem], s_ord[kAcceptSmem];
+  __shared__ int s_nacc;
+  const DevMerge &mg = a.mg;
+  for (int j = threadIdx.x; j < nf; j += blockDim.x) {
+    const int al = mg.found[j];
+    s_lab[j] = al;
+    s_key[j] = mg.req_min[al];
+    s_tgt[j] = mg.target[al];
   }
   __syncthreads();
-  __threadfence_block();
+  for (int j = threadIdx.x; j < nf; j += blockDim.x) {
+    const int key = s_key[j];
+    int rank = 0;
+    for (int i = 0; i < nf; i++) rank += s_key[i] < key;  // keys are distinct block indices
+    s_ord[rank] = j;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int acc = 0;
-    for (int r = 0; r < rq; r++) {
-      const int al = g.order[r];
-      const int n = g.target[al];
-      if (n < 0 || g.involved[al] || g.involved[n]) continue;
-      g.involved[al] = 1;
-      g.involved[n] = 1;
-      g.acc[acc++] = make_int2(al, n);
+    for (int r = 0; r < nf; r++) {
+      const int j = s_ord[r];
+      const int al = s_lab[j], n = s_tgt[j];
+      bool inv = false;
+      for (int i = 0; i < acc; i++) {
+        const int2 q = s_acc[i];
+        inv |= (q.x == al) | (q.y == al) | (q.x == n) | (q.y == n);
+      }
+      if (!inv) s_acc[acc++] = make_int2(al, n);
+    }
+    s_nacc = acc;
+  }
+  __syncthreads();
+  return s_nacc;
+}
+
+// The same walk for any number of found requests, on CTA 0, in global memory (mg.order,
+// mg.involved, mg.acc, *mg.acc_count).
+__device__ void merge_walk_big(const StageArgs &a, int nf) {
+  const DevMerge &mg = a.mg;
+  for (int j = threadIdx.x; j < nf; j += blockDim.x) {
+    const int key = mg.req_min[mg.found[j]];
+    int rank = 0;
+    for (int i = 0; i < nf; i++) rank += mg.req_min[mg.found[i]] < key;
+    mg.order[rank] = mg.found[j];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int r = 0; r < nf; r++) {
+      const int al = mg.order[r], n = mg.target[al];
+      if (mg.involved[al] || mg.involved[n]) continue;
+      mg.involved[al] = 1;
+      mg.involved[n] = 1;
+      mg.acc[acc++] = make_int2(al, n);
+    }
+    *mg.acc_count = acc;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < *(volatile int *)mg.acc_count; j += blockDim.x) {
+    const int2 p = mg.acc[j];
+    mg.involved[p.x] = 0;
+    mg.involved[p.y] = 0;
+  }
+}
+
+// Apply accepted merges (list in shared or global memory) and finish every found request.
+__device__ void merge_apply(const StageArgs &a, const int2 *acc, int nacc, int nf, int g,
+                            unsigned long long *changes) {
+  const DevStats &s = a.st;
+  const DevMerge &mg = a.mg;
+  for (int j = blockIdx.x; j < nacc; j += gridDim.x) {
+    const int al = acc[j].x, n = acc[j].y;
+    const int4 ba = s.bbox[al];
+    if (threadIdx.x == 0) {
       s.N[n] += s.N[al];
       s.R[n] += s.R[al];
       s.G[n] += s.G[al];
@@ -264,48 +413,33 @@ __device__ void merge_accept(const StageArgs &a, int rq, unsigned long long *cha
       s.N[al] = s.R[al] = s.G[al] = s.B[al] = s.X[al] = s.Y[al] = 0;
       set_means(s, n);
       set_means(s, al);
+      s.chg[n] = 2 * g + 1;
+      s.chg[al] = 2 * g + 1;
+      *a.ctl.last_merge = 2 * g + 1;
       int4 bn = s.bbox[n];
-      const int4 ba = s.bbox[al];
       bn.x = min(bn.x, ba.x);
       bn.y = min(bn.y, ba.y);
       bn.z = max(bn.z, ba.z);
       bn.w = max(bn.w, ba.w);
       s.bbox[n] = bn;
     }
-    *g.acc_count = acc;
-    *g.req_count = 0;
-    if (acc) {
-      a.ctl.cnt[CNT_MERGES] += acc;
-      *changes += (unsigned long long)acc;
-    }
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < rq; j += blockDim.x) {
-    const int al = g.req_list[j];
-    g.req_flag[al] = 0;
-    g.req_min[al] = INT_MAX;
-    g.target[al] = -1;
-  }
-  const int nacc = *(volatile int *)g.acc_count;
-  for (int j = threadIdx.x; j < nacc; j += blockDim.x) {
-    const int2 p = g.acc[j];
-    g.involved[p.x] = 0;
-    g.involved[p.y] = 0;
-  }
-}
-
-// Relabel accepted merges a -> n over a's bounding box, one CTA per merge.
-__device__ void merge_relabel(const StageArgs &a, int nacc) {
-  for (int j = blockIdx.x; j < nacc; j += gridDim.x) {
-    const int2 p = a.mg.acc[j];
-    const int4 bb = a.st.bbox[p.x];
-    const int bx0 = bb.x / a.side, bx1 = bb.z / a.side, by0 = bb.y / a.side, by1 = bb.w / a.side;
+    const int bx0 = ba.x / a.side, bx1 = ba.z / a.side, by0 = ba.y / a.side, by1 = ba.w / a.side;
     const int bw = bx1 - bx0 + 1;
     const long long total = (long long)bw * (by1 - by0 + 1);
     for (long long t = threadIdx.x; t < total; t += blockDim.x) {
       const long long idx = (long long)(by0 + (int)(t / bw)) * a.nbx + bx0 + (int)(t % bw);
-      if (a.lab[idx] == p.x) a.lab[idx] = p.y;
+      if (a.lab[idx] == al) a.lab[idx] = n;
     }
+  }
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += gridDim.x * blockDim.x) {
+    const int al = mg.found[j];
+    mg.req_flag[al] = 0;
+    mg.req_min[al] = INT_MAX;
+    mg.target[al] = -1;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && nacc) {
+    a.ctl.cnt[CNT_MERGES] += nacc;
+    *changes += (unsigned long long)nacc;
   }
 }
 
@@ -325,30 +459,59 @@ struct Timer {
   }
 };
 
-__global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs a) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.st.M; k += gridDim.x * blockDim.x) set_means(a.st, k);
-  if (!grid_sync(a.ctl)) return;
+__global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
+  __shared__ WarpTile wts[kThreads / 32];
+  __shared__ int2 s_acc[kAcceptSmem];
+  __shared__ int s_draw;
+  unsigned epoch = 0;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+  for (int k = blockIdx.x + gridDim.x * threadIdx.x; k < a.st.M; k += gstride) {
+
+    set_means(a.st, k);
+    a.st.chg[k] = 0;
+    a.mg.cache_stamp[k] = 0;
+    a.st.adj[k] = 0;
+  }
+  const int nrec = a.ntx * a.nty * 9;
+  for (int i = gtid; i < nrec; i += gstride) a.trec[(long long)i * kRecInts] = 0;
+  if (!grid_sync(a.ctl, epoch)) return;
   Timer tm(a.ctl.prof);
+  int g = 0;
   for (int sweep = 0; sweep < a.max_sweeps; sweep++) {
     unsigned long long *changes = &a.ctl.changes[sweep % 3];
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl.changes[(sweep + 1) % 3] = 0;
     for (int ph = 0; ph < 9; ph++) {
-      eval_phase(a, ph, changes);
+      g++;
+      eval_phase(a, wts, &s_draw, ph, g, changes);
+
       tm.lap(PROF_EVAL);
-      if (!grid_sync(a.ctl)) return;
+      if (!grid_sync(a.ctl, epoch)) return;
       tm.lap(PROF_SYNC1);
-      const int rq = ld_volatile_i32(a.mg.req_count);
-      commit_phase(a);
+      const int gp = g & 1;
+      const int rq = ld_volatile_i32(a.mg.req_count + gp);
+      if (blockIdx.x == 0 && threadIdx.x == 0) {  // slots of the next phase; last read a phase ago
+        a.mg.req_count[gp ^ 1] = 0;
+        a.mg.found_count[gp ^ 1] = 0;
+      }
+      commit_phase(a, g);
       tm.lap(PROF_COMMIT);
-      if (!grid_sync(a.ctl)) return;
+      if (!grid_sync(a.ctl, epoch)) return;
       tm.lap(PROF_SYNC2);
       if (rq > 0) {
-        merge_targets(a, rq);
-        if (!grid_sync(a.ctl)) return;
-        if (blockIdx.x == 0) merge_accept(a, rq, changes);
-        if (!grid_sync(a.ctl)) return;
-        merge_relabel(a, ld_volatile_i32(a.mg.acc_count));
-        if (!grid_sync(a.ctl)) return;
+        merge_targets(a, rq, g);
+        if (!grid_sync(a.ctl, epoch)) return;
+        const int nf = ld_volatile_i32(a.mg.found_count + gp);
+        if (nf > 0) {
+          if (nf <= kAcceptSmem) {
+            const int nacc = merge_walk_small(a, nf, s_acc);
+            merge_apply(a, s_acc, nacc, nf, g, changes);
+          } else {
+            if (blockIdx.x == 0) merge_walk_big(a, nf);
+            if (!grid_sync(a.ctl, epoch)) return;
+            merge_apply(a, a.mg.acc, ld_volatile_i32(a.mg.acc_count), nf, g, changes);
+          }
+          if (!grid_sync(a.ctl, epoch)) return;
+        }
         tm.lap(PROF_MERGE);
       }
     }

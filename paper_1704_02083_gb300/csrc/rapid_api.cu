@@ -51,6 +51,8 @@ struct rapid_ctx {
   int *d_lab[2];
   long long lab_cap;
   int *d_full;  // full-res staging for host reads at side > 1
+  int *d_trec;  // tile scan records, sized for the finest stage
+  long long trec_cap;
   long long full_cap;
   // labels
   int M, M_cap;
@@ -105,6 +107,9 @@ extern "C" void rapid_default_params(rapid_params *p) {
   p->max_sweeps = 64;
   p->h_T = 150;
   p->spin_limit_ns = 2000000000ll;
+  p->use_filter = 1;
+  p->skip_tiles = 1;
+  p->verify_filter = 0;
 }
 
 static bool params_ok(const rapid_params *p) {
@@ -115,7 +120,8 @@ static bool params_ok(const rapid_params *p) {
   if (p->K < 1 || p->size_mode < 0 || p->size_mode > 2 || p->max_sweeps < 1) return false;
   if (p->lo_den <= 0 || p->hi_den <= 0 || p->lo_num < 0 || p->hi_num < 0) return false;
   if (!std::isfinite(p->lambda_pos0) || !std::isfinite(p->lambda_b)) return false;
-  if ((p->predict | p->reuse | p->importance_rule) & ~1) return false;
+  if ((p->predict | p->reuse | p->importance_rule | p->use_filter | p->skip_tiles | p->verify_filter) & ~1)
+    return false;
   if (p->spin_limit_ns < 0 || p->h_T < 0 || p->h_T > (1ll << 40)) return false;
   long long f1 = 1;
   for (int i = 1; i < p->num_levels; i++) {
@@ -151,7 +157,7 @@ extern "C" rapid_status rapid_create(const rapid_params *p, void *cuda_stream, r
   ctx->coop_grid = ctx->nsm * per_sm;
   // control block: barrier (2 u32), error (i32), request/accept counts, sweep changes
   // (3 u64), counters.
-  size_t ctl_bytes = 64 + sizeof(long long) * (CNT_N + PROF_N) * RAPID_MAX_STAGES;
+  size_t ctl_bytes = 128 + sizeof(long long) * (CNT_N + PROF_N) * RAPID_MAX_STAGES;
   if (cudaMalloc(&ctx->d_ctl_block, ctl_bytes) != cudaSuccess) {
     delete ctx;
     return RAPID_ENOMEM;
@@ -159,11 +165,14 @@ extern "C" rapid_status rapid_create(const rapid_params *p, void *cuda_stream, r
   char *b = (char *)ctx->d_ctl_block;
   ctx->ctl.bar = (unsigned *)(b + 0);
   ctx->ctl.err = (int *)(b + 8);
-  ctx->mg.req_count = (int *)(b + 12);
-  ctx->mg.acc_count = (int *)(b + 16);
-  ctx->ctl.changes = (unsigned long long *)(b + 24);
-  ctx->ctl.cnt = (long long *)(b + 64);
-  ctx->prof = (long long *)(b + 64 + sizeof(long long) * CNT_N * RAPID_MAX_STAGES);
+  ctx->ctl.last_merge = (int *)(b + 12);
+  ctx->mg.req_count = (int *)(b + 16);    // [2], by phase parity
+  ctx->mg.found_count = (int *)(b + 24);  // [2], by phase parity
+  ctx->mg.acc_count = (int *)(b + 32);
+  ctx->ctl.changes = (unsigned long long *)(b + 40);
+  ctx->ctl.tiles = (unsigned long long *)(b + 64);
+  ctx->ctl.cnt = (long long *)(b + 128);
+  ctx->prof = (long long *)(b + 128 + sizeof(long long) * CNT_N * RAPID_MAX_STAGES);
   ctx->ctl.spin_ns = p->spin_limit_ns;
   if (cudaMemsetAsync(ctx->d_ctl_block, 0, ctl_bytes, ctx->stream) != cudaSuccess) {
     cudaFree(ctx->d_ctl_block);
@@ -191,6 +200,9 @@ static void free_image_buffers(rapid_ctx *ctx) {
   cudaFree(ctx->d_full);
   ctx->d_full = nullptr;
   ctx->full_cap = 0;
+  cudaFree(ctx->d_trec);
+  ctx->d_trec = nullptr;
+  ctx->trec_cap = 0;
 }
 
 extern "C" void rapid_destroy(rapid_ctx *ctx) {
@@ -291,6 +303,18 @@ extern "C" rapid_status rapid_set_image(rapid_ctx *ctx, const uint8_t *rgb, int3
     if (cudaMalloc(&ctx->d_lab[1], cap * sizeof(int)) != cudaSuccess) return RAPID_ENOMEM;
     ctx->lab_cap = cap;
   }
+  {
+    // tile records: the finest stage has the most tiles
+    const long long nbx = ceil_div(W, sl), nby = ceil_div(H, sl);
+    const long long nrec = ((nbx + kTileW - 1) / kTileW) * ((nby + kTileH - 1) / kTileH) * 9 * kRecInts;
+    if (nrec > ctx->trec_cap) {
+      cudaFree(ctx->d_trec);
+      ctx->d_trec = nullptr;
+      ctx->trec_cap = 0;
+      if (cudaMalloc(&ctx->d_trec, nrec * sizeof(int)) != cudaSuccess) return RAPID_ENOMEM;
+      ctx->trec_cap = nrec;
+    }
+  }
   CK(cudaMemcpy2DAsync(ctx->d_img, ctx->pitch, rgb, row_pitch_bytes, 3ull * W, H,
                        rgb_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
   if (!rgb_is_device) CK(cudaStreamSynchronize(ctx->stream));
@@ -330,59 +354,32 @@ static StageArgs stage_args(rapid_ctx *ctx) {
   a.hi_num = ctx->p.hi_num;
   a.hi_den = ctx->p.hi_den;
   a.max_sweeps = ctx->p.max_sweeps;
+  a.trec = ctx->d_trec;
+  a.ntx = (a.nbx + kTileW - 1) / kTileW;
+  a.nty = (a.nby + kTileH - 1) / kTileH;
+  a.lam_pos_f = (float)ctx->lam_pos;
+  a.lam_b2_f = (float)ctx->lam_b2;
+  // single-precision decisions need blocks under 2^24 pixels and exact float block centres
+  a.use_filter = ctx->p.use_filter && a.side <= 4096 && ctx->W < (1 << 22) && ctx->H < (1 << 22);
+  a.verify_filter = ctx->p.verify_filter;
+  a.skip_tiles = ctx->p.skip_tiles;
   return a;
 }
 
 static rapid_status ensure_label_arrays(rapid_ctx *ctx, int M) {
-  if (M <= ctx->M_cap) return RAPID_OK;
+  if (M <= ctx->M_cap) {
+    carve_label_arrays(ctx->d_label_block, label_arrays_bytes(ctx->M_cap), M, &ctx->st, &ctx->mg);
+    return RAPID_OK;
+  }
   cudaFree(ctx->d_label_block);
   cudaFree(ctx->d_pack);
   ctx->d_label_block = nullptr;
   ctx->d_pack = nullptr;
   ctx->M_cap = 0;
-  const size_t m = (size_t)M;
-  // 13 int64 + 5 double + int4 + int2 + 5 int32 + 4 bytes per label, 256-byte aligned slabs
-  const size_t slab8 = ((m * 8 + 255) / 256) * 256, slab16 = ((m * 16 + 255) / 256) * 256;
-  const size_t slab4 = ((m * 4 + 255) / 256) * 256, slab1 = ((m + 255) / 256) * 256;
-  const size_t total = 18 * slab8 + slab16 + slab8 /*int2*/ + 5 * slab4 + 4 * slab1;
-  if (cudaMalloc(&ctx->d_label_block, total) != cudaSuccess) return RAPID_ENOMEM;
-  if (cudaMalloc(&ctx->d_pack, m * sizeof(rapid_sp_stats)) != cudaSuccess) return RAPID_ENOMEM;
-  char *b = (char *)ctx->d_label_block;
-  auto take = [&](size_t n) {
-    char *r = b;
-    b += n;
-    return r;
-  };
-  DevStats &s = ctx->st;
-  s.N = (long long *)take(slab8);
-  s.R = (long long *)take(slab8);
-  s.G = (long long *)take(slab8);
-  s.B = (long long *)take(slab8);
-  s.X = (long long *)take(slab8);
-  s.Y = (long long *)take(slab8);
-  s.init = (long long *)take(slab8);
-  s.dN = (long long *)take(slab8);
-  s.dR = (long long *)take(slab8);
-  s.dG = (long long *)take(slab8);
-  s.dB = (long long *)take(slab8);
-  s.dX = (long long *)take(slab8);
-  s.dY = (long long *)take(slab8);
-  s.mR = (double *)take(slab8);
-  s.mG = (double *)take(slab8);
-  s.mB = (double *)take(slab8);
-  s.mX = (double *)take(slab8);
-  s.mY = (double *)take(slab8);
-  s.bbox = (int4 *)take(slab16);
-  ctx->mg.acc = (int2 *)take(slab8);
-  ctx->mg.req_list = (int *)take(slab4);
-  ctx->mg.req_min = (int *)take(slab4);
-  ctx->mg.req_flag = (int *)take(slab4);
-  ctx->mg.target = (int *)take(slab4);
-  ctx->mg.order = (int *)take(slab4);
-  s.dirty = (unsigned char *)take(slab1);
-  s.y = (signed char *)take(slab1);
-  s.imp = (unsigned char *)take(slab1);
-  ctx->mg.involved = (unsigned char *)take(slab1);
+  const size_t bytes = label_arrays_bytes(M);
+  if (cudaMalloc(&ctx->d_label_block, bytes) != cudaSuccess) return RAPID_ENOMEM;
+  if (cudaMalloc(&ctx->d_pack, (size_t)M * sizeof(rapid_sp_stats)) != cudaSuccess) return RAPID_ENOMEM;
+  carve_label_arrays(ctx->d_label_block, bytes, M, &ctx->st, &ctx->mg);
   ctx->M_cap = M;
   return RAPID_OK;
 }
@@ -429,7 +426,7 @@ extern "C" rapid_status rapid_seed_grid(rapid_ctx *ctx, int32_t *M_out) {
   }
   CK(launch_init_counters(ctx->ctl.cnt, sch, ctx->stream));
   CK(cudaMemsetAsync(ctx->prof, 0, sizeof(long long) * PROF_N * RAPID_MAX_STAGES, ctx->stream));
-  CK(cudaMemsetAsync(ctx->mg.req_count, 0, 2 * sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->mg.req_count, 0, 4 * sizeof(int), ctx->stream));
   int nl = 1;
   StageArgs a = stage_args(ctx);
   CK(launch_seed(a, gx, gy, ctx->stream, &nl));
@@ -463,7 +460,9 @@ extern "C" rapid_status rapid_refine_stage(rapid_ctx *ctx, int32_t *sweeps_out, 
   const int i = ctx->cur;
   // fresh barrier words and sweep-change slots for the launch
   CK(cudaMemsetAsync(ctx->ctl.bar, 0, 8, ctx->stream));
-  CK(cudaMemsetAsync(ctx->ctl.changes, 0, 3 * sizeof(unsigned long long), ctx->stream));
+  // last merge, request / found counts, sweep changes, tile counters
+  CK(cudaMemsetAsync((char *)ctx->d_ctl_block + 12, 0, 116, ctx->stream));
+
   StageArgs a = stage_args(ctx);
   if (ctx->profiling) {
     if (!ctx->ev_ok[i]) {
@@ -626,6 +625,12 @@ extern "C" rapid_status rapid_read_counters(rapid_ctx *ctx, rapid_counters *dst)
     o.moves = ci[CNT_MOVES];
     o.merge_requests = ci[CNT_REQ];
     o.merges = ci[CNT_MERGES];
+    o.fp64_fallbacks = ci[CNT_FALLBACK];
+    o.filter_mismatches = ci[CNT_MISMATCH];
+    o.tiles_scanned = ci[CNT_SCANNED];
+    o.tiles_skipped = ci[CNT_SKIPPED];
+    o.merge_searches = ci[CNT_SEARCHES];
+    o.merge_cache_hits = ci[CNT_CACHE_HITS];
     o.kernel_ms = -1.0f;
     for (int j = 0; j < PROF_N; j++) o.section_ms[j] = ctx->profiling ? (float)(pr[i * PROF_N + j] * 1e-6) : 0.0f;
     if (ctx->profiling && ctx->ev_ok[i] && i <= ctx->cur) {

@@ -2,13 +2,15 @@
 // coarse-to-fine topology-preserving superpixel refinement (RAPID, ICME 2017).
 //
 // Layout in HBM (all row-major):
-//   image   H x W interleaved RGB bytes, rows img_pitch bytes apart (multiple of 16)
+//   image   H x W interleaved RGB bytes, rows img_pitch bytes apart
 //   level   for each image level with factor f > 1: ceil(H/f) x ceil(W/f) int4 = exact
 //           (R, G, B, 0) sums of the f x f full-res footprint (Sec. 2.2, box "resize")
 //   labels  two int32 maps sized for the finest stage; the current stage uses nby x nbx
 //   S       structure of arrays over label ids: count, R, G, B, x, y, InitSize (int64),
-//           phase deltas of the first six (int64), snapshot means (5 doubles), class y
-//           (int8), boundary-superpixel flag (uint8), conservative bounding box (int4)
+//           phase deltas of the first six (int64), snapshot means (5 doubles) and their
+//           single-precision hi/lo splits, last-change stamps, class y (int8),
+//           boundary-superpixel flag (uint8), conservative bounding box (int4)
+//   tiles   per (tile, phase class) scan record: stamp, label set, counts
 // Position sums of a block are not stored: a block is an axis-aligned rectangle of
 // full-res pixels, so its count and x/y sums follow from its corners.
 #pragma once
@@ -17,18 +19,36 @@
 
 namespace rapid {
 
-enum { CNT_LEVEL = 0, CNT_SIDE, CNT_SWEEPS, CNT_ELIG, CNT_EVAL, CNT_MOVES, CNT_REQ, CNT_MERGES, CNT_N };
+enum { CNT_LEVEL = 0, CNT_SIDE, CNT_SWEEPS, CNT_ELIG, CNT_EVAL, CNT_MOVES, CNT_REQ, CNT_MERGES,
+       CNT_FALLBACK, CNT_MISMATCH, CNT_SCANNED, CNT_SKIPPED, CNT_SEARCHES, CNT_CACHE_HITS, CNT_N };
+
+// Tile hand-out: warps with global index w take tiles w % kTileCounters + kTileCounters i
+// from counter w % kTileCounters.
+constexpr int kTileCounters = 8;
 
 // Sections timed by the first CTA when profiling is on.
 enum { PROF_EVAL = 0, PROF_SYNC1, PROF_COMMIT, PROF_SYNC2, PROF_MERGE, PROF_N };
 
 // Device error word values (0 = fine).
-enum { DERR_TIMEOUT = 1, DERR_MERGE_OVERFLOW = 2 };
+enum { DERR_TIMEOUT = 1 };
+
+// Evaluation tiles: TW x TH blocks, one warp each; a phase class has at most 11 x 6 blocks
+// of a tile.
+constexpr int kTileW = 32, kTileH = 16, kTileLabels = 16;
+// tile record: stamp of the last scan, label count (-1: too many), eligible and evaluated
+// counts, the labels, and a bit per phase-class block that issued a merge request
+constexpr int kRecInts = 4 + kTileLabels + 3;
+constexpr int kCacheLabels = 16;           // neighbour labels remembered by a failed merge
 
 struct DevStats {
   long long *N, *R, *G, *B, *X, *Y, *init;
   long long *dN, *dR, *dG, *dB, *dX, *dY;
   double *mR, *mG, *mB, *mX, *mY;
+  float4 *fhi, *flo;  // single-precision (hi, lo) of cR, cG, cB, mX
+  float2 *fy;         // (hi, lo) of mY
+  int *chg;           // stamp of the last change of S_k in this stage (2g: moves of phase g,
+                      // 2g + 1: merges of phase g; 0 = before the stage)
+  int *adj;           // stamp (2g) of the last move of a block of label k or 4-adjacent to one
   unsigned char *dirty;
   signed char *y;
   unsigned char *imp;
@@ -37,7 +57,10 @@ struct DevStats {
 };
 
 struct DevMerge {
-  int *req_count;   // requests (distinct labels) of the phase
+  int *req_count;   // [2] requests (distinct labels) of the phase, slot = phase parity
+  int *found_count; // [2] requests whose target search found a target, slot = phase parity
+  int *found;       // [M] those requested labels
+
   int *req_list;    // [M] requested label ids
   int *req_min;     // [M] smallest requesting block index per label (INT_MAX = none)
   int *req_flag;    // [M] 1 when the label is in req_list
@@ -46,13 +69,18 @@ struct DevMerge {
   int2 *acc;        // [M] accepted (source, target) pairs of the phase
   int *acc_count;
   unsigned char *involved;  // [M]
+  int *cache_stamp; // [M] stamp of the last target search that found no target (0 = none)
+  int *cache_n;     // [M] number of neighbour labels it saw (-1 = too many to remember)
+  int *cache_nb;    // [M * kCacheLabels] those neighbour labels
 };
 
 struct DevCtl {
-  unsigned int *bar;             // [0] arrivals, [1] generation
+  unsigned int *bar;             // [0] arrivals (monotone within a launch)
   int *err;                      // first device error (0 = none)
   long long spin_ns;             // give-up time of one barrier wait
   unsigned long long *changes;   // [3] moves + merges of the sweep, rotating slots
+  unsigned long long *tiles;     // [kTileCounters] tile hand-out counters (monotone within a launch)
+  int *last_merge;               // stamp (2g + 1) of the last accepted merge of the launch
   long long *cnt;                // this stage's counters [CNT_N]
   long long *prof;               // this stage's section times [PROF_N] in ns, or null
 };
@@ -67,11 +95,17 @@ struct StageArgs {
   long long img_pitch;
   const int4 *pyr;    // level sums (f > 1), else unused
   int *lab;           // nby x nbx labels
+  int *trec;          // tile records [ntiles * 9 * kRecInts]
+  int ntx, nty;       // tile grid
   DevStats st;
   DevMerge mg;
   DevCtl ctl;
   int imp_on, imp_rule;
   double lam_pos, lam_b2;
+  float lam_pos_f, lam_b2_f;
+  int use_filter;     // 1: single-precision decisions with certified bounds, binary64 when undecided
+  int verify_filter;  // 1: also decide every block in binary64 and count disagreements
+  int skip_tiles;     // 1: skip tiles whose inputs did not change since their last scan
   int size_mode, lo_num, lo_den, hi_num, hi_den;
   int max_sweeps;
 };
@@ -120,45 +154,47 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(const volatile int *)p; }
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
   return *(const volatile unsigned long long *)p;
 }
 
-// All CTAs of a co-resident (cooperative) grid meet here.  Thread 0 of each CTA arrives
-// on a counter; the last arrival resets it and bumps the generation.  Every wait is
-// bounded by ctl.spin_ns (and an iteration cap); on give-up the CTA records
-// DERR_TIMEOUT and the whole grid returns false, so no kernel can hang.
-__device__ inline bool grid_sync(const DevCtl &c) {
+// All CTAs of a co-resident (cooperative) grid meet here.  The arrival counter only grows
+// during a launch: barrier number `epoch` (counted by every CTA) completes when it reaches
+// (epoch + 1) * gridDim.x.  Thread 0 arrives with a release add (after the CTA barrier, so
+// it publishes the whole CTA's writes) and polls with acquire loads.  Every wait is bounded
+// by ctl.spin_ns (and an iteration cap); on give-up the CTA records DERR_TIMEOUT and the
+// whole grid returns false, so no kernel can hang.
+__device__ inline bool grid_sync(const DevCtl &c, unsigned &epoch) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int good = 1;
-    unsigned nb = gridDim.x * gridDim.y * gridDim.z;
-    unsigned gen = ld_acquire_u32(&c.bar[1]);
-    __threadfence();
-    unsigned arrived = atomicAdd(&c.bar[0], 1u);
-    if (arrived == nb - 1) {
-      atomicExch(&c.bar[0], 0u);
-      __threadfence();
-      atomicAdd(&c.bar[1], 1u);
-    } else {
-      unsigned long long t0 = global_ns();
+    const unsigned target = (epoch + 1) * gridDim.x;
+    red_release_add_u32(&c.bar[0], 1u);
+    if (ld_acquire_u32(&c.bar[0]) < target) {
+      const unsigned long long t0 = global_ns();
       long long iters = 0;
-      while (ld_acquire_u32(&c.bar[1]) == gen) {
-        if (ld_volatile_i32(c.err) != 0) { good = 0; break; }
-        if ((long long)(global_ns() - t0) > c.spin_ns || ++iters > (1ll << 26)) {
+      while (ld_acquire_u32(&c.bar[0]) < target) {
+        if (ld_volatile_i32(c.err) != 0) {
+          good = 0;
+          break;
+        }
+        if ((long long)(global_ns() - t0) > c.spin_ns || ++iters > (1ll << 28)) {
           atomicCAS(c.err, 0, (int)DERR_TIMEOUT);
           good = 0;
           break;
         }
-        __nanosleep(32);
+        __nanosleep(20);  // keep the pollers from crowding the arrivals on the counter's line
       }
     }
-    __threadfence();
     ok = good;
   }
   __syncthreads();
+  epoch++;
   return ok != 0;
 }
 
@@ -225,19 +261,39 @@ __device__ __forceinline__ double blk_energy(double w, double r2, double g2, dou
   return __dadd_rn(__dadd_rn(ec, __dmul_rn(lam_pos, ep)), __dmul_rn(lam_b2, Bk));
 }
 
-// Snapshot means of label k from its exact sums: c = S / N (IEEE division).
+// Snapshot means of label k from its exact sums: c = S / N (IEEE division), plus their
+// single-precision hi/lo splits (hi = nearest float, lo = nearest float of the rest).
+__device__ __forceinline__ void split_f(double v, float &hi, float &lo) {
+  hi = __double2float_rn(v);
+  lo = __double2float_rn(__dsub_rn(v, (double)hi));
+}
+
 __device__ __forceinline__ void set_means(const DevStats &s, int k) {
   long long n = s.N[k];
+  double cr = 0.0, cg = 0.0, cb = 0.0, mx = 0.0, my = 0.0;
   if (n > 0) {
     double dn = __ll2double_rn(n);
-    s.mR[k] = __ddiv_rn(__ll2double_rn(s.R[k]), dn);
-    s.mG[k] = __ddiv_rn(__ll2double_rn(s.G[k]), dn);
-    s.mB[k] = __ddiv_rn(__ll2double_rn(s.B[k]), dn);
-    s.mX[k] = __ddiv_rn(__ll2double_rn(s.X[k]), dn);
-    s.mY[k] = __ddiv_rn(__ll2double_rn(s.Y[k]), dn);
-  } else {
-    s.mR[k] = s.mG[k] = s.mB[k] = s.mX[k] = s.mY[k] = 0.0;
+    cr = __ddiv_rn(__ll2double_rn(s.R[k]), dn);
+    cg = __ddiv_rn(__ll2double_rn(s.G[k]), dn);
+    cb = __ddiv_rn(__ll2double_rn(s.B[k]), dn);
+    mx = __ddiv_rn(__ll2double_rn(s.X[k]), dn);
+    my = __ddiv_rn(__ll2double_rn(s.Y[k]), dn);
   }
+  s.mR[k] = cr;
+  s.mG[k] = cg;
+  s.mB[k] = cb;
+  s.mX[k] = mx;
+  s.mY[k] = my;
+  float4 hi, lo;
+  float2 fy;
+  split_f(cr, hi.x, lo.x);
+  split_f(cg, hi.y, lo.y);
+  split_f(cb, hi.z, lo.z);
+  split_f(mx, hi.w, lo.w);
+  split_f(my, fy.x, fy.y);
+  s.fhi[k] = hi;
+  s.flo[k] = lo;
+  s.fy[k] = fy;
 }
 
 // Merge cost of labels a and n (Sec. 3.1): the Ward increase of the colour and position
@@ -265,5 +321,10 @@ __device__ __forceinline__ void atomic_add_i64(long long *p, long long v) {
 cudaError_t launch_stage(const StageArgs &a, int grid, int block, cudaStream_t s);
 int stage_block_threads();
 const void *stage_kernel_ptr();
+
+// Carve the per-label arrays of M labels from `base` (256-byte aligned pieces); returns the
+// bytes used, or 0 when they do not fit in `cap` bytes.  label_arrays_bytes(M) is the size.
+size_t carve_label_arrays(void *base, size_t cap, int M, DevStats *st, DevMerge *mg);
+size_t label_arrays_bytes(int M);
 
 }  // namespace rapid

@@ -149,44 +149,36 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   rapid_status rs = scratch_on_current_device(&base);
   if (rs != RAPID_OK) return rs;
   Carve cv{base, 0, kStaticScratchBytes};
-  const size_t ctl_bytes = 64 + sizeof(long long) * CNT_N * RAPID_MAX_STAGES;
+  const size_t ctl_bytes = 128 + sizeof(long long) * CNT_N * RAPID_MAX_STAGES;
   unsigned char *ctl = (unsigned char *)cv.take(ctl_bytes);
   int4 *pyr[kMaxLevelsStatic + 1] = {nullptr};
   for (int l = 1; l <= L; l++)
     if (f[l] > 1) pyr[l] = (int4 *)cv.take((size_t)Wl[l] * Hl[l] * sizeof(int4));
   const long long cap = (long long)cdiv(W, side[nst - 1]) * cdiv(H, side[nst - 1]);
   int *lab[2] = {(int *)cv.take(cap * sizeof(int)), (int *)cv.take(cap * sizeof(int))};
-  const size_t m = (size_t)M;
+  const int ntx_max = (cdiv(W, side[nst - 1]) + kTileW - 1) / kTileW;
+  const int nty_max = (cdiv(H, side[nst - 1]) + kTileH - 1) / kTileH;
+  int *trec = (int *)cv.take((size_t)ntx_max * nty_max * 9 * kRecInts * sizeof(int));
   DevStats st;
   DevMerge mg;
   std::memset(&st, 0, sizeof st);
   std::memset(&mg, 0, sizeof mg);
-  long long **i64[] = {&st.N, &st.R, &st.G, &st.B, &st.X, &st.Y, &st.init, &st.dN, &st.dR, &st.dG, &st.dB, &st.dX, &st.dY};
-  for (long long **q : i64) *q = (long long *)cv.take(m * 8);
-  double **f64[] = {&st.mR, &st.mG, &st.mB, &st.mX, &st.mY};
-  for (double **q : f64) *q = (double *)cv.take(m * 8);
-  st.bbox = (int4 *)cv.take(m * 16);
-  mg.acc = (int2 *)cv.take(m * 8);
-  int **i32[] = {&mg.req_list, &mg.req_min, &mg.req_flag, &mg.target, &mg.order};
-  for (int **q : i32) *q = (int *)cv.take(m * 4);
-  st.dirty = (unsigned char *)cv.take(m);
-  st.y = (signed char *)cv.take(m);
-  st.imp = (unsigned char *)cv.take(m);
-  mg.involved = (unsigned char *)cv.take(m);
-  bool ok = ctl && lab[0] && lab[1] && st.bbox && mg.acc && st.dirty && st.y && st.imp && mg.involved;
-  for (long long **q : i64) ok = ok && *q;
-  for (double **q : f64) ok = ok && *q;
-  for (int **q : i32) ok = ok && *q;
+  const size_t lbytes = label_arrays_bytes(M);
+  void *lblock = cv.take(lbytes);
+  bool ok = ctl && lab[0] && lab[1] && trec && lblock;
   for (int l = 1; l <= L; l++) ok = ok && (f[l] == 1 || pyr[l]);
   if (!ok) return RAPID_ERANGE;  // this image and parameter set need more than the fixed array
-  st.M = M;
+  carve_label_arrays(lblock, lbytes, M, &st, &mg);
   DevCtl c;
   c.bar = (unsigned *)(ctl + 0);
   c.err = (int *)(ctl + 8);
-  mg.req_count = (int *)(ctl + 12);
-  mg.acc_count = (int *)(ctl + 16);
-  c.changes = (unsigned long long *)(ctl + 24);
-  c.cnt = (long long *)(ctl + 64);
+  c.last_merge = (int *)(ctl + 12);
+  mg.req_count = (int *)(ctl + 16);
+  mg.found_count = (int *)(ctl + 24);
+  mg.acc_count = (int *)(ctl + 32);
+  c.changes = (unsigned long long *)(ctl + 40);
+  c.tiles = (unsigned long long *)(ctl + 64);
+  c.cnt = (long long *)(ctl + 128);
   c.prof = nullptr;
   c.spin_ns = p->spin_limit_ns;
 
@@ -234,6 +226,11 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   a.hi_num = p->hi_num;
   a.hi_den = p->hi_den;
   a.max_sweeps = p->max_sweeps;
+  a.trec = trec;
+  a.lam_pos_f = (float)a.lam_pos;
+  a.lam_b2_f = (float)a.lam_b2;
+  a.verify_filter = p->verify_filter;
+  a.skip_tiles = p->skip_tiles;
   int buf = 0, nbx = nbx0, nby = nby0, launches = 0;
   auto set_stage = [&](int i) {
     a.side = side[i];
@@ -248,6 +245,9 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
     a.lab = lab[buf];
     a.ctl = c;
     a.ctl.cnt = c.cnt + (long long)CNT_N * i;
+    a.ntx = (nbx + kTileW - 1) / kTileW;
+    a.nty = (nby + kTileH - 1) / kTileH;
+    a.use_filter = p->use_filter && a.side <= 4096 && W < (1 << 22) && H < (1 << 22);
   };
   set_stage(0);
   CKS(launch_seed(a, gx, gy, stream, &launches));
@@ -266,7 +266,8 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
       if (!p->reuse && lev[i] != lev[i - 1]) CKS(launch_recompute(a, stream, &launches));
     }
     CKS(cudaMemsetAsync(c.bar, 0, 8, stream));
-    CKS(cudaMemsetAsync(c.changes, 0, 3 * sizeof(unsigned long long), stream));
+    CKS(cudaMemsetAsync(ctl + 12, 0, 116, stream));  // last merge, request / found counts, sweep changes, tile counters
+
     CKS(launch_stage(a, nsm * per_sm, stage_block_threads(), stream));
   }
   // Outputs into the caller's buffers.

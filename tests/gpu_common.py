@@ -29,8 +29,21 @@ def gpu_run(rgb: np.ndarray, device_input: bool = True, **params):
 
 
 def oracle_run(rgb: np.ndarray, **params):
-    p = {k: v for k, v in params.items() if k != "spin_limit_ns"}
+    p = {k: v for k, v in params.items() if k in oracle.DEFAULTS}
     return oracle.run(rgb, **p)
+
+
+def gpu_counters(rgb: np.ndarray, **params):
+    """Full rapid_counters of one run (for the implementation counters)."""
+    import torch
+
+    import paper_1704_02083_gb300 as pkg
+
+    with pkg.Context(stream=torch.cuda.current_stream(), **params) as ctx:
+        ctx.set_image(torch.from_numpy(np.ascontiguousarray(rgb)).cuda())
+        ctx.run()
+        c = ctx.counters()
+        return [c.stage[i] for i in range(c.num_stages)], ctx.labels()
 
 
 def assert_parity(rgb, **params):

@@ -58,6 +58,7 @@ def test_host_only_calls(pkg):
     assert (p.lambda_pos0, p.lambda_b) == (400.0, 50.0)
     assert (p.lo_num, p.lo_den, p.hi_num, p.hi_den) == (1, 4, 3, 2)
     assert (p.max_sweeps, p.h_T, p.spin_limit_ns) == (64, 150, 2_000_000_000)
+    assert (p.use_filter, p.skip_tiles, p.verify_filter) == (1, 1, 0)
     with pytest.raises(pkg.RapidError) as e:  # argument check happens before any CUDA call
         pkg.rapid_create(pkg.rapid_default_params(K=0))
     assert e.value.status == pkg.RAPID_EINVAL

@@ -1,0 +1,60 @@
+"""The two exact shortcuts of the stage kernel: single-precision decisions with a certified
+error bound (binary64 when undecided) and skipping tiles whose inputs did not change.
+Both must leave labels, statistics and every oracle counter unchanged, and the
+single-precision decisions must never disagree with binary64."""
+import numpy as np
+import pytest
+
+from gpu_common import gpu_counters, gpu_run, oracle_run
+from paper_1704_02083_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+CASES = [
+    ("bsd", synth.workload_image("he321x481_k200").rgb, synth.WORKLOADS["he321x481_k200"]["params"]),
+    ("l3", synth.he_image(512, 640, 60, 4).rgb,
+     dict(num_levels=3, ratio_C=4, init_block=32, K=320, predict=1, size_mode=2)),
+    ("rand", synth.random_image(96, 128, 5, levels=4), dict(K=40, init_block=8, size_mode=1)),
+    ("flat-ish", synth.random_image(80, 80, 6, levels=2), dict(K=16, init_block=4, size_mode=0, lambda_pos0=0.0)),
+]
+
+
+@pytest.mark.parametrize("name,rgb,params", CASES, ids=[c[0] for c in CASES])
+def test_shortcuts_change_nothing(name, rgb, params):
+    ref = gpu_run(rgb, use_filter=0, skip_tiles=0, **params)
+    for uf, st in ((1, 0), (0, 1), (1, 1)):
+        got = gpu_run(rgb, use_filter=uf, skip_tiles=st, **params)
+        for x, y in zip(got, ref):
+            np.testing.assert_array_equal(x, y, err_msg=f"use_filter={uf} skip_tiles={st}")
+    o = oracle_run(rgb, **params)
+    np.testing.assert_array_equal(ref[0], o[0])
+    np.testing.assert_array_equal(ref[4], o[4])
+
+
+@pytest.mark.parametrize("name,rgb,params", CASES, ids=[c[0] for c in CASES])
+def test_filter_never_disagrees_with_binary64(name, rgb, params):
+    stages, _ = gpu_counters(rgb, verify_filter=1, **params)
+    assert sum(s.filter_mismatches for s in stages) == 0
+    evaluated = sum(s.evaluated for s in stages)
+    fallbacks = sum(s.fp64_fallbacks for s in stages)
+    assert evaluated > 0
+    assert fallbacks <= evaluated
+    if name != "flat-ish":  # exact ties are common there and go to binary64 by design
+        assert fallbacks < 0.05 * evaluated, (fallbacks, evaluated)
+
+
+def test_tiles_are_skipped_on_long_stages():
+    img = synth.he_image(512, 640, 60, 4).rgb
+    stages, _ = gpu_counters(img, num_levels=3, ratio_C=4, init_block=32, K=320, predict=1)
+    last = stages[-1]
+    assert last.tiles_skipped > 0 and last.tiles_scanned > 0
