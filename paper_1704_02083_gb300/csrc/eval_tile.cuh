@@ -35,7 +35,7 @@ __device__ __forceinline__ void tab_insert(WarpTile &W, int v) {
     if (cur == -1) {
       cur = atomicCAS(&W.hkey[h], -1, v);
       if (cur == -1) {
-        if (atomicAdd(&W.hcount, 1) >= kTileLabels) W.over = 1;
+        if (atomicAdd(&W.hcount, 1) >= kTileLabels) *(volatile int *)&W.over = 1;
         return;
       }
       if (cur == v) return;
@@ -343,7 +343,8 @@ __device__ void eval_phase(const StageArgs &a, WarpTile *wts, int *s_draw, int p
       for (int wy = 0; wy < kWinH; wy++) {
         const int v = vals[wy];
         W.win[wy * kWinW + col] = v;
-        if (v != prev && v >= 0) tab_insert(W, v);
+        // once the window has more labels than a record holds the table is not used
+        if (v != prev && v >= 0 && !*(volatile int *)&W.over) tab_insert(W, v);
         prev = v;
       }
     }

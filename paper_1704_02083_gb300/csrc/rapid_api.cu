@@ -41,8 +41,11 @@ struct rapid_ctx {
   size_t img_cap;
   int L;
   int f[kMaxLevels + 1], Wl[kMaxLevels + 1], Hl[kMaxLevels + 1];
-  int4 *d_pyr[kMaxLevels + 1];
-  size_t pyr_cap[kMaxLevels + 1];
+  // box-sum levels for block sums (factors sf[i] > 1, ascending)
+  int nsf;
+  int sf[kMaxSumLevels], sfW[kMaxSumLevels], sfH[kMaxSumLevels];
+  int4 *d_pyr[kMaxSumLevels];
+  size_t pyr_cap[kMaxSumLevels];
   // schedule
   int nstages;
   int st_level[RAPID_MAX_STAGES], st_side[RAPID_MAX_STAGES];
@@ -188,7 +191,7 @@ static void free_image_buffers(rapid_ctx *ctx) {
   cudaFree(ctx->d_img);
   ctx->d_img = nullptr;
   ctx->img_cap = 0;
-  for (int l = 0; l <= kMaxLevels; l++) {
+  for (int l = 0; l < kMaxSumLevels; l++) {
     cudaFree(ctx->d_pyr[l]);
     ctx->d_pyr[l] = nullptr;
     ctx->pyr_cap[l] = 0;
@@ -281,9 +284,11 @@ extern "C" rapid_status rapid_set_image(rapid_ctx *ctx, const uint8_t *rgb, int3
     if (cudaMalloc(&ctx->d_img, need) != cudaSuccess) return RAPID_ENOMEM;
     ctx->img_cap = need;
   }
-  for (int l = 1; l <= ctx->L; l++) {
-    if (ctx->f[l] == 1) continue;
-    size_t pn = (size_t)ctx->Wl[l] * ctx->Hl[l] * sizeof(int4);
+  ctx->nsf = sum_factors(ctx->f, ctx->L, ctx->st_side[0], ctx->sf);
+  for (int l = 0; l < ctx->nsf; l++) {
+    ctx->sfW[l] = ceil_div(W, ctx->sf[l]);
+    ctx->sfH[l] = ceil_div(H, ctx->sf[l]);
+    size_t pn = (size_t)ctx->sfW[l] * ctx->sfH[l] * sizeof(int4);
     if (pn > ctx->pyr_cap[l]) {
       cudaFree(ctx->d_pyr[l]);
       ctx->d_pyr[l] = nullptr;
@@ -331,13 +336,20 @@ static StageArgs stage_args(rapid_ctx *ctx) {
   a.nbx = ctx->nbx;
   a.nby = ctx->nby;
   a.level = ctx->st_level[ctx->cur];
-  a.f = ctx->f[a.level];
+  // colour sums from the coarsest box-sum level whose cells fit in a block
+  a.f = 1;
+  a.pyr = nullptr;
+  for (int l = 0; l < ctx->nsf; l++)
+    if (ctx->sf[l] <= a.side) {
+      a.f = ctx->sf[l];
+      a.pyr = ctx->d_pyr[l];
+    }
   a.k = a.side / a.f;
-  a.Wl = ctx->Wl[a.level];
-  a.Hl = ctx->Hl[a.level];
+  a.Wl = ceil_div(ctx->W, a.f);
+  a.Hl = ceil_div(ctx->H, a.f);
   a.img = ctx->d_img;
   a.img_pitch = ctx->pitch;
-  a.pyr = ctx->d_pyr[a.level];
+
   a.lab = ctx->d_lab[ctx->cur_buf];
   a.st = ctx->st;
   a.mg = ctx->mg;
@@ -388,13 +400,13 @@ extern "C" rapid_status rapid_seed_grid(rapid_ctx *ctx, int32_t *M_out) {
   if (!ctx) return RAPID_EINVAL;
   if (ctx->sticky != RAPID_OK) return ctx->sticky;
   if (!ctx->image_set) return RAPID_ESTATE;
-  // level images
-  for (int l = 1; l <= ctx->L; l++) {
-    if (ctx->f[l] == 1) continue;
-    CK(launch_pyramid(ctx->d_img, ctx->pitch, ctx->H, ctx->W, ctx->f[l], ctx->Wl[l], ctx->Hl[l], ctx->d_pyr[l],
+  // level images (exact box sums, Sec. 2.2) and the extra box-sum levels for block sums
+  for (int l = 0; l < ctx->nsf; l++) {
+    CK(launch_pyramid(ctx->d_img, ctx->pitch, ctx->H, ctx->W, ctx->sf[l], ctx->sfW[l], ctx->sfH[l], ctx->d_pyr[l],
                       ctx->stream));
     ctx->launches++;
   }
+
   ctx->cur = 0;
   ctx->cur_buf = 0;
   const int s0 = ctx->st_side[0];

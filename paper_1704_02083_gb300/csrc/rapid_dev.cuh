@@ -110,6 +110,32 @@ struct StageArgs {
   int max_sweeps;
 };
 
+// Box-sum levels kept for block sums: the method's level factors (> 1) plus 4, 16 and 64
+// when a stage block is at least that large, so a block's colour sum never needs more than
+// a few cells (the sums are exact integers whichever level supplies them).  Returns the
+// count; out[] ascending.
+constexpr int kMaxSumLevels = 12;
+inline int sum_factors(const int *level_f, int L, int max_side, int *out) {
+  int n = 0;
+  auto add = [&](int v) {
+    if (v <= 1 || v > max_side) return;
+    for (int i = 0; i < n; i++)
+      if (out[i] == v) return;
+    if (n < kMaxSumLevels) out[n++] = v;
+  };
+  for (int l = 1; l <= L; l++) add(level_f[l]);
+  add(4);
+  add(16);
+  add(64);
+  for (int i = 1; i < n; i++)  // insertion sort, ascending
+    for (int j = i; j > 0 && out[j - 1] > out[j]; j--) {
+      const int t = out[j];
+      out[j] = out[j - 1];
+      out[j - 1] = t;
+    }
+  return n;
+}
+
 // Stage schedule handed to the counter initialiser (by value).
 struct Schedule {
   int n;

@@ -151,9 +151,10 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   Carve cv{base, 0, kStaticScratchBytes};
   const size_t ctl_bytes = 128 + sizeof(long long) * CNT_N * RAPID_MAX_STAGES;
   unsigned char *ctl = (unsigned char *)cv.take(ctl_bytes);
-  int4 *pyr[kMaxLevelsStatic + 1] = {nullptr};
-  for (int l = 1; l <= L; l++)
-    if (f[l] > 1) pyr[l] = (int4 *)cv.take((size_t)Wl[l] * Hl[l] * sizeof(int4));
+  int sf[kMaxSumLevels];
+  const int nsf = sum_factors(f, L, side[0], sf);
+  int4 *pyr[kMaxSumLevels] = {nullptr};
+  for (int l = 0; l < nsf; l++) pyr[l] = (int4 *)cv.take((size_t)cdiv(W, sf[l]) * cdiv(H, sf[l]) * sizeof(int4));
   const long long cap = (long long)cdiv(W, side[nst - 1]) * cdiv(H, side[nst - 1]);
   int *lab[2] = {(int *)cv.take(cap * sizeof(int)), (int *)cv.take(cap * sizeof(int))};
   const int ntx_max = (cdiv(W, side[nst - 1]) + kTileW - 1) / kTileW;
@@ -166,7 +167,7 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   const size_t lbytes = label_arrays_bytes(M);
   void *lblock = cv.take(lbytes);
   bool ok = ctl && lab[0] && lab[1] && trec && lblock;
-  for (int l = 1; l <= L; l++) ok = ok && (f[l] == 1 || pyr[l]);
+  for (int l = 0; l < nsf; l++) ok = ok && pyr[l];
   if (!ok) return RAPID_ERANGE;  // this image and parameter set need more than the fixed array
   carve_label_arrays(lblock, lbytes, M, &st, &mg);
   DevCtl c;
@@ -198,8 +199,8 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
 
   // Start from a clean control block: barrier, error word, request counts, counters.
   CKS(cudaMemsetAsync(ctl, 0, ctl_bytes, stream));
-  for (int l = 1; l <= L; l++)
-    if (f[l] > 1) CKS(launch_pyramid(rgb_dev, rgb_pitch_bytes, H, W, f[l], Wl[l], Hl[l], pyr[l], stream));
+  for (int l = 0; l < nsf; l++)
+    CKS(launch_pyramid(rgb_dev, rgb_pitch_bytes, H, W, sf[l], cdiv(W, sf[l]), cdiv(H, sf[l]), pyr[l], stream));
   Schedule sch;
   std::memset(&sch, 0, sizeof sch);
   sch.n = nst;
@@ -237,11 +238,17 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
     a.nbx = nbx;
     a.nby = nby;
     a.level = lev[i];
-    a.f = f[a.level];
+    a.f = 1;
+    a.pyr = nullptr;
+    for (int l = 0; l < nsf; l++)
+      if (sf[l] <= a.side) {
+        a.f = sf[l];
+        a.pyr = pyr[l];
+      }
     a.k = a.side / a.f;
-    a.Wl = Wl[a.level];
-    a.Hl = Hl[a.level];
-    a.pyr = pyr[a.level];
+    a.Wl = cdiv(W, a.f);
+    a.Hl = cdiv(H, a.f);
+
     a.lab = lab[buf];
     a.ctl = c;
     a.ctl.cnt = c.cnt + (long long)CNT_N * i;
