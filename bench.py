@@ -147,18 +147,25 @@ def stage_alg_bytes(H, W, stage_counters, level_factor):
 
 
 def kernel_traffic():
-    """Per-launch DRAM bytes of the stage kernel from the committed ncu summary, when it was
-    taken on the current kernel source; else None."""
+    """Per-launch DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of the finest
+    stage's launch from the committed ncu summary, when it was taken on the current kernel
+    source; else None."""
     path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
     if not os.path.exists(path):
         return None, None
     d = json.load(open(path))
-    src = os.path.join(ROOT, "paper_1704_02083_gb300", "csrc", "k_stage.cu")
-    hdr = os.path.join(ROOT, "paper_1704_02083_gb300", "csrc", "rapid_dev.cuh")
-    sha = hashlib.sha256(open(src, "rb").read() + open(hdr, "rb").read()).hexdigest()
-    if d.get("kernel_source_sha256") != sha:
+    if d.get("kernel_source_sha256") != kernel_source_sha256():
         return None, d
-    return d.get("dram_bytes_per_launch_full_workload"), d
+    return d.get("dram_bytes_per_launch"), d
+
+
+def kernel_source_sha256():
+    """Hash of the sources the stage kernel is compiled from."""
+    csrc = os.path.join(ROOT, "paper_1704_02083_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in ("k_stage.cu", "eval_tile.cuh", "rapid_dev.cuh"):
+        h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()
 
 
 def measured_peak():
@@ -227,7 +234,7 @@ def run_rapid(args, rank, world, local):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    step_ms, stage_ms, stage_bytes = [], 0.0, 0
+    step_ms, stage_ms, stage_bytes = [], {}, {}
     for _ in range(args.steps):
         flush.zero_()  # L2 flush between steps (outside the timed events)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -240,8 +247,8 @@ def run_rapid(args, rank, world, local):
         c = ctx.counters()
         for i in range(c.num_stages):
             st = c.stage[i]
-            stage_ms += st.kernel_ms
-            stage_bytes += stage_alg_bytes(H, W, st, lf)
+            stage_ms[i] = stage_ms.get(i, 0.0) + st.kernel_ms
+            stage_bytes[i] = stage_bytes.get(i, 0) + stage_alg_bytes(H, W, st, lf)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -291,9 +298,17 @@ def run_rapid(args, rank, world, local):
         cpu = {"value": rgb_s.shape[0] * rgb_s.shape[1] / ts[0] / 1e6, "unit": UNIT, "cores": 1,
                "kind": "oracle", "sample": desc}
 
+    # roofline of the dominant launch: the stage launch with the largest device time (the
+    # finest stage); its duration from CUDA events around each stage launch on ``stream``
     peak, peak_kind = measured_peak()
-    achieved = stage_bytes / (stage_ms / 1e3) / 1e9 if stage_ms > 0 else None
+    dom = max(stage_ms, key=stage_ms.get)
+    launch_ms = stage_ms[dom] / args.steps
+    launch_bytes = stage_bytes[dom] / args.steps
+    achieved = launch_bytes / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else None
+    all_ms, all_bytes = sum(stage_ms.values()), sum(stage_bytes.values())
+    all_achieved = all_bytes / (all_ms / 1e3) / 1e9 if all_ms > 0 else None
     traffic, _ = kernel_traffic()
+    st_dom = c1.stage[dom]
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -305,11 +320,16 @@ def run_rapid(args, rank, world, local):
                        "size_mode": params["size_mode"], "predict": params["predict"], "reuse": params["reuse"],
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": {"kernel": "stage_kernel (all stage launches)", "bound": "hbm", "achieved": achieved,
-                         "peak": peak, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-                         "peak_source": peak_kind, "traffic": traffic,
-                         "stage_kernel_ms_per_step": stage_ms / args.steps,
-                         "alg_bytes_per_step": stage_bytes / args.steps},
+            "roofline": {"kernel": f"stage_kernel, stage {dom} (level {st_dom.level}, block side {st_dom.block})",
+                         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
+                         "traffic": traffic, "alg_bytes_per_launch": launch_bytes, "launch_ms": launch_ms,
+                         "share_of_step": launch_ms / (total_ms / args.steps),
+                         "all_stage_launches": {"launches_per_step": len(stage_ms),
+                                                "ms_per_step": all_ms / args.steps,
+                                                "alg_bytes_per_step": all_bytes / args.steps,
+                                                "achieved": all_achieved,
+                                                "frac": (all_achieved / peak) if all_achieved else None}},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(round(launches_per_step * args.steps)),

@@ -142,7 +142,8 @@ rapid_status rapid_create(const rapid_params *p, void *cuda_stream, rapid_ctx **
  * host input and stream-ordered for device input.  Allocates the per-image buffers;
  * resets the context to "image set, not seeded".  EINVAL (H or W < 1, H*W >= 2^31, or
  * H*W*max(H,W) >= 2^53, which would break exact double conversion of position sums),
- * ENOMEM, ECUDA. */
+ * ERANGE (a level factor f with min(f,W)*min(f,H)*255 > 2^31 - 1: the level's int32
+ * colour sums would overflow), ENOMEM, ECUDA. */
 rapid_status rapid_set_image(rapid_ctx *ctx, const uint8_t *rgb, int32_t H, int32_t W,
                              int64_t row_pitch_bytes, int32_t rgb_is_device);
 

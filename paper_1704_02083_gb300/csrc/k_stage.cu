@@ -10,11 +10,13 @@
 // Merge requests of the phase (size bound hit, Sec. 3.1) are then resolved against the
 // post-move state.
 //
-// Work layout: a CTA takes 64 x 32-block tiles, stages the tile's labels (with a 1-block
-// halo) in shared memory and gives each thread one block of the phase class.  A tile is
-// skipped when no label present in it has changed since its last scan in this phase class
-// and that scan issued no merge request: its blocks would decide exactly as before (no
-// move), so the recorded counts are replayed instead.
+// Work layout: one persistent CTA of 1024 threads per SM.  In the evaluation each warp takes
+// tiles of 32 x 16 blocks (CTA b takes tiles b, b + grid, ...; its warps draw them from a
+// shared counter), stages the tile's labels with a 1-block halo in shared memory and
+// decides the tile's blocks of the phase class (eval_tile.cuh).  A tile is skipped when no
+// label present in it has changed since its last scan in this phase class and that scan
+// issued no merge request: its blocks would decide exactly as before (no move), so the
+// recorded counts are replayed instead.
 //
 // Decisions: the energy difference of each candidate label k against the block's label a
 // is first computed in single precision in the well-conditioned form

@@ -1,6 +1,7 @@
 // rapid_api.cu — the C ABI (include/rapid.h): context, device buffers, stage schedule and
 // launch orchestration.  Host code only; every step of the method runs in the kernels of
 // k_prep.cu and k_stage.cu.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdlib>
@@ -173,7 +174,6 @@ extern "C" rapid_status rapid_create(const rapid_params *p, void *cuda_stream, r
   ctx->mg.found_count = (int *)(b + 24);  // [2], by phase parity
   ctx->mg.acc_count = (int *)(b + 32);
   ctx->ctl.changes = (unsigned long long *)(b + 40);
-  ctx->ctl.tiles = (unsigned long long *)(b + 64);
   ctx->ctl.cnt = (long long *)(b + 128);
   ctx->prof = (long long *)(b + 128 + sizeof(long long) * CNT_N * RAPID_MAX_STAGES);
   ctx->ctl.spin_ns = p->spin_limit_ns;
@@ -285,6 +285,9 @@ extern "C" rapid_status rapid_set_image(rapid_ctx *ctx, const uint8_t *rgb, int3
     ctx->img_cap = need;
   }
   ctx->nsf = sum_factors(ctx->f, ctx->L, ctx->st_side[0], ctx->sf);
+  // a sum level keeps int32 channel sums: one cell (at most f x f pixels of 255) must fit
+  for (int l = 0; l < ctx->nsf; l++)
+    if ((long long)std::min(ctx->sf[l], W) * std::min(ctx->sf[l], H) * 255 > INT_MAX) return RAPID_ERANGE;
   for (int l = 0; l < ctx->nsf; l++) {
     ctx->sfW[l] = ceil_div(W, ctx->sf[l]);
     ctx->sfH[l] = ceil_div(H, ctx->sf[l]);

@@ -22,10 +22,6 @@ namespace rapid {
 enum { CNT_LEVEL = 0, CNT_SIDE, CNT_SWEEPS, CNT_ELIG, CNT_EVAL, CNT_MOVES, CNT_REQ, CNT_MERGES,
        CNT_FALLBACK, CNT_MISMATCH, CNT_SCANNED, CNT_SKIPPED, CNT_SEARCHES, CNT_CACHE_HITS, CNT_N };
 
-// Tile hand-out: warps with global index w take tiles w % kTileCounters + kTileCounters i
-// from counter w % kTileCounters.
-constexpr int kTileCounters = 8;
-
 // Sections timed by the first CTA when profiling is on.
 enum { PROF_EVAL = 0, PROF_SYNC1, PROF_COMMIT, PROF_SYNC2, PROF_MERGE, PROF_N };
 
@@ -79,7 +75,6 @@ struct DevCtl {
   int *err;                      // first device error (0 = none)
   long long spin_ns;             // give-up time of one barrier wait
   unsigned long long *changes;   // [3] moves + merges of the sweep, rotating slots
-  unsigned long long *tiles;     // [kTileCounters] tile hand-out counters (monotone within a launch)
   int *last_merge;               // stamp (2g + 1) of the last accepted merge of the launch
   long long *cnt;                // this stage's counters [CNT_N]
   long long *prof;               // this stage's section times [PROF_N] in ns, or null

@@ -178,7 +178,6 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   mg.found_count = (int *)(ctl + 24);
   mg.acc_count = (int *)(ctl + 32);
   c.changes = (unsigned long long *)(ctl + 40);
-  c.tiles = (unsigned long long *)(ctl + 64);
   c.cnt = (long long *)(ctl + 128);
   c.prof = nullptr;
   c.spin_ns = p->spin_limit_ns;

@@ -60,6 +60,20 @@ def test_invalid_arguments(pkg):
         assert e.value.status == pkg.RAPID_EINVAL
 
 
+def test_level_sums_that_would_overflow_are_refused(pkg):
+    """A level cell of 4096 x 4096 pixels could hold a channel sum of 255 * 2^24 > 2^31 - 1:
+    rapid_set_image refuses it with RAPID_ERANGE before copying anything."""
+    rgb = np.zeros((4096, 4096, 3), np.uint8)
+    with pkg.Context(num_levels=2, ratio_C=4096, init_block=4096, K=1) as ctx:
+        with pytest.raises(pkg.RapidError) as e:
+            ctx.set_image(rgb)
+        assert e.value.status == pkg.RAPID_ERANGE
+    with pkg.Context(num_levels=2, ratio_C=2048, init_block=2048, K=4) as ctx:
+        ctx.set_image(rgb[:2048, :2048]).run()  # 255 * 2^22 fits
+        ctx.sync()
+        assert ctx.state()["M"] == 1  # the first stage has a single 2048-px block
+
+
 def test_barrier_give_up_reports_timeout(pkg):
     """spin_limit_ns = 0: every grid-barrier wait gives up at once; the launch returns,
     the context reports RAPID_ETIMEOUT, and a fresh context still works."""
