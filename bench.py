@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="full grid for every stage")
+    ap.add_argument("--no-graph", action="store_true", help="launch stage by stage instead of a CUDA graph")
     return ap.parse_args()
 
 
@@ -55,17 +57,40 @@ def dist_env():
 
 # ---------------------------------------------------------------- CPU sample (oracle legs)
 def cpu_sample(workload: str):
+    """A bounded sample of the workload for the CPU oracle: a 1024 x 1024 tile of the same
+    generator with the same superpixel size and parameters."""
     from paper_1704_02083_gb300 import synth
-    w = synth.WORKLOADS[workload]
-    frac = (SAMPLE_SIDE * SAMPLE_SIDE) / float(w["H"] * w["W"])
-    side_h, side_w = min(SAMPLE_SIDE, w["H"]), min(SAMPLE_SIDE, w["W"])
-    params = dict(w["params"])
-    params["K"] = max(1, int(round(params["K"] * frac)))
-    cells = max(1, int(round(w["n_cells"] * frac)))
-    img = synth.he_image(side_h, side_w, cells, w["seed"])
-    desc = (f"{side_w}x{side_h} tile of the same generator (seed {w['seed']}, {cells} regions) and parameters "
+    if workload in synth.BATCHES:
+        b = synth.BATCHES[workload]
+        params = dict(b["params"])
+        npx = SAMPLE_SIDE * SAMPLE_SIDE
+        params["K"] = max(1, npx // b["px_per_superpixel"])
+        cells = max(1, npx // b["px_per_cell"])
+        seed = b["seed"]
+        side_h = side_w = SAMPLE_SIDE
+    else:
+        w = synth.WORKLOADS[workload]
+        frac = (SAMPLE_SIDE * SAMPLE_SIDE) / float(w["H"] * w["W"])
+        side_h, side_w = min(SAMPLE_SIDE, w["H"]), min(SAMPLE_SIDE, w["W"])
+        params = dict(w["params"])
+        params["K"] = max(1, int(round(params["K"] * frac)))
+        cells = max(1, int(round(w["n_cells"] * frac)))
+        seed = w["seed"]
+    img = synth.he_image(side_h, side_w, cells, seed)
+    desc = (f"{side_w}x{side_h} tile of the same generator (seed {seed}, {cells} regions) and parameters "
             f"(K={params['K']}, superpixel size and density as the workload), full schedule")
     return img.rgb, params, desc
+
+
+def load_workload(name: str):
+    """Images, per-image K and the common parameters of a workload (one image or a batch)."""
+    from paper_1704_02083_gb300 import synth
+    if name in synth.BATCHES:
+        imgs, K = synth.batch_workload(name)
+        return imgs, K, dict(synth.BATCHES[name]["params"])
+    w = synth.WORKLOADS[name]
+    params = dict(w["params"])
+    return [synth.workload_image(name).rgb], [params.pop("K")], params
 
 
 def time_oracle(rgb, params, reps=1):
@@ -146,15 +171,15 @@ def stage_alg_bytes(H, W, stage_counters, level_factor):
     return 4 * nb * stage_counters.sweeps + 4 * stage_counters.moves + src
 
 
-def kernel_traffic():
+def kernel_traffic(workload: str):
     """Per-launch DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of the finest
-    stage's launch from the committed ncu summary, when it was taken on the current kernel
-    source; else None."""
+    stage's launch on this workload from the committed ncu summary, when it was taken on the
+    current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
     if not os.path.exists(path):
         return None, None
-    d = json.load(open(path))
-    if d.get("kernel_source_sha256") != kernel_source_sha256():
+    d = json.load(open(path)).get(workload)
+    if not d or d.get("kernel_source_sha256") != kernel_source_sha256():
         return None, d
     return d.get("dram_bytes_per_launch"), d
 
@@ -201,7 +226,6 @@ def run_rapid(args, rank, world, local):
 
     import __graft_entry__
     import paper_1704_02083_gb300 as pkg
-    from paper_1704_02083_gb300 import synth
 
     __graft_entry__.build()
     torch.cuda.set_device(local)
@@ -210,31 +234,33 @@ def run_rapid(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w = synth.WORKLOADS[args.workload]
-    H, W = w["H"], w["W"]
-    params = dict(w["params"])
-    img = synth.workload_image(args.workload)
-    stream = torch.cuda.current_stream()
-    rgb_dev = torch.from_numpy(img.rgb).cuda()
+    imgs, Ks, params = load_workload(args.workload)
+    n = len(imgs)
+    sizes = [(int(x.shape[0]), int(x.shape[1])) for x in imgs]
+    npx = sum(h * w for h, w in sizes)
+    stream = torch.cuda.Stream()  # a graph needs a non-default stream
+    torch.cuda.set_stream(stream)
+    dev_imgs = [torch.from_numpy(x).cuda() for x in imgs]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     ctx = pkg.Context(stream=stream, **params)
-    ctx.set_image(rgb_dev)
+    ctx.set_images(dev_imgs, Ks)
+    grids = ctx.autotune() if not args.no_autotune else None
     ctx.set_profiling(True)
+    ctx.set_graph(not args.no_graph)
     for _ in range(args.warmup):
         ctx.run()
     ctx.sync()
-    c0 = ctx.counters()
-    lf = {}
+    c0 = ctx.counters(0)
+    nst = c0.num_stages
     L, C = params["num_levels"], params["ratio_C"]
-    for l in range(1, L + 1):
-        lf[l] = C ** (L - l)
+    lf = {l: C ** (L - l) for l in range(1, L + 1)}
 
     clocks = ClockSampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    step_ms, stage_ms, stage_bytes = [], {}, {}
+    step_ms, stage_ms, stage_bytes = [], [0.0] * nst, [0] * nst
     for _ in range(args.steps):
         flush.zero_()  # L2 flush between steps (outside the timed events)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -244,16 +270,18 @@ def run_rapid(args, rank, world, local):
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        c = ctx.counters()
-        for i in range(c.num_stages):
-            st = c.stage[i]
-            stage_ms[i] = stage_ms.get(i, 0.0) + st.kernel_ms
-            stage_bytes[i] = stage_bytes.get(i, 0) + stage_alg_bytes(H, W, st, lf)
+        for i in range(n):
+            c = ctx.counters(i)
+            for s in range(nst):
+                st = c.stage[s]
+                if i == 0:
+                    stage_ms[s] += st.kernel_ms  # the launch covers every image
+                stage_bytes[s] += stage_alg_bytes(sizes[i][0], sizes[i][1], st, lf)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    c1 = ctx.counters()
+    c1 = ctx.counters(0)
     launches_per_step = (c1.launches - c0.launches) / max(1, args.steps)
 
     total_ms = sum(step_ms)
@@ -261,26 +289,30 @@ def run_rapid(args, rank, world, local):
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    npx = H * W
     value = world * npx * args.steps / (total_ms / 1e3) / 1e6
 
-    # end to end through the C ABI from pinned host memory: H2D image, run, D2H labels + stats
+    # end to end through the C ABI from pinned host memory: H2D images, run, D2H labels + stats
     e2e = None
     if not args.no_e2e:
-        pin = torch.from_numpy(img.rgb).pin_memory()
-        lab_host = torch.empty((H, W), dtype=torch.int32).pin_memory()
-        M = ctx.state()["M"]
-        stats_host = np.zeros(M, pkg.SP_STATS_DTYPE)
+        pins = [torch.from_numpy(x).pin_memory() for x in imgs]
+        labs = [torch.empty(hw, dtype=torch.int32).pin_memory() for hw in sizes]
+        Ms = [ctx.image_info(i)["M"] for i in range(n)]
+        stats_host = [np.zeros(m, pkg.SP_STATS_DTYPE) for m in Ms]
         e2e_ctx = pkg.Context(stream=stream, **params)
+        if grids is not None:
+            e2e_ctx.set_stage_grids(grids)
+        ptrs = [p.data_ptr() for p in pins]
         times = []
-        for i in range(args.warmup + args.steps):
+        for it in range(args.warmup + args.steps):
             torch.cuda.synchronize()
             t = time.perf_counter()
-            pkg.rapid_set_image(e2e_ctx.h, pin.data_ptr(), H, W, 3 * W, 0)
+            pkg.rapid_set_images(e2e_ctx.h, ptrs, [h for h, _ in sizes], [w for _, w in sizes],
+                                 [3 * w for _, w in sizes], Ks, 0)
             pkg.rapid_run(e2e_ctx.h)
-            pkg.rapid_read_labels(e2e_ctx.h, lab_host.data_ptr(), 4 * W, 0)
-            pkg.rapid_read_stats(e2e_ctx.h, stats_host.ctypes.data, M)
-            if i >= args.warmup:
+            for i in range(n):
+                pkg.rapid_read_image_labels(e2e_ctx.h, i, labs[i].data_ptr(), 4 * sizes[i][1], 0)
+                pkg.rapid_read_image_stats(e2e_ctx.h, i, stats_host[i].ctypes.data, Ms[i])
+            if it >= args.warmup:
                 times.append(time.perf_counter() - t)
         e2e_ctx.close()
         tot = sum(times)
@@ -288,8 +320,8 @@ def run_rapid(args, rank, world, local):
             t = torch.tensor([tot], dtype=torch.float64, device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             tot = float(t.item())
-        e2e = {"value": world * npx * len(times) / tot / 1e6, "unit": UNIT,
-               "h2d_bytes_per_step": 3 * npx, "d2h_bytes_per_step": 4 * npx + M * pkg.SP_STATS_DTYPE.itemsize}
+        e2e = {"value": world * npx * len(times) / tot / 1e6, "unit": UNIT, "h2d_bytes_per_step": 3 * npx,
+               "d2h_bytes_per_step": 4 * npx + sum(Ms) * pkg.SP_STATS_DTYPE.itemsize}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -301,31 +333,36 @@ def run_rapid(args, rank, world, local):
     # roofline of the dominant launch: the stage launch with the largest device time (the
     # finest stage); its duration from CUDA events around each stage launch on ``stream``
     peak, peak_kind = measured_peak()
-    dom = max(stage_ms, key=stage_ms.get)
+    dom = max(range(nst), key=lambda s: stage_ms[s])
     launch_ms = stage_ms[dom] / args.steps
     launch_bytes = stage_bytes[dom] / args.steps
     achieved = launch_bytes / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else None
-    all_ms, all_bytes = sum(stage_ms.values()), sum(stage_bytes.values())
+    all_ms, all_bytes = sum(stage_ms), sum(stage_bytes)
     all_achieved = all_bytes / (all_ms / 1e3) / 1e9 if all_ms > 0 else None
-    traffic, _ = kernel_traffic()
+    traffic, _ = kernel_traffic(args.workload)
     st_dom = c1.stage[dom]
     if rank == 0:
+        cfg = {"workload": args.workload, "images": n, "pixels": npx, "K_total": int(sum(Ks)),
+               "M_total": int(sum(ctx.image_info(i)["M"] for i in range(n))),
+               "levels": params["num_levels"], "ratio_C": params["ratio_C"], "init_block": params["init_block"],
+               "final_grain": params["final_grain"], "size_mode": params["size_mode"],
+               "predict": params["predict"], "reuse": params["reuse"],
+               "stage_grids": grids[:nst] if grids is not None else None, "cuda_graph": not args.no_graph,
+               "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
+               "parallelism": f"replicas x{world}"}
+        if n == 1:
+            cfg.update({"H": sizes[0][0], "W": sizes[0][1]})
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "H": H, "W": W, "K": params["K"], "M": c1.M,
-                       "levels": params["num_levels"], "ratio_C": params["ratio_C"],
-                       "init_block": params["init_block"], "final_grain": params["final_grain"],
-                       "size_mode": params["size_mode"], "predict": params["predict"], "reuse": params["reuse"],
-                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
-                       "parallelism": f"replicas x{world}"},
+            "config": cfg,
             "roofline": {"kernel": f"stage_kernel, stage {dom} (level {st_dom.level}, block side {st_dom.block})",
                          "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
                          "traffic": traffic, "alg_bytes_per_launch": launch_bytes, "launch_ms": launch_ms,
                          "share_of_step": launch_ms / (total_ms / args.steps),
-                         "all_stage_launches": {"launches_per_step": len(stage_ms),
+                         "all_stage_launches": {"launches_per_step": nst,
                                                 "ms_per_step": all_ms / args.steps,
                                                 "alg_bytes_per_step": all_bytes / args.steps,
                                                 "achieved": all_achieved,

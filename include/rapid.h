@@ -167,9 +167,59 @@ rapid_status rapid_refine_stage(rapid_ctx *ctx, int32_t *sweeps_out, int64_t *mo
  * stage. */
 rapid_status rapid_split(rapid_ctx *ctx);
 
-/* The whole schedule on the context's image: level images, seeding, then refine / split
- * through every stage.  Enqueue only; a later synchronising call reports errors. */
+/* The whole schedule on the context's image(s): level images, seeding, then refine / split
+ * through every stage.  Enqueue only; a later synchronising call reports errors.  With
+ * graph mode on (rapid_set_graph) the first call captures these launches into a CUDA
+ * graph and every call launches that graph. */
 rapid_status rapid_run(rapid_ctx *ctx);
+
+/* ---- Batches: many images refined together (the data partitioning of Sec. 3.3) ----
+ * A context may hold up to RAPID_MAX_BATCH images of any sizes.  Every stage then refines
+ * all of them in one persistent launch; each image keeps its own block grid, seed grid
+ * (from its own K), lambda_pos and sweep count (an image stops sweeping a stage after its
+ * own sweep without change), so each image's labels, statistics and counters are exactly
+ * those of refining it alone with the same parameters.  The single-image calls above act
+ * on image 0. */
+#define RAPID_MAX_BATCH 64
+
+/* Copy n images into the context (replacing any previous ones).  rgb[i]: H[i] x W[i]
+ * interleaved RGB, host or device (rgb_is_device), rows row_pitch_bytes[i] apart (>= 3 W[i]).
+ * K: requested superpixels per image (NULL = params.K for all).  The caller keeps
+ * ownership; host input is copied before the call returns.  EINVAL as for
+ * rapid_set_image (per image) or n < 1; ERANGE for n > RAPID_MAX_BATCH, an overflowing
+ * level sum, or more than 2^31 - 1 blocks or labels over the batch; ENOMEM, ECUDA. */
+rapid_status rapid_set_images(rapid_ctx *ctx, int32_t n, const uint8_t *const *rgb, const int32_t *H,
+                              const int32_t *W, const int64_t *row_pitch_bytes, const int32_t *K,
+                              int32_t rgb_is_device);
+
+/* Size and superpixel count M of image i (any pointer may be NULL).  EINVAL for a bad i. */
+rapid_status rapid_get_image_info(rapid_ctx *ctx, int32_t i, int32_t *H, int32_t *W, int32_t *M);
+
+/* Image i's full-resolution label map (ids 0 .. M_i - 1, layout as rapid_read_labels),
+ * statistics (as rapid_read_stats) and per-stage counters (as rapid_read_counters; the
+ * section times and kernel_ms are those of the whole launch).  All synchronise. */
+rapid_status rapid_read_image_labels(rapid_ctx *ctx, int32_t i, int32_t *dst, int64_t row_pitch_bytes,
+                                     int32_t dst_is_device);
+rapid_status rapid_read_image_stats(rapid_ctx *ctx, int32_t i, rapid_sp_stats *dst, int64_t capacity,
+                                    int64_t *M_out);
+rapid_status rapid_read_image_counters(rapid_ctx *ctx, int32_t i, rapid_counters *dst);
+
+/* Launch geometry.  Results never depend on it (a phase's decisions are independent and
+ * merges are ordered by block index), only the time does.  rapid_set_stage_grids: CTAs of
+ * each stage's launch for stages 0 .. n-1 (0 = the full co-resident grid, larger values are
+ * capped to it; the others reset to 0).  rapid_autotune: time the whole schedule on the
+ * context's current images once per candidate grid (the full grid, then halvings down to
+ * one CTA), keep per stage the fastest, and write them to grids_out (RAPID_MAX_STAGES
+ * entries, may be NULL).  Synchronises; the context's results afterwards are those of a
+ * normal run.  EINVAL on a negative grid, ESTATE without images. */
+rapid_status rapid_set_stage_grids(rapid_ctx *ctx, const int32_t *grids, int32_t n);
+rapid_status rapid_autotune(rapid_ctx *ctx, int32_t *grids_out);
+
+/* Graph mode (0 = off, the default): rapid_run captures the schedule into a CUDA graph on
+ * its first call after rapid_set_images and replays it afterwards (profiling events are
+ * captured as event-record nodes, so kernel_ms keeps working).  Needs a non-default stream
+ * (EINVAL with stream 0). */
+rapid_status rapid_set_graph(rapid_ctx *ctx, int32_t on);
 
 /* Current position in the schedule: stage index (-1 before seeding), its level and block
  * side, and M.  Host-side only (no synchronisation).  Any pointer may be NULL. */

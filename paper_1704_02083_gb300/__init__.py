@@ -97,6 +97,14 @@ def lib() -> C.CDLL:
         "rapid_sync": (i32, [P]),
         "rapid_simple_table": (i32, [P]),
         "rapid_run_static": (i32, [C.POINTER(rapid_params), P, i32, i32, i64, P, i64, P, i64, pi32, P]),
+        "rapid_set_images": (i32, [P, i32, C.POINTER(P), pi32, pi32, pi64, pi32, i32]),
+        "rapid_get_image_info": (i32, [P, i32, pi32, pi32, pi32]),
+        "rapid_read_image_labels": (i32, [P, i32, P, i64, i32]),
+        "rapid_read_image_stats": (i32, [P, i32, P, i64, pi64]),
+        "rapid_read_image_counters": (i32, [P, i32, C.POINTER(rapid_counters)]),
+        "rapid_set_graph": (i32, [P, i32]),
+        "rapid_set_stage_grids": (i32, [P, pi32, i32]),
+        "rapid_autotune": (i32, [P, pi32]),
         "rapid_status_string": (C.c_char_p, [i32]),
         "rapid_destroy": (None, [P]),
     }
@@ -190,6 +198,60 @@ def rapid_read_counters(ctx: int) -> rapid_counters:
     return c
 
 
+RAPID_MAX_BATCH = 64
+
+
+def rapid_set_images(ctx: int, rgb_ptrs, H, W, row_pitch_bytes, K, rgb_is_device: int):
+    """n images at once (pointer, height, width, row pitch per image; K per image or None)."""
+    n = len(rgb_ptrs)
+    ptrs = (C.c_void_p * n)(*rgb_ptrs)
+    h = (C.c_int32 * n)(*H)
+    w = (C.c_int32 * n)(*W)
+    pitch = (C.c_int64 * n)(*row_pitch_bytes)
+    k = (C.c_int32 * n)(*K) if K is not None else None
+    _check(lib().rapid_set_images(ctx, n, ptrs, h, w, pitch, k, rgb_is_device), "rapid_set_images")
+
+
+def rapid_get_image_info(ctx: int, i: int):
+    v = [C.c_int32() for _ in range(3)]
+    _check(lib().rapid_get_image_info(ctx, i, *[C.byref(x) for x in v]), "rapid_get_image_info")
+    return dict(zip(("H", "W", "M"), [x.value for x in v]))
+
+
+def rapid_read_image_labels(ctx: int, i: int, dst_ptr: int, row_pitch_bytes: int, dst_is_device: int):
+    _check(lib().rapid_read_image_labels(ctx, i, dst_ptr, row_pitch_bytes, dst_is_device),
+           "rapid_read_image_labels")
+
+
+def rapid_read_image_stats(ctx: int, i: int, dst_ptr: int, capacity: int) -> int:
+    M = C.c_int64()
+    _check(lib().rapid_read_image_stats(ctx, i, dst_ptr, capacity, C.byref(M)), "rapid_read_image_stats")
+    return M.value
+
+
+def rapid_read_image_counters(ctx: int, i: int) -> rapid_counters:
+    c = rapid_counters()
+    _check(lib().rapid_read_image_counters(ctx, i, C.byref(c)), "rapid_read_image_counters")
+    return c
+
+
+def rapid_set_graph(ctx: int, on: bool):
+    _check(lib().rapid_set_graph(ctx, 1 if on else 0), "rapid_set_graph")
+
+
+def rapid_set_stage_grids(ctx: int, grids):
+    n = len(grids)
+    arr = (C.c_int32 * max(1, n))(*grids)
+    _check(lib().rapid_set_stage_grids(ctx, arr, n), "rapid_set_stage_grids")
+
+
+def rapid_autotune(ctx: int):
+    """Per-stage grid sizes chosen by timing (RAPID_MAX_STAGES entries)."""
+    out = (C.c_int32 * RAPID_MAX_STAGES)()
+    _check(lib().rapid_autotune(ctx, out), "rapid_autotune")
+    return list(out)
+
+
 def rapid_set_profiling(ctx: int, on: bool):
     _check(lib().rapid_set_profiling(ctx, 1 if on else 0), "rapid_set_profiling")
 
@@ -277,6 +339,7 @@ class Context:
             H, W = int(rgb.shape[0]), int(rgb.shape[1])
             rapid_set_image(self.h, rgb.data_ptr(), H, W, rgb.stride(0), 1)
         self.H, self.W = int(H), int(W)
+        self.sizes = [(self.H, self.W)]
         return self
 
     def seed(self) -> int:
@@ -317,13 +380,13 @@ class Context:
         rapid_read_stats(self.h, a.ctypes.data, a.size)
         return a[:M]
 
-    def counters(self) -> rapid_counters:
-        return rapid_read_counters(self.h)
+    def counters(self, i: int = 0) -> rapid_counters:
+        return rapid_read_image_counters(self.h, i)
 
-    def counters_array(self) -> np.ndarray:
+    def counters_array(self, i: int = 0) -> np.ndarray:
         """num_stages x 8 int64: level, block, sweeps, eligible, evaluated, moves, merge
         requests, merges (the oracle's counter layout)."""
-        c = self.counters()
+        c = self.counters(i)
         rows = []
         for i in range(c.num_stages):
             s = c.stage[i]
@@ -332,6 +395,63 @@ class Context:
 
     def set_profiling(self, on: bool = True):
         rapid_set_profiling(self.h, on)
+
+    # ---- batches (rapid_set_images): image i's results
+    def set_images(self, images, K=None):
+        """A batch: a list of numpy H x W x 3 uint8 arrays (host copies) or of CUDA uint8
+        tensors of that shape (device copies); K: superpixels per image (None: params.K)."""
+        if len(images) == 0:
+            raise ValueError("empty batch")
+        on_device = not isinstance(images[0], np.ndarray)
+        ptrs, H, W, pitch, keep = [], [], [], [], []
+        for rgb in images:
+            if isinstance(rgb, np.ndarray):
+                if on_device:
+                    raise ValueError("mixed host and device images")
+                rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
+                if rgb.ndim != 3 or rgb.shape[2] != 3:
+                    raise ValueError("expected H x W x 3 uint8")
+                ptrs.append(rgb.ctypes.data)
+                pitch.append(rgb.strides[0])
+            else:
+                if not on_device or str(rgb.dtype) != "torch.uint8" or rgb.dim() != 3 or rgb.shape[2] != 3 \
+                        or not rgb.is_cuda or rgb.stride(2) != 1 or rgb.stride(1) != 3:
+                    raise ValueError("expected CUDA uint8 tensors of shape H x W x 3 with interleaved rows")
+                ptrs.append(rgb.data_ptr())
+                pitch.append(rgb.stride(0))
+            keep.append(rgb)
+            H.append(int(rgb.shape[0]))
+            W.append(int(rgb.shape[1]))
+        rapid_set_images(self.h, ptrs, H, W, pitch, None if K is None else [int(k) for k in K],
+                         1 if on_device else 0)
+        self.sizes = list(zip(H, W))
+        self.H, self.W = self.sizes[0]
+        return self
+
+    def image_info(self, i: int):
+        return rapid_get_image_info(self.h, i)
+
+    def image_labels(self, i: int) -> np.ndarray:
+        H, W = self.sizes[i]
+        a = np.empty((H, W), np.int32)
+        rapid_read_image_labels(self.h, i, a.ctypes.data, a.strides[0], 0)
+        return a
+
+    def image_stats(self, i: int) -> np.ndarray:
+        M = self.image_info(i)["M"]
+        a = np.zeros(max(M, 1), SP_STATS_DTYPE)
+        rapid_read_image_stats(self.h, i, a.ctypes.data, a.size)
+        return a[:M]
+
+    def set_graph(self, on: bool = True):
+        rapid_set_graph(self.h, on)
+
+    def set_stage_grids(self, grids):
+        rapid_set_stage_grids(self.h, grids)
+
+    def autotune(self):
+        """Time the schedule at several grid sizes and keep the fastest per stage."""
+        return rapid_autotune(self.h)[:max(1, self.counters().num_stages)]
 
     def sync(self):
         rapid_sync(self.h)

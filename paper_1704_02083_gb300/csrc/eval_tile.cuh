@@ -62,8 +62,8 @@ __device__ __forceinline__ bool win_label_changed(const WarpTile &W, int k) {
 // smaller label, a move only on a strict decrease).  The candidates are visited once,
 // keeping the best one's interval, the smallest lower bound among the others and the
 // largest magnitude seen.
-__device__ __forceinline__ int decide(const StageArgs &a, const BlockIn &in, Local &lc) {
-  if (!a.use_filter) return decide_f64(a, in);
+__device__ __forceinline__ int decide(const StageArgs &a, const ImageDesc &im, const BlockIn &in, Local &lc) {
+  if (!im.use_filter) return decide_f64(a, in, im.lam_pos);
   const DevStats &s = a.st;
   const BlockSums &bs = in.bs;
   const int lbl = in.lbl;
@@ -72,7 +72,7 @@ __device__ __forceinline__ int decide(const StageArgs &a, const BlockIn &in, Loc
   const float x2f = (float)(2 * bs.x), y2f = (float)(2 * bs.y);
   const float pbx = (float)in.x0 + 0.5f * (float)(bs.bw - 1);  // P_x / w, exact
   const float pby = (float)in.y0 + 0.5f * (float)(bs.bh - 1);
-  const float lamf = a.lam_pos_f, lamb2f = a.lam_b2_f;
+  const float lamf = im.lam_pos_f, lamb2f = a.lam_b2_f;
   const float rlam = 1.0001f * kU * lamf, rlamb = 1.0001f * kU * lamb2f;  // |float - binary64| weights
   const float4 ha = s.fhi[lbl], la = s.flo[lbl];
   const float2 ya = s.fy[lbl];
@@ -138,10 +138,10 @@ __device__ __forceinline__ int decide(const StageArgs &a, const BlockIn &in, Loc
   }
   if (result == -2) {
     lc.fallback++;
-    return decide_f64(a, in);
+    return decide_f64(a, in, im.lam_pos);
   }
   if (a.verify_filter) {
-    const int ref = decide_f64(a, in);
+    const int ref = decide_f64(a, in, im.lam_pos);
     if (ref != result) {
       lc.mismatch++;
       return ref;
@@ -192,8 +192,8 @@ __device__ __forceinline__ bool block_needs_decision(const StageArgs &a, const W
 
 // Pass 2 (one compacted block per lane): block sums, the decision (Eq. operation), the size
 // term (Sec. 3.1) and the move.
-__device__ __forceinline__ void decide_block(const StageArgs &a, WarpTile &W, int c, int j, int bx, int by, int g,
-                                             Local &lc) {
+__device__ __forceinline__ void decide_block(const StageArgs &a, const ImageDesc &im, WarpTile &W, int c, int j, int bx,
+                                             int by, int g, Local &lc) {
   const int *win = W.win;
   const DevStats &s = a.st;
   BlockIn in;
@@ -202,18 +202,18 @@ __device__ __forceinline__ void decide_block(const StageArgs &a, WarpTile &W, in
   in.nb[1] = win[c - 1];
   in.nb[2] = win[c + 1];
   in.nb[3] = win[c + kWinW];
-  in.bs = block_sums(a, bx, by);
+  in.bs = block_sums(a, im, bx, by);
   in.x0 = bx * a.side;
   in.y0 = by * a.side;
   const int lbl = in.lbl;
-  const int k = decide(a, in, lc);
+  const int k = decide(a, im, in, lc);
   if (k < 0) return;
-  const long long idx = (long long)by * a.nbx + bx;
+  const long long idx = (long long)by * im.nbx + bx;
   if (a.size_mode != 0 && (long long)a.lo_den * (s.N[lbl] - in.bs.w) < (long long)a.lo_num * s.init[lbl]) {
     if (a.size_mode == 2) {
       lc.req++;
       atomicOr(&W.req[j >> 5], 1u << (j & 31));
-      atomicMin(&a.mg.req_min[lbl], (int)idx);
+      atomicMin(&a.mg.req_min[lbl], im.blk0 + (int)idx);  // global block order
       if (atomicExch(&a.mg.req_flag[lbl], 1) == 0) {
         const int slot = atomicAdd(a.mg.req_count + (g & 1), 1);
         a.mg.req_list[slot] = lbl;
@@ -223,7 +223,7 @@ __device__ __forceinline__ void decide_block(const StageArgs &a, WarpTile &W, in
   }
   // Move: relabel in place, accumulate the exact deltas of both labels.
   const BlockSums &bs = in.bs;
-  a.lab[idx] = k;
+  im.lab[idx] = k;
   atomic_add_i64(&s.dN[lbl], -bs.w);
   atomic_add_i64(&s.dR[lbl], -bs.r);
   atomic_add_i64(&s.dG[lbl], -bs.g);
@@ -272,31 +272,70 @@ __device__ __forceinline__ void set_insert(int *set, int cap, int v, int *over) 
 }
 
 // ---------------------------------------------------------------- one phase
-// g: 1-based phase number within the launch.
-// CTA b owns the tiles b, b + grid, b + 2 grid, ... (spread over the image); its warps draw
-// them one at a time from a shared-memory counter, the next draw issued before the current
-// tile is processed.
-__device__ void eval_phase(const StageArgs &a, WarpTile *wts, int *s_draw, int phase, int g,
-                           unsigned long long *changes) {
+// Counters of one warp's run of tiles of one image, added to the image's counters at once.
+__device__ __forceinline__ void flush_counts(const StageArgs &a, int ii, int slot, Local &lc, int &scanned,
+                                             int &skipped) {
+  const int lane = threadIdx.x & 31;
+  const int e = warp_sum(lc.elig), v = warp_sum(lc.eval), m = warp_sum(lc.moves), r = warp_sum(lc.req);
+  const int fb = warp_sum(lc.fallback), mm = warp_sum(lc.mismatch);
+  const int sc = warp_sum(scanned), sk = warp_sum(skipped);
+  if (lane == 0 && ii >= 0) {
+    long long *cnt = a.ctl.cnt + (long long)ii * kCntStride;
+    if (e) atomic_add_i64(&cnt[CNT_ELIG], e);
+    if (v) atomic_add_i64(&cnt[CNT_EVAL], v);
+    if (m) {
+      atomic_add_i64(&cnt[CNT_MOVES], m);
+      atomicAdd(&a.ctl.changes[3 * ii + slot], (unsigned long long)m);
+    }
+    if (r) atomic_add_i64(&cnt[CNT_REQ], r);
+    if (fb) atomic_add_i64(&cnt[CNT_FALLBACK], fb);
+    if (mm) atomic_add_i64(&cnt[CNT_MISMATCH], mm);
+    if (sc) atomic_add_i64(&cnt[CNT_SCANNED], sc);
+    if (sk) atomic_add_i64(&cnt[CNT_SKIPPED], sk);
+  }
+  lc = Local{0, 0, 0, 0, 0, 0};
+  scanned = skipped = 0;
+}
+
+// g: 1-based phase number within the launch; slot: the sweep's change-count slot.  imgs,
+// tile0 and active are the CTA's shared copies of the images, their first tiles and
+// whether each still refines in this stage.
+template <bool kBatch>
+__device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *imgs, const int *tile0,
+                                           const unsigned char *active, WarpTile *wts, int *s_draw, int phase,
+                                           int g, int slot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpTile &W = wts[warp];
   const int py = phase / 3, px = phase % 3;
-  const int ntiles = a.ntx * a.nty;
   if (threadIdx.x == 0) *s_draw = 0;
   __syncthreads();
   int draw = 0;
   if (lane == 0) draw = atomicAdd(s_draw, 1);
   draw = __shfl_sync(0xffffffffu, draw, 0);
   Local lc = {0, 0, 0, 0, 0, 0};
-  int scanned = 0, skipped = 0;
+  int scanned = 0, skipped = 0, cur = -1;
   for (;;) {
     const long long tt = (long long)blockIdx.x + (long long)draw * gridDim.x;
-    if (tt >= ntiles) break;
+    if (tt >= a.ntiles) break;
     const int t = (int)tt;
     int nxt = 0;
     if (lane == 0) nxt = atomicAdd(s_draw, 1);
     draw = __shfl_sync(0xffffffffu, nxt, 0);  // used by the next iteration
-    const int tx = t % a.ntx, ty = t / a.ntx;
+    // the tile's image: the last one whose first tile is <= t (a warp's tiles only go up)
+    int lo = cur < 0 ? 0 : cur, hi = kBatch ? a.nimg - 1 : 0;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile0[mid] <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    if (lo != cur) {
+      flush_counts(a, cur, slot, lc, scanned, skipped);
+      cur = lo;
+    }
+    if (!active[cur]) continue;  // the image finished this stage
+    const ImageDesc &im = kBatch ? imgs[cur] : a.img0;
+    const int lt = t - im.tile0;
+    const int tx = lt % im.ntx, ty = lt / im.ntx;
     const int bx0 = tx * kTileW, by0 = ty * kTileH;
     int *rec = a.trec + ((long long)t * 9 + phase) * kRecInts;
     const int rv = lane < kRecInts ? rec[lane] : 0;
@@ -331,12 +370,12 @@ __device__ void eval_phase(const StageArgs &a, WarpTile *wts, int *s_draw, int p
     // run of equal labels down a column goes into the table
     for (int col = lane; col < kWinW; col += 32) {
       const int gx = bx0 - 1 + col;
-      const bool inx = gx >= 0 && gx < a.nbx;
+      const bool inx = gx >= 0 && gx < im.nbx;
       int vals[kWinH];
 #pragma unroll
       for (int wy = 0; wy < kWinH; wy++) {
         const int gy = by0 - 1 + wy;
-        vals[wy] = (inx && gy >= 0 && gy < a.nby) ? a.lab[(long long)gy * a.nbx + gx] : -1;
+        vals[wy] = (inx && gy >= 0 && gy < im.nby) ? im.lab[(long long)gy * im.nbx + gx] : -1;
       }
       int prev = -2;
 #pragma unroll
@@ -350,7 +389,7 @@ __device__ void eval_phase(const StageArgs &a, WarpTile *wts, int *s_draw, int p
     }
     // the tile's blocks of this phase class
     const int lx0 = ((px - bx0) % 3 + 3) % 3, ly0 = ((py - by0) % 3 + 3) % 3;
-    const int tw = min(kTileW, a.nbx - bx0), th = min(kTileH, a.nby - by0);
+    const int tw = min(kTileW, im.nbx - bx0), th = min(kTileH, im.nby - by0);
     const int nx = tw > lx0 ? (tw - lx0 + 2) / 3 : 0, ny = th > ly0 ? (th - ly0 + 2) / 3 : 0;
     __syncwarp();
     // which of the window's labels changed since the previous scan of this tile and class
@@ -377,7 +416,7 @@ __device__ void eval_phase(const StageArgs &a, WarpTile *wts, int *s_draw, int p
     for (int it = lane; it < nitems; it += 32) {
       const int j = W.items[it];
       const int lx = lx0 + 3 * (j % nx), ly = ly0 + 3 * (j / nx);
-      decide_block(a, W, (ly + 1) * kWinW + (lx + 1), j, bx0 + lx, by0 + ly, g, lc);
+      decide_block(a, im, W, (ly + 1) * kWinW + (lx + 1), j, bx0 + lx, by0 + ly, g, lc);
     }
     const int de = warp_sum(lc.elig - e0), dv = warp_sum(lc.eval - v0);
     __syncwarp();
@@ -396,21 +435,5 @@ __device__ void eval_phase(const StageArgs &a, WarpTile *wts, int *s_draw, int p
     }
     __syncwarp();
   }
-  const int e = warp_sum(lc.elig), v = warp_sum(lc.eval), m = warp_sum(lc.moves), r = warp_sum(lc.req);
-  const int fb = warp_sum(lc.fallback), mm = warp_sum(lc.mismatch);
-  const int sc = warp_sum(scanned), sk = warp_sum(skipped);
-
-  if (lane == 0) {
-    if (e) atomic_add_i64(&a.ctl.cnt[CNT_ELIG], e);
-    if (v) atomic_add_i64(&a.ctl.cnt[CNT_EVAL], v);
-    if (m) {
-      atomic_add_i64(&a.ctl.cnt[CNT_MOVES], m);
-      atomicAdd(changes, (unsigned long long)m);
-    }
-    if (r) atomic_add_i64(&a.ctl.cnt[CNT_REQ], r);
-    if (fb) atomic_add_i64(&a.ctl.cnt[CNT_FALLBACK], fb);
-    if (mm) atomic_add_i64(&a.ctl.cnt[CNT_MISMATCH], mm);
-    if (sc) atomic_add_i64(&a.ctl.cnt[CNT_SCANNED], sc);
-    if (sk) atomic_add_i64(&a.ctl.cnt[CNT_SKIPPED], sk);
-  }
+  flush_counts(a, cur, slot, lc, scanned, skipped);
 }

@@ -39,13 +39,13 @@ cudaError_t launch_pyramid(const unsigned char *img, long long pitch, int H, int
 // Regular seed grid (Algorithm RAPID): block (bx, by) of the first stage gets label
 // floor(by gy / nby) gx + floor(bx gx / nbx); its sums go to S and its rectangle to the
 // label's bounding box.
-__global__ void seed_kernel(StageArgs a, int gx, int gy) {
+__global__ void seed_kernel(StageArgs a, ImageDesc im, int gx, int gy) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)a.nbx * a.nby) return;
-  const int bx = (int)(i % a.nbx), by = (int)(i / a.nbx);
-  const int lbl = (int)(((long long)by * gy / a.nby) * gx + ((long long)bx * gx / a.nbx));
-  a.lab[i] = lbl;
-  const BlockSums bs = block_sums(a, bx, by);
+  if (i >= (long long)im.nbx * im.nby) return;
+  const int bx = (int)(i % im.nbx), by = (int)(i / im.nbx);
+  const int lbl = im.label0 + (int)(((long long)by * gy / im.nby) * gx + ((long long)bx * gx / im.nbx));
+  im.lab[i] = lbl;
+  const BlockSums bs = block_sums(a, im, bx, by);
   atomic_add_i64(&a.st.N[lbl], bs.w);
   atomic_add_i64(&a.st.R[lbl], bs.r);
   atomic_add_i64(&a.st.G[lbl], bs.g);
@@ -79,12 +79,17 @@ __global__ void init_size_kernel(DevStats st) {
   if (k < st.M) st.init[k] = st.N[k];
 }
 
-cudaError_t launch_seed(const StageArgs &a, int gx, int gy, cudaStream_t s, int *launches) {
+// Seeding of a batch: every label cleared, each image's grid (gx[i] x gy[i] labels from
+// its label0) with its sums, then InitSize = N.  ims: host copies of the stage-0 images.
+cudaError_t launch_seed(const StageArgs &a, const ImageDesc *ims, const int *gx, const int *gy, int n,
+                        cudaStream_t s, int *launches) {
   reset_labels_kernel<<<blocks_for(a.st.M, 256), 256, 0, s>>>(a.st, a.mg);
-  const long long n = (long long)a.nbx * a.nby;
-  seed_kernel<<<blocks_for(n, 256), 256, 0, s>>>(a, gx, gy);
+  for (int i = 0; i < n; i++) {
+    const long long nb = (long long)ims[i].nbx * ims[i].nby;
+    seed_kernel<<<blocks_for(nb, 256), 256, 0, s>>>(a, ims[i], gx[i], gy[i]);
+  }
   init_size_kernel<<<blocks_for(a.st.M, 256), 256, 0, s>>>(a.st);
-  *launches += 3;
+  *launches += 2 + n;
   return cudaGetLastError();
 }
 
@@ -95,12 +100,12 @@ __global__ void zero_stats_kernel(DevStats st) {
   if (k < st.M) st.N[k] = st.R[k] = st.G[k] = st.B[k] = st.X[k] = st.Y[k] = 0;
 }
 
-__global__ void accumulate_stats_kernel(StageArgs a) {
+__global__ void accumulate_stats_kernel(StageArgs a, ImageDesc im) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)a.nbx * a.nby) return;
-  const int bx = (int)(i % a.nbx), by = (int)(i / a.nbx);
-  const int lbl = a.lab[i];
-  const BlockSums bs = block_sums(a, bx, by);
+  if (i >= (long long)im.nbx * im.nby) return;
+  const int bx = (int)(i % im.nbx), by = (int)(i / im.nbx);
+  const int lbl = im.lab[i];
+  const BlockSums bs = block_sums(a, im, bx, by);
   atomic_add_i64(&a.st.N[lbl], bs.w);
   atomic_add_i64(&a.st.R[lbl], bs.r);
   atomic_add_i64(&a.st.G[lbl], bs.g);
@@ -109,10 +114,11 @@ __global__ void accumulate_stats_kernel(StageArgs a) {
   atomic_add_i64(&a.st.Y[lbl], bs.y);
 }
 
-cudaError_t launch_recompute(const StageArgs &a, cudaStream_t s, int *launches) {
+cudaError_t launch_recompute(const StageArgs &a, const ImageDesc *ims, int n, cudaStream_t s, int *launches) {
   zero_stats_kernel<<<blocks_for(a.st.M, 256), 256, 0, s>>>(a.st);
-  accumulate_stats_kernel<<<blocks_for((long long)a.nbx * a.nby, 256), 256, 0, s>>>(a);
-  *launches += 2;
+  for (int i = 0; i < n; i++)
+    accumulate_stats_kernel<<<blocks_for((long long)ims[i].nbx * ims[i].nby, 256), 256, 0, s>>>(a, ims[i]);
+  *launches += 1 + n;
   return cudaGetLastError();
 }
 
@@ -161,31 +167,37 @@ __global__ void importance_kernel(const int *lab, int nbx, int nby, DevStats st)
   }
 }
 
-cudaError_t launch_predict(const int *lab, int nbx, int nby, const DevStats &st, long long hT, cudaStream_t s,
+cudaError_t launch_predict(const ImageDesc *ims, int n, const DevStats &st, long long hT, cudaStream_t s,
                            int *launches) {
   classify_kernel<<<blocks_for(st.M, 256), 256, 0, s>>>(st, hT);
-  importance_kernel<<<blocks_for((long long)nbx * nby, 256), 256, 0, s>>>(lab, nbx, nby, st);
-  *launches += 2;
+  for (int i = 0; i < n; i++)
+    importance_kernel<<<blocks_for((long long)ims[i].nbx * ims[i].nby, 256), 256, 0, s>>>(ims[i].lab, ims[i].nbx,
+                                                                                           ims[i].nby, st);
+  *launches += 1 + n;
   return cudaGetLastError();
 }
 
-// Full-resolution label map from a block-resolution one.
-__global__ void upsample_kernel(const int *lab, int nbx, int side, int H, int W, int *dst, long long pitch_elems) {
+// Full-resolution label map from a block-resolution one, as image-local ids (global id -
+// label0).
+__global__ void upsample_kernel(const int *lab, int nbx, int side, int H, int W, int label0, int *dst,
+                                long long pitch_elems) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long long)H * W) return;
   const int x = (int)(i % W), y = (int)(i / W);
-  dst[(long long)y * pitch_elems + x] = lab[(long long)(y / side) * nbx + x / side];
+  dst[(long long)y * pitch_elems + x] = lab[(long long)(y / side) * nbx + x / side] - label0;
 }
 
-cudaError_t launch_upsample(const int *lab, int nbx, int side, int H, int W, int *dst, long long pitch_elems,
-                            cudaStream_t s) {
-  upsample_kernel<<<blocks_for((long long)H * W, 256), 256, 0, s>>>(lab, nbx, side, H, W, dst, pitch_elems);
+cudaError_t launch_upsample(const int *lab, int nbx, int side, int H, int W, int label0, int *dst,
+                            long long pitch_elems, cudaStream_t s) {
+  upsample_kernel<<<blocks_for((long long)H * W, 256), 256, 0, s>>>(lab, nbx, side, H, W, label0, dst, pitch_elems);
   return cudaGetLastError();
 }
 
-__global__ void pack_stats_kernel(DevStats st, rapid_sp_stats *out) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= st.M) return;
+// rapid_sp_stats records of the labels label0 .. label0 + M - 1 (entry k - label0).
+__global__ void pack_stats_kernel(DevStats st, int label0, int M, rapid_sp_stats *out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const int k = label0 + j;
   rapid_sp_stats v;
   v.n = st.N[k];
   v.sum_r = st.R[k];
@@ -196,26 +208,29 @@ __global__ void pack_stats_kernel(DevStats st, rapid_sp_stats *out) {
   v.init_size = st.init[k];
   v.y = st.y[k];
   v.important = st.imp[k];
-  out[k] = v;
+  out[j] = v;
 }
 
-cudaError_t launch_pack_stats(const DevStats &st, rapid_sp_stats *out, cudaStream_t s) {
-  pack_stats_kernel<<<blocks_for(st.M, 256), 256, 0, s>>>(st, out);
+cudaError_t launch_pack_stats(const DevStats &st, int label0, int M, rapid_sp_stats *out, cudaStream_t s) {
+  pack_stats_kernel<<<blocks_for(M, 256), 256, 0, s>>>(st, label0, M, out);
   return cudaGetLastError();
 }
 
-__global__ void init_counters_kernel(long long *cnt, Schedule sch) {
-  const int i = threadIdx.x;
-  if (i >= RAPID_MAX_STAGES) return;
-  for (int j = 0; j < CNT_N; j++) cnt[i * CNT_N + j] = 0;
-  if (i < sch.n) {
-    cnt[i * CNT_N + CNT_LEVEL] = sch.level[i];
-    cnt[i * CNT_N + CNT_SIDE] = sch.side[i];
+// Counters of n images x 32 stages: level and side of every stage, the rest zero.
+__global__ void init_counters_kernel(long long *cnt, Schedule sch, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * RAPID_MAX_STAGES) return;
+  const int st = i % RAPID_MAX_STAGES;
+  long long *c = cnt + (long long)i * CNT_N;
+  for (int j = 0; j < CNT_N; j++) c[j] = 0;
+  if (st < sch.n) {
+    c[CNT_LEVEL] = sch.level[st];
+    c[CNT_SIDE] = sch.side[st];
   }
 }
 
-cudaError_t launch_init_counters(long long *cnt, const Schedule &sch, cudaStream_t s) {
-  init_counters_kernel<<<1, RAPID_MAX_STAGES, 0, s>>>(cnt, sch);
+cudaError_t launch_init_counters(long long *cnt, const Schedule &sch, int n, cudaStream_t s) {
+  init_counters_kernel<<<blocks_for((long long)n * RAPID_MAX_STAGES, 128), 128, 0, s>>>(cnt, sch, n);
   return cudaGetLastError();
 }
 

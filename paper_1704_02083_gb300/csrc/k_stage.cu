@@ -55,7 +55,7 @@ struct BlockIn {
 // ---------------------------------------------------------------- binary64 decision
 // Exactly the oracle's evaluation: e(a), then e(k) - e(a) per distinct neighbour label,
 // least value (ties to the smaller label).  Returns the best label or -1 (no decrease).
-__device__ __noinline__ int decide_f64(const StageArgs &a, const BlockIn &in) {
+__device__ __noinline__ int decide_f64(const StageArgs &a, const BlockIn &in, double lam_pos) {
   const DevStats &s = a.st;
   const BlockSums &bs = in.bs;
   const double w = __ll2double_rn(bs.w);
@@ -67,7 +67,7 @@ __device__ __noinline__ int decide_f64(const StageArgs &a, const BlockIn &in) {
   for (int j = 0; j < 4; j++)
     if (in.nb[j] >= 0 && in.nb[j] != lbl) Ba += len[j];
   const double ea = blk_energy(w, r2, g2, b2, x2, y2, s.mR[lbl], s.mG[lbl], s.mB[lbl], s.mX[lbl], s.mY[lbl],
-                               __ll2double_rn(Ba), a.lam_pos, a.lam_b2);
+                               __ll2double_rn(Ba), lam_pos, a.lam_b2);
   int bestk = -1;
   double best = 0.0;
   for (int j = 0; j < 4; j++) {
@@ -80,7 +80,7 @@ __device__ __noinline__ int decide_f64(const StageArgs &a, const BlockIn &in) {
     for (int i = 0; i < 4; i++)
       if (in.nb[i] >= 0 && in.nb[i] != k) Bk += len[i];
     const double ek = blk_energy(w, r2, g2, b2, x2, y2, s.mR[k], s.mG[k], s.mB[k], s.mX[k], s.mY[k],
-                                 __ll2double_rn(Bk), a.lam_pos, a.lam_b2);
+                                 __ll2double_rn(Bk), lam_pos, a.lam_b2);
     const double dE = __dsub_rn(ek, ea);
     if (bestk < 0 || dE < best || (dE == best && k < bestk)) {
       best = dE;
@@ -177,7 +177,20 @@ __device__ void commit_phase(const StageArgs &a, int g) {
 // least merge cost among those that stay within u * InitSize; ties to the smaller id.  A
 // search that found no target is remembered with its neighbour labels; while neither the
 // label nor any of them has changed since, the answer is the same and the scan is skipped.
-__device__ void merge_targets(const StageArgs &a, int rq, int g) {
+// Image of global label v: the last image whose first label is <= v.
+__device__ __forceinline__ int image_of_label(const int *label0, int nimg, int v) {
+  int lo = 0, hi = nimg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (label0[mid] <= v) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <bool kBatch>
+__device__ __forceinline__ void merge_targets(const StageArgs &a, const ImageDesc *imgs, const int *label0, int rq,
+                                              int g) {
   __shared__ double sw[kThreads];
   __shared__ int sn[kThreads];
   __shared__ int nset[kMergeSet];
@@ -187,12 +200,16 @@ __device__ void merge_targets(const StageArgs &a, int rq, int g) {
   const DevMerge &mg = a.mg;
   for (int j = blockIdx.x; j < rq; j += gridDim.x) {
     const int al = mg.req_list[j];
+    const int ii = kBatch ? image_of_label(label0, a.nimg, al) : 0;
+    const ImageDesc &im = kBatch ? imgs[ii] : a.img0;
+    long long *cnt = a.ctl.cnt + (long long)ii * kCntStride;
     // A cached failure still holds when the neighbour set is provably the same (no move of
-    // or next to a block of al, no merge since) and every cached neighbour still fails the
-    // size condition with the current counts.
+    // or next to a block of al, no merge in its image since) and every cached neighbour
+    // still fails the size condition with the current counts.
     if (threadIdx.x < 32) {
       const int cs = mg.cache_stamp[al], cn = mg.cache_n[al];
-      const bool can = cs > 0 && cn >= 0 && s.adj[al] <= cs && ld_volatile_i32(a.ctl.last_merge) <= cs;
+      const bool can =
+          cs > 0 && cn >= 0 && s.adj[al] <= cs && ld_volatile_i32(a.ctl.last_merge + ii) <= cs;
       bool fits = false;
       if (can && (int)threadIdx.x < cn) {
         const int n = mg.cache_nb[(long long)al * kCacheLabels + threadIdx.x];
@@ -201,7 +218,7 @@ __device__ void merge_targets(const StageArgs &a, int rq, int g) {
       fits = __any_sync(0xffffffffu, fits);
       if (threadIdx.x == 0) {
         s_hit = can && !fits;
-        atomic_add_i64(&a.ctl.cnt[s_hit ? CNT_CACHE_HITS : CNT_SEARCHES], 1);
+        atomic_add_i64(&cnt[s_hit ? CNT_CACHE_HITS : CNT_SEARCHES], 1);
         s_over = 0;
         s_ext[0] = s_ext[1] = INT_MAX;
         s_ext[2] = s_ext[3] = -1;
@@ -224,17 +241,19 @@ __device__ void merge_targets(const StageArgs &a, int rq, int g) {
     const int bx0 = bb.x / a.side, bx1 = bb.z / a.side, by0 = bb.y / a.side, by1 = bb.w / a.side;
     const int bw = bx1 - bx0 + 1;
     const long long total = (long long)bw * (by1 - by0 + 1);
+    const int *lab = im.lab;
+    const int nbx = im.nbx, nby = im.nby;
     int mnx = INT_MAX, mny = INT_MAX, mxx = -1, mxy = -1;
     for (long long t = threadIdx.x; t < total; t += blockDim.x) {
       const int cx = bx0 + (int)(t % bw), cy = by0 + (int)(t / bw);
-      const long long idx = (long long)cy * a.nbx + cx;
-      if (a.lab[idx] != al) continue;
+      const long long idx = (long long)cy * nbx + cx;
+      if (lab[idx] != al) continue;
       mnx = min(mnx, cx);
       mxx = max(mxx, cx);
       mny = min(mny, cy);
       mxy = max(mxy, cy);
-      const int q[4] = {cy > 0 ? a.lab[idx - a.nbx] : -1, cx > 0 ? a.lab[idx - 1] : -1,
-                        cx + 1 < a.nbx ? a.lab[idx + 1] : -1, cy + 1 < a.nby ? a.lab[idx + a.nbx] : -1};
+      const int q[4] = {cy > 0 ? lab[idx - nbx] : -1, cx > 0 ? lab[idx - 1] : -1,
+                        cx + 1 < nbx ? lab[idx + 1] : -1, cy + 1 < nby ? lab[idx + nbx] : -1};
       for (int i = 0; i < 4; i++)
         if (q[i] >= 0 && q[i] != al) set_insert(nset, kMergeSet, q[i], &s_over);
     }
@@ -246,8 +265,8 @@ __device__ void merge_targets(const StageArgs &a, int rq, int g) {
     }
     __syncthreads();
     if (threadIdx.x == 0 && s_ext[2] >= 0) {
-      s.bbox[al] = make_int4(s_ext[0] * a.side, s_ext[1] * a.side, min((s_ext[2] + 1) * a.side, a.W) - 1,
-                             min((s_ext[3] + 1) * a.side, a.H) - 1);
+      s.bbox[al] = make_int4(s_ext[0] * a.side, s_ext[1] * a.side, min((s_ext[2] + 1) * a.side, im.W) - 1,
+                             min((s_ext[3] + 1) * a.side, im.H) - 1);
     }
     double best = 0.0;
     int bestn = INT_MAX;
@@ -256,7 +275,7 @@ __device__ void merge_targets(const StageArgs &a, int rq, int g) {
         const int n = nset[i];
         if (n < 0) continue;
         if ((long long)a.hi_den * (s.N[n] + s.N[al]) > (long long)a.hi_num * s.init[n]) continue;
-        const double wv = ward_cost(s, al, n, a.lam_pos);
+        const double wv = ward_cost(s, al, n, im.lam_pos);
         if (bestn == INT_MAX || wv < best || (wv == best && n < bestn)) {
           best = wv;
           bestn = n;
@@ -265,15 +284,15 @@ __device__ void merge_targets(const StageArgs &a, int rq, int g) {
     } else {  // more neighbours than the set holds: evaluate every adjacency directly
       for (long long t = threadIdx.x; t < total; t += blockDim.x) {
         const int cx = bx0 + (int)(t % bw), cy = by0 + (int)(t / bw);
-        const long long idx = (long long)cy * a.nbx + cx;
-        if (a.lab[idx] != al) continue;
-        const int q[4] = {cy > 0 ? a.lab[idx - a.nbx] : -1, cx > 0 ? a.lab[idx - 1] : -1,
-                          cx + 1 < a.nbx ? a.lab[idx + 1] : -1, cy + 1 < a.nby ? a.lab[idx + a.nbx] : -1};
+        const long long idx = (long long)cy * nbx + cx;
+        if (lab[idx] != al) continue;
+        const int q[4] = {cy > 0 ? lab[idx - nbx] : -1, cx > 0 ? lab[idx - 1] : -1,
+                          cx + 1 < nbx ? lab[idx + 1] : -1, cy + 1 < nby ? lab[idx + nbx] : -1};
         for (int i = 0; i < 4; i++) {
           const int n = q[i];
           if (n < 0 || n == al) continue;
           if ((long long)a.hi_den * (s.N[n] + s.N[al]) > (long long)a.hi_num * s.init[n]) continue;
-          const double wv = ward_cost(s, al, n, a.lam_pos);
+          const double wv = ward_cost(s, al, n, im.lam_pos);
           if (bestn == INT_MAX || wv < best || (wv == best && n < bestn)) {
             best = wv;
             bestn = n;
@@ -398,12 +417,15 @@ __device__ void merge_walk_big(const StageArgs &a, int nf) {
 }
 
 // Apply accepted merges (list in shared or global memory) and finish every found request.
-__device__ void merge_apply(const StageArgs &a, const int2 *acc, int nacc, int nf, int g,
-                            unsigned long long *changes) {
+template <bool kBatch>
+__device__ __forceinline__ void merge_apply(const StageArgs &a, const ImageDesc *imgs, const int *label0,
+                                            const int2 *acc, int nacc, int nf, int g, int slot) {
   const DevStats &s = a.st;
   const DevMerge &mg = a.mg;
   for (int j = blockIdx.x; j < nacc; j += gridDim.x) {
     const int al = acc[j].x, n = acc[j].y;
+    const int ii = kBatch ? image_of_label(label0, a.nimg, al) : 0;
+    const ImageDesc &im = kBatch ? imgs[ii] : a.img0;
     const int4 ba = s.bbox[al];
     if (threadIdx.x == 0) {
       s.N[n] += s.N[al];
@@ -417,20 +439,22 @@ __device__ void merge_apply(const StageArgs &a, const int2 *acc, int nacc, int n
       set_means(s, al);
       s.chg[n] = 2 * g + 1;
       s.chg[al] = 2 * g + 1;
-      *a.ctl.last_merge = 2 * g + 1;
+      a.ctl.last_merge[ii] = 2 * g + 1;
       int4 bn = s.bbox[n];
       bn.x = min(bn.x, ba.x);
       bn.y = min(bn.y, ba.y);
       bn.z = max(bn.z, ba.z);
       bn.w = max(bn.w, ba.w);
       s.bbox[n] = bn;
+      atomic_add_i64(&a.ctl.cnt[(long long)ii * kCntStride + CNT_MERGES], 1);
+      atomicAdd(&a.ctl.changes[3 * ii + slot], 1ull);
     }
     const int bx0 = ba.x / a.side, bx1 = ba.z / a.side, by0 = ba.y / a.side, by1 = ba.w / a.side;
     const int bw = bx1 - bx0 + 1;
     const long long total = (long long)bw * (by1 - by0 + 1);
     for (long long t = threadIdx.x; t < total; t += blockDim.x) {
-      const long long idx = (long long)(by0 + (int)(t / bw)) * a.nbx + bx0 + (int)(t % bw);
-      if (a.lab[idx] == al) a.lab[idx] = n;
+      const long long idx = (long long)(by0 + (int)(t / bw)) * im.nbx + bx0 + (int)(t % bw);
+      if (im.lab[idx] == al) im.lab[idx] = n;
     }
   }
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += gridDim.x * blockDim.x) {
@@ -438,10 +462,6 @@ __device__ void merge_apply(const StageArgs &a, const int2 *acc, int nacc, int n
     mg.req_flag[al] = 0;
     mg.req_min[al] = INT_MAX;
     mg.target[al] = -1;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && nacc) {
-    a.ctl.cnt[CNT_MERGES] += nacc;
-    *changes += (unsigned long long)nacc;
   }
 }
 
@@ -461,30 +481,45 @@ struct Timer {
   }
 };
 
+// kBatch: a launch over several images (descriptors copied to shared memory); otherwise
+// one image, whose descriptor the kernel reads from its parameters.
+template <bool kBatch>
 __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
+  constexpr int kImgs = kBatch ? kMaxBatch : 1;
   __shared__ WarpTile wts[kThreads / 32];
   __shared__ int2 s_acc[kAcceptSmem];
-  __shared__ int s_draw;
+  __shared__ ImageDesc s_img[kImgs];
+  __shared__ int s_tile0[kImgs], s_label0[kImgs];
+  __shared__ unsigned char s_active[kImgs];
+  __shared__ int s_draw, s_any;
   unsigned epoch = 0;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+  for (int i = threadIdx.x; i < (kBatch ? a.nimg : 1); i += blockDim.x) {
+    if (kBatch) {
+      s_img[i] = a.imgs[i];
+      s_tile0[i] = a.imgs[i].tile0;
+      s_label0[i] = a.imgs[i].label0;
+    }
+    s_active[i] = 1;
+  }
   for (int k = blockIdx.x + gridDim.x * threadIdx.x; k < a.st.M; k += gstride) {
-
     set_means(a.st, k);
     a.st.chg[k] = 0;
     a.mg.cache_stamp[k] = 0;
     a.st.adj[k] = 0;
   }
-  const int nrec = a.ntx * a.nty * 9;
-  for (int i = gtid; i < nrec; i += gstride) a.trec[(long long)i * kRecInts] = 0;
+  const long long nrec = (long long)a.ntiles * 9;
+  for (long long i = gtid; i < nrec; i += gstride) a.trec[i * kRecInts] = 0;
   if (!grid_sync(a.ctl, epoch)) return;
   Timer tm(a.ctl.prof);
   int g = 0;
   for (int sweep = 0; sweep < a.max_sweeps; sweep++) {
-    unsigned long long *changes = &a.ctl.changes[sweep % 3];
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl.changes[(sweep + 1) % 3] = 0;
+    const int slot = sweep % 3;
+    if (blockIdx.x == 0)
+      for (int i = threadIdx.x; i < a.nimg; i += blockDim.x) a.ctl.changes[3 * i + (sweep + 1) % 3] = 0;
     for (int ph = 0; ph < 9; ph++) {
       g++;
-      eval_phase(a, wts, &s_draw, ph, g, changes);
+      eval_phase<kBatch>(a, s_img, s_tile0, s_active, wts, &s_draw, ph, g, slot);
 
       tm.lap(PROF_EVAL);
       if (!grid_sync(a.ctl, epoch)) return;
@@ -500,35 +535,49 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
       if (!grid_sync(a.ctl, epoch)) return;
       tm.lap(PROF_SYNC2);
       if (rq > 0) {
-        merge_targets(a, rq, g);
+        merge_targets<kBatch>(a, s_img, s_label0, rq, g);
         if (!grid_sync(a.ctl, epoch)) return;
         const int nf = ld_volatile_i32(a.mg.found_count + gp);
         if (nf > 0) {
           if (nf <= kAcceptSmem) {
             const int nacc = merge_walk_small(a, nf, s_acc);
-            merge_apply(a, s_acc, nacc, nf, g, changes);
+            merge_apply<kBatch>(a, s_img, s_label0, s_acc, nacc, nf, g, slot);
           } else {
             if (blockIdx.x == 0) merge_walk_big(a, nf);
             if (!grid_sync(a.ctl, epoch)) return;
-            merge_apply(a, a.mg.acc, ld_volatile_i32(a.mg.acc_count), nf, g, changes);
+            merge_apply<kBatch>(a, s_img, s_label0, a.mg.acc, ld_volatile_i32(a.mg.acc_count), nf, g, slot);
           }
           if (!grid_sync(a.ctl, epoch)) return;
         }
         tm.lap(PROF_MERGE);
       }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl.cnt[CNT_SWEEPS] += 1;
-    if (ld_volatile_u64(changes) == 0) break;
+    // End of the sweep (every CTA decides the same from the same counts): an image whose
+    // sweep changed nothing has finished this stage, and its tiles are no longer visited.
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < (kBatch ? a.nimg : 1); i += blockDim.x) {
+      if (!s_active[i]) continue;
+      if (blockIdx.x == 0) a.ctl.cnt[(long long)i * kCntStride + CNT_SWEEPS] += 1;
+      if (ld_volatile_u64(&a.ctl.changes[3 * i + slot]) == 0)
+        s_active[i] = 0;
+      else
+        s_any = 1;
+    }
+    __syncthreads();
+    if (!s_any) break;
   }
 }
 
 int stage_block_threads() { return kThreads; }
-const void *stage_kernel_ptr() { return (const void *)stage_kernel; }
+const void *stage_kernel_ptr(bool batch) {
+  return batch ? (const void *)stage_kernel<true> : (const void *)stage_kernel<false>;
+}
 
 cudaError_t launch_stage(const StageArgs &a, int grid, int block, cudaStream_t s) {
   StageArgs copy = a;
   void *args[] = {&copy};
-  return cudaLaunchCooperativeKernel((const void *)stage_kernel, dim3(grid), dim3(block), args, 0, s);
+  return cudaLaunchCooperativeKernel(stage_kernel_ptr(a.nimg > 1), dim3(grid), dim3(block), args, 0, s);
 }
 
 }  // namespace rapid

@@ -1,6 +1,6 @@
 // rapid_api.cu — the C ABI (include/rapid.h): context, device buffers, stage schedule and
-// launch orchestration.  Host code only; every step of the method runs in the kernels of
-// k_prep.cu and k_stage.cu.
+// launch orchestration for a batch of images (a single image is a batch of one).  Host
+// code only; every step of the method runs in the kernels of k_prep.cu and k_stage.cu.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -14,66 +14,93 @@
 namespace rapid {
 cudaError_t launch_pyramid(const unsigned char *img, long long pitch, int H, int W, int f, int Wl, int Hl,
                            int4 *out, cudaStream_t s);
-cudaError_t launch_seed(const StageArgs &a, int gx, int gy, cudaStream_t s, int *launches);
-cudaError_t launch_recompute(const StageArgs &a, cudaStream_t s, int *launches);
+cudaError_t launch_seed(const StageArgs &a, const ImageDesc *ims, const int *gx, const int *gy, int n,
+                        cudaStream_t s, int *launches);
+cudaError_t launch_recompute(const StageArgs &a, const ImageDesc *ims, int n, cudaStream_t s, int *launches);
 cudaError_t launch_split(const int *src, int snbx, int *dst, int dnbx, int dnby, cudaStream_t s);
-cudaError_t launch_predict(const int *lab, int nbx, int nby, const DevStats &st, long long hT, cudaStream_t s,
+cudaError_t launch_predict(const ImageDesc *ims, int n, const DevStats &st, long long hT, cudaStream_t s,
                            int *launches);
-cudaError_t launch_upsample(const int *lab, int nbx, int side, int H, int W, int *dst, long long pitch_elems,
-                            cudaStream_t s);
-cudaError_t launch_pack_stats(const DevStats &st, rapid_sp_stats *out, cudaStream_t s);
+cudaError_t launch_upsample(const int *lab, int nbx, int side, int H, int W, int label0, int *dst,
+                            long long pitch_elems, cudaStream_t s);
+cudaError_t launch_pack_stats(const DevStats &st, int label0, int M, rapid_sp_stats *out, cudaStream_t s);
 cudaError_t launch_simple_table(unsigned char *out, cudaStream_t s);
-cudaError_t launch_init_counters(long long *cnt, const Schedule &sch, cudaStream_t s);
+cudaError_t launch_init_counters(long long *cnt, const Schedule &sch, int n, cudaStream_t s);
 }  // namespace rapid
 
 using namespace rapid;
 
+static_assert(RAPID_MAX_STAGES == 32, "the device counter layout holds 32 stages per image");
+static_assert(RAPID_MAX_BATCH == kMaxBatch, "header and device batch limits differ");
+
 static const int kMaxLevels = 8;
+
+// One image of the context's batch.
+struct ImgHost {
+  int H, W, K;
+  long long pitch;                // row pitch of the device copy
+  size_t img_off;                 // byte offset of the copy in d_img
+  size_t pyr_off[kMaxSumLevels];  // int4 offset of its cells in each sum level
+  size_t lab_off;                 // int offset of its label maps in d_lab[0] and d_lab[1]
+  int gx, gy, M, label0;          // seed grid, labels label0 .. label0 + M - 1
+  double lam_pos;
+};
 
 struct rapid_ctx {
   rapid_params p;
   cudaStream_t stream;
   int device, nsm, coop_grid, coop_block;
   rapid_status sticky;
-  // image and levels
-  int H, W;
-  long long pitch;
+  // images and levels
+  int nimg;
+  ImgHost im[kMaxBatch];
   unsigned char *d_img;
   size_t img_cap;
   int L;
-  int f[kMaxLevels + 1], Wl[kMaxLevels + 1], Hl[kMaxLevels + 1];
-  // box-sum levels for block sums (factors sf[i] > 1, ascending)
-  int nsf;
-  int sf[kMaxSumLevels], sfW[kMaxSumLevels], sfH[kMaxSumLevels];
+  int f[kMaxLevels + 1];
+  int nsf;  // box-sum levels for block sums (factors sf[i] > 1, ascending)
+  int sf[kMaxSumLevels];
   int4 *d_pyr[kMaxSumLevels];
   size_t pyr_cap[kMaxSumLevels];
   // schedule
   int nstages;
   int st_level[RAPID_MAX_STAGES], st_side[RAPID_MAX_STAGES];
-  int cur, nbx, nby, cur_buf;
+  int cur, cur_buf;
   bool image_set;
   int *d_lab[2];
-  long long lab_cap;
-  int *d_full;  // full-res staging for host reads at side > 1
+  size_t lab_cap[2];
+  int *d_full;  // full-res staging for host reads
+  size_t full_cap;
   int *d_trec;  // tile scan records, sized for the finest stage
-  long long trec_cap;
-  long long full_cap;
+  size_t trec_cap;
+  // per (stage, image) descriptors
+  ImageDesc *h_desc;  // [nstages * nimg]
+  ImageDesc *d_desc;
+  size_t desc_cap;
+  int ntiles[RAPID_MAX_STAGES];
+  int stage_grid[RAPID_MAX_STAGES];  // CTAs of each stage's launch (0 = the full co-resident grid)
   // labels
-  int M, M_cap;
+  int M_total, M_cap;
   void *d_label_block;
   DevStats st;
   DevMerge mg;
   rapid_sp_stats *d_pack;
+  size_t pack_cap;
   // control
   void *d_ctl_block;
+  CtlLayout cl;
   DevCtl ctl;
-  double lam_pos, lam_b2;
+  long long *prof;  // [RAPID_MAX_STAGES][PROF_N] section times (ns)
+  double lam_b2;
   int imp_on;
   long long launches;
   int profiling;
-  long long *prof;  // [RAPID_MAX_STAGES][PROF_N] section times (ns)
   cudaEvent_t ev[RAPID_MAX_STAGES][2];
   int ev_ok[RAPID_MAX_STAGES];
+  // CUDA graph of rapid_run
+  int graph_on, graph_ok, capturing;
+  cudaGraph_t graph;
+  cudaGraphExec_t gexec;
+  long long graph_launches;
 };
 
 static rapid_status cuda_fail(rapid_ctx *c) {
@@ -81,14 +108,15 @@ static rapid_status cuda_fail(rapid_ctx *c) {
   return RAPID_ECUDA;
 }
 
-#define CK(call)                             \
-  do {                                       \
-    cudaError_t e_ = (call);                 \
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
     if (e_ != cudaSuccess) return cuda_fail(ctx); \
   } while (0)
 
 static bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 static int ceil_div(int a, int b) { return (a + b - 1) / b; }
+static size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
 extern "C" void rapid_default_params(rapid_params *p) {
   if (!p) return;
@@ -151,40 +179,48 @@ extern "C" rapid_status rapid_create(const rapid_params *p, void *cuda_stream, r
   int coop = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
   ctx->coop_block = stage_block_threads();
-  int per_sm = 0;
+  int per_sm = 0, per_sm_batch = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_ptr(), ctx->coop_block, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_ptr(false), ctx->coop_block, 0);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_batch, stage_kernel_ptr(true), ctx->coop_block, 0);
+  per_sm = std::min(per_sm, per_sm_batch);
   if (e != cudaSuccess || !coop || per_sm < 1) {
     delete ctx;
     return RAPID_ECUDA;
   }
   ctx->coop_grid = ctx->nsm * per_sm;
-  // control block: barrier (2 u32), error (i32), request/accept counts, sweep changes
-  // (3 u64), counters.
-  size_t ctl_bytes = 128 + sizeof(long long) * (CNT_N + PROF_N) * RAPID_MAX_STAGES;
-  if (cudaMalloc(&ctx->d_ctl_block, ctl_bytes) != cudaSuccess) {
+  ctx->cl = ctl_layout(kMaxBatch);
+  if (cudaMalloc(&ctx->d_ctl_block, ctx->cl.total) != cudaSuccess) {
     delete ctx;
     return RAPID_ENOMEM;
   }
   char *b = (char *)ctx->d_ctl_block;
   ctx->ctl.bar = (unsigned *)(b + 0);
   ctx->ctl.err = (int *)(b + 8);
-  ctx->ctl.last_merge = (int *)(b + 12);
   ctx->mg.req_count = (int *)(b + 16);    // [2], by phase parity
   ctx->mg.found_count = (int *)(b + 24);  // [2], by phase parity
   ctx->mg.acc_count = (int *)(b + 32);
-  ctx->ctl.changes = (unsigned long long *)(b + 40);
-  ctx->ctl.cnt = (long long *)(b + 128);
-  ctx->prof = (long long *)(b + 128 + sizeof(long long) * CNT_N * RAPID_MAX_STAGES);
+  ctx->ctl.last_merge = (int *)(b + ctx->cl.last_merge);
+  ctx->ctl.changes = (unsigned long long *)(b + ctx->cl.changes);
+  ctx->ctl.cnt = (long long *)(b + ctx->cl.cnt);
+  ctx->prof = (long long *)(b + ctx->cl.prof);
   ctx->ctl.spin_ns = p->spin_limit_ns;
-  if (cudaMemsetAsync(ctx->d_ctl_block, 0, ctl_bytes, ctx->stream) != cudaSuccess) {
+  if (cudaMemsetAsync(ctx->d_ctl_block, 0, ctx->cl.total, ctx->stream) != cudaSuccess) {
     cudaFree(ctx->d_ctl_block);
     delete ctx;
     return RAPID_ECUDA;
   }
-  for (int i = 0; i < RAPID_MAX_STAGES; i++) ctx->ev_ok[i] = 0;
   *out = ctx;
   return RAPID_OK;
+}
+
+static void drop_graph(rapid_ctx *ctx) {
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  ctx->gexec = nullptr;
+  ctx->graph = nullptr;
+  ctx->graph_ok = 0;
 }
 
 static void free_image_buffers(rapid_ctx *ctx) {
@@ -196,21 +232,28 @@ static void free_image_buffers(rapid_ctx *ctx) {
     ctx->d_pyr[l] = nullptr;
     ctx->pyr_cap[l] = 0;
   }
-  cudaFree(ctx->d_lab[0]);
-  cudaFree(ctx->d_lab[1]);
-  ctx->d_lab[0] = ctx->d_lab[1] = nullptr;
-  ctx->lab_cap = 0;
+  for (int b = 0; b < 2; b++) {
+    cudaFree(ctx->d_lab[b]);
+    ctx->d_lab[b] = nullptr;
+    ctx->lab_cap[b] = 0;
+  }
   cudaFree(ctx->d_full);
   ctx->d_full = nullptr;
   ctx->full_cap = 0;
   cudaFree(ctx->d_trec);
   ctx->d_trec = nullptr;
   ctx->trec_cap = 0;
+  cudaFree(ctx->d_desc);
+  ctx->d_desc = nullptr;
+  ctx->desc_cap = 0;
+  std::free(ctx->h_desc);
+  ctx->h_desc = nullptr;
 }
 
 extern "C" void rapid_destroy(rapid_ctx *ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  drop_graph(ctx);
   free_image_buffers(ctx);
   cudaFree(ctx->d_label_block);
   cudaFree(ctx->d_pack);
@@ -225,7 +268,7 @@ extern "C" void rapid_destroy(rapid_ctx *ctx) {
 
 // Levels f_l = C^(L-l) and the stage schedule: the block side halves from the initial
 // block (at least f_1) to the final grain; each side belongs to the coarsest level whose
-// factor does not exceed it.
+// factor does not exceed it.  Depends on the parameters only.
 static rapid_status make_schedule(rapid_ctx *ctx) {
   const rapid_params &p = ctx->p;
   ctx->L = p.num_levels;
@@ -233,8 +276,6 @@ static rapid_status make_schedule(rapid_ctx *ctx) {
     int f = 1;
     for (int i = 0; i < ctx->L - l; i++) f *= p.ratio_C;
     ctx->f[l] = f;
-    ctx->Wl[l] = ceil_div(ctx->W, f);
-    ctx->Hl[l] = ceil_div(ctx->H, f);
   }
   int s = p.init_block < ctx->f[1] ? ctx->f[1] : p.init_block;
   ctx->nstages = 0;
@@ -257,128 +298,20 @@ static rapid_status make_schedule(rapid_ctx *ctx) {
     ctx->st_side[0] = p.init_block < ctx->f[1] ? ctx->f[1] : p.init_block;
     ctx->nstages = 1;
   }
-  return RAPID_OK;
-}
-
-extern "C" rapid_status rapid_set_image(rapid_ctx *ctx, const uint8_t *rgb, int32_t H, int32_t W,
-                                        int64_t row_pitch_bytes, int32_t rgb_is_device) {
-  if (!ctx || !rgb) return RAPID_EINVAL;
-  if (ctx->sticky != RAPID_OK) return ctx->sticky;
-  if (H < 1 || W < 1 || row_pitch_bytes < 3ll * W) return RAPID_EINVAL;
-  const long long npx = (long long)H * W;
-  if (npx >= (1ll << 31)) return RAPID_EINVAL;
-  // position sums reach about H*W*max(H,W)/2; keep them exact in binary64
-  if ((double)npx * (double)(H > W ? H : W) >= 9007199254740992.0) return RAPID_EINVAL;
-  ctx->H = H;
-  ctx->W = W;
-  ctx->image_set = false;
-  ctx->cur = -1;
-  rapid_status rs = make_schedule(ctx);
-  if (rs != RAPID_OK) return rs;
-  ctx->pitch = ((3ll * W + 15) / 16) * 16;
-  size_t need = (size_t)ctx->pitch * H;
-  if (need > ctx->img_cap) {
-    cudaFree(ctx->d_img);
-    ctx->d_img = nullptr;
-    ctx->img_cap = 0;
-    if (cudaMalloc(&ctx->d_img, need) != cudaSuccess) return RAPID_ENOMEM;
-    ctx->img_cap = need;
-  }
   ctx->nsf = sum_factors(ctx->f, ctx->L, ctx->st_side[0], ctx->sf);
-  // a sum level keeps int32 channel sums: one cell (at most f x f pixels of 255) must fit
-  for (int l = 0; l < ctx->nsf; l++)
-    if ((long long)std::min(ctx->sf[l], W) * std::min(ctx->sf[l], H) * 255 > INT_MAX) return RAPID_ERANGE;
-  for (int l = 0; l < ctx->nsf; l++) {
-    ctx->sfW[l] = ceil_div(W, ctx->sf[l]);
-    ctx->sfH[l] = ceil_div(H, ctx->sf[l]);
-    size_t pn = (size_t)ctx->sfW[l] * ctx->sfH[l] * sizeof(int4);
-    if (pn > ctx->pyr_cap[l]) {
-      cudaFree(ctx->d_pyr[l]);
-      ctx->d_pyr[l] = nullptr;
-      ctx->pyr_cap[l] = 0;
-      if (cudaMalloc(&ctx->d_pyr[l], pn) != cudaSuccess) return RAPID_ENOMEM;
-      ctx->pyr_cap[l] = pn;
-    }
-  }
-  const int sl = ctx->st_side[ctx->nstages - 1];
-  long long cap = (long long)ceil_div(W, sl) * ceil_div(H, sl);
-  if (cap > ctx->lab_cap) {
-    cudaFree(ctx->d_lab[0]);
-    cudaFree(ctx->d_lab[1]);
-    ctx->d_lab[0] = ctx->d_lab[1] = nullptr;
-    ctx->lab_cap = 0;
-    if (cudaMalloc(&ctx->d_lab[0], cap * sizeof(int)) != cudaSuccess) return RAPID_ENOMEM;
-    if (cudaMalloc(&ctx->d_lab[1], cap * sizeof(int)) != cudaSuccess) return RAPID_ENOMEM;
-    ctx->lab_cap = cap;
-  }
-  {
-    // tile records: the finest stage has the most tiles
-    const long long nbx = ceil_div(W, sl), nby = ceil_div(H, sl);
-    const long long nrec = ((nbx + kTileW - 1) / kTileW) * ((nby + kTileH - 1) / kTileH) * 9 * kRecInts;
-    if (nrec > ctx->trec_cap) {
-      cudaFree(ctx->d_trec);
-      ctx->d_trec = nullptr;
-      ctx->trec_cap = 0;
-      if (cudaMalloc(&ctx->d_trec, nrec * sizeof(int)) != cudaSuccess) return RAPID_ENOMEM;
-      ctx->trec_cap = nrec;
-    }
-  }
-  CK(cudaMemcpy2DAsync(ctx->d_img, ctx->pitch, rgb, row_pitch_bytes, 3ull * W, H,
-                       rgb_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
-  if (!rgb_is_device) CK(cudaStreamSynchronize(ctx->stream));
-  ctx->image_set = true;
   return RAPID_OK;
 }
 
-static StageArgs stage_args(rapid_ctx *ctx) {
-  StageArgs a;
-  std::memset(&a, 0, sizeof a);
-  a.H = ctx->H;
-  a.W = ctx->W;
-  a.side = ctx->st_side[ctx->cur];
-  a.nbx = ctx->nbx;
-  a.nby = ctx->nby;
-  a.level = ctx->st_level[ctx->cur];
-  // colour sums from the coarsest box-sum level whose cells fit in a block
-  a.f = 1;
-  a.pyr = nullptr;
-  for (int l = 0; l < ctx->nsf; l++)
-    if (ctx->sf[l] <= a.side) {
-      a.f = ctx->sf[l];
-      a.pyr = ctx->d_pyr[l];
-    }
-  a.k = a.side / a.f;
-  a.Wl = ceil_div(ctx->W, a.f);
-  a.Hl = ceil_div(ctx->H, a.f);
-  a.img = ctx->d_img;
-  a.img_pitch = ctx->pitch;
-
-  a.lab = ctx->d_lab[ctx->cur_buf];
-  a.st = ctx->st;
-  a.mg = ctx->mg;
-  a.ctl = ctx->ctl;
-  a.ctl.cnt = ctx->ctl.cnt + (long long)CNT_N * ctx->cur;
-  a.ctl.prof = ctx->profiling ? ctx->prof + (long long)PROF_N * ctx->cur : nullptr;
-  a.imp_on = ctx->imp_on;
-  a.imp_rule = ctx->p.importance_rule;
-  a.lam_pos = ctx->lam_pos;
-  a.lam_b2 = ctx->lam_b2;
-  a.size_mode = ctx->p.size_mode;
-  a.lo_num = ctx->p.lo_num;
-  a.lo_den = ctx->p.lo_den;
-  a.hi_num = ctx->p.hi_num;
-  a.hi_den = ctx->p.hi_den;
-  a.max_sweeps = ctx->p.max_sweeps;
-  a.trec = ctx->d_trec;
-  a.ntx = (a.nbx + kTileW - 1) / kTileW;
-  a.nty = (a.nby + kTileH - 1) / kTileH;
-  a.lam_pos_f = (float)ctx->lam_pos;
-  a.lam_b2_f = (float)ctx->lam_b2;
-  // single-precision decisions need blocks under 2^24 pixels and exact float block centres
-  a.use_filter = ctx->p.use_filter && a.side <= 4096 && ctx->W < (1 << 22) && ctx->H < (1 << 22);
-  a.verify_filter = ctx->p.verify_filter;
-  a.skip_tiles = ctx->p.skip_tiles;
-  return a;
+// Make *pp a device buffer of at least `need` bytes (contents not kept).
+template <class T>
+static bool grow(T **pp, size_t *cap, size_t need) {
+  if (need <= *cap && *pp) return true;
+  cudaFree(*pp);
+  *pp = nullptr;
+  *cap = 0;
+  if (cudaMalloc((void **)pp, need ? need : 1) != cudaSuccess) return false;
+  *cap = need;
+  return true;
 }
 
 static rapid_status ensure_label_arrays(rapid_ctx *ctx, int M) {
@@ -387,50 +320,220 @@ static rapid_status ensure_label_arrays(rapid_ctx *ctx, int M) {
     return RAPID_OK;
   }
   cudaFree(ctx->d_label_block);
-  cudaFree(ctx->d_pack);
   ctx->d_label_block = nullptr;
-  ctx->d_pack = nullptr;
   ctx->M_cap = 0;
   const size_t bytes = label_arrays_bytes(M);
   if (cudaMalloc(&ctx->d_label_block, bytes) != cudaSuccess) return RAPID_ENOMEM;
-  if (cudaMalloc(&ctx->d_pack, (size_t)M * sizeof(rapid_sp_stats)) != cudaSuccess) return RAPID_ENOMEM;
   carve_label_arrays(ctx->d_label_block, bytes, M, &ctx->st, &ctx->mg);
   ctx->M_cap = M;
   return RAPID_OK;
 }
+
+// Factor of the sum level a stage reads: the coarsest box-sum level whose cells fit in a
+// block (1 = the image itself).
+static int stage_sum_factor(const rapid_ctx *ctx, int side) {
+  int f = 1;
+  for (int l = 0; l < ctx->nsf; l++)
+    if (ctx->sf[l] <= side) f = ctx->sf[l];
+  return f;
+}
+
+// Descriptors of every (stage, image), on the host and uploaded once.
+static rapid_status build_descriptors(rapid_ctx *ctx) {
+  const size_t n = (size_t)ctx->nstages * ctx->nimg;
+  std::free(ctx->h_desc);
+  ctx->h_desc = (ImageDesc *)std::calloc(n, sizeof(ImageDesc));
+  if (!ctx->h_desc) return RAPID_ENOMEM;
+  if (!grow(&ctx->d_desc, &ctx->desc_cap, n * sizeof(ImageDesc))) return RAPID_ENOMEM;
+  for (int s = 0; s < ctx->nstages; s++) {
+    const int side = ctx->st_side[s];
+    const int f = stage_sum_factor(ctx, side);
+    int li = -1;
+    for (int l = 0; l < ctx->nsf; l++)
+      if (ctx->sf[l] == f) li = l;
+    long long tile0 = 0, blk0 = 0;
+    for (int i = 0; i < ctx->nimg; i++) {
+      const ImgHost &h = ctx->im[i];
+      ImageDesc &d = ctx->h_desc[(size_t)s * ctx->nimg + i];
+      d.H = h.H;
+      d.W = h.W;
+      d.nbx = ceil_div(h.W, side);
+      d.nby = ceil_div(h.H, side);
+      d.ntx = (d.nbx + kTileW - 1) / kTileW;
+      d.nty = (d.nby + kTileH - 1) / kTileH;
+      d.Wl = ceil_div(h.W, f);
+      d.Hl = ceil_div(h.H, f);
+      d.tile0 = (int)tile0;
+      d.label0 = h.label0;
+      d.M = h.M;
+      d.blk0 = (int)blk0;
+      // single-precision decisions need blocks under 2^24 pixels and exact float block centres
+      d.use_filter = ctx->p.use_filter && side <= 4096 && h.W < (1 << 22) && h.H < (1 << 22);
+      d.img = ctx->d_img + h.img_off;
+      d.img_pitch = h.pitch;
+      d.pyr = li >= 0 ? ctx->d_pyr[li] + h.pyr_off[li] : nullptr;
+      d.lab = ctx->d_lab[s & 1] + h.lab_off;
+      d.lam_pos = h.lam_pos;
+      d.lam_pos_f = (float)h.lam_pos;
+      tile0 += (long long)d.ntx * d.nty;
+      blk0 += (long long)d.nbx * d.nby;
+    }
+    if (tile0 >= INT_MAX / 9 || blk0 >= INT_MAX) return RAPID_ERANGE;
+    ctx->ntiles[s] = (int)tile0;
+  }
+  if (cudaMemcpy(ctx->d_desc, ctx->h_desc, n * sizeof(ImageDesc), cudaMemcpyHostToDevice) != cudaSuccess)
+    return cuda_fail(ctx);
+  return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_set_images(rapid_ctx *ctx, int32_t n, const uint8_t *const *rgb, const int32_t *H,
+                                         const int32_t *W, const int64_t *row_pitch_bytes, const int32_t *K,
+                                         int32_t rgb_is_device) {
+  if (!ctx || !rgb || !H || !W || !row_pitch_bytes) return RAPID_EINVAL;
+  if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  if (n < 1) return RAPID_EINVAL;
+  if (n > kMaxBatch) return RAPID_ERANGE;
+  for (int i = 0; i < n; i++) {
+    if (!rgb[i] || H[i] < 1 || W[i] < 1 || row_pitch_bytes[i] < 3ll * W[i]) return RAPID_EINVAL;
+    if (K && K[i] < 1) return RAPID_EINVAL;
+    const long long npx = (long long)H[i] * W[i];
+    if (npx >= (1ll << 31)) return RAPID_EINVAL;
+    // position sums reach about H*W*max(H,W)/2; keep them exact in binary64
+    if ((double)npx * (double)(H[i] > W[i] ? H[i] : W[i]) >= 9007199254740992.0) return RAPID_EINVAL;
+  }
+  drop_graph(ctx);
+  ctx->image_set = false;
+  ctx->cur = -1;
+  rapid_status rs = make_schedule(ctx);
+  if (rs != RAPID_OK) return rs;
+  // a sum level keeps int32 channel sums: one cell (at most f x f pixels of 255) must fit
+  for (int i = 0; i < n; i++)
+    for (int l = 0; l < ctx->nsf; l++)
+      if ((long long)std::min(ctx->sf[l], W[i]) * std::min(ctx->sf[l], H[i]) * 255 > INT_MAX) return RAPID_ERANGE;
+  // per-image layout (image copy, sum levels, label maps), seed grid and label range
+  const int s0 = ctx->st_side[0], sl = ctx->st_side[ctx->nstages - 1];
+  size_t img_bytes = 0, pyr_n[kMaxSumLevels] = {0}, lab_n = 0;
+  long long tiles_last = 0, M_total = 0, max_M = 0, npx_max = 0;
+  for (int i = 0; i < n; i++) {
+    ImgHost &h = ctx->im[i];
+    h.H = H[i];
+    h.W = W[i];
+    h.K = K ? K[i] : ctx->p.K;
+    h.pitch = (long long)round_up(3ull * h.W, 16);
+    h.img_off = img_bytes;
+    img_bytes = round_up(img_bytes + (size_t)h.pitch * h.H, 256);
+    for (int l = 0; l < ctx->nsf; l++) {
+      h.pyr_off[l] = pyr_n[l];
+      pyr_n[l] = round_up(pyr_n[l] + (size_t)ceil_div(h.W, ctx->sf[l]) * ceil_div(h.H, ctx->sf[l]), 16);
+    }
+    const int lnbx = ceil_div(h.W, sl), lnby = ceil_div(h.H, sl);
+    h.lab_off = lab_n;
+    lab_n = round_up(lab_n + (size_t)lnbx * lnby, 64);
+    tiles_last += (long long)((lnbx + kTileW - 1) / kTileW) * ((lnby + kTileH - 1) / kTileH);
+    // seed grid gx x gy (same rounding as the stated formula) on the first stage's blocks
+    const int nbx0 = ceil_div(h.W, s0), nby0 = ceil_div(h.H, s0);
+    int gx = (int)std::floor(std::sqrt((double)h.K * (double)h.W / (double)h.H) + 0.5);
+    if (gx < 1) gx = 1;
+    int gy = (int)std::floor((double)h.K / (double)gx + 0.5);
+    if (gy < 1) gy = 1;
+    if (gx > nbx0) gx = nbx0;
+    if (gy > nby0) gy = nby0;
+    h.gx = gx;
+    h.gy = gy;
+    h.M = gx * gy;
+    h.label0 = (int)M_total;
+    M_total += h.M;
+    max_M = std::max<long long>(max_M, h.M);
+    npx_max = std::max<long long>(npx_max, (long long)h.H * h.W);
+    h.lam_pos = ctx->p.lambda_pos0 * ((double)h.M / ((double)h.H * (double)h.W));
+  }
+  if (M_total >= INT_MAX || lab_n >= (size_t)INT_MAX) return RAPID_ERANGE;
+  ctx->nimg = n;
+  ctx->M_total = (int)M_total;
+  ctx->lam_b2 = 2.0 * ctx->p.lambda_b;
+  if (!grow(&ctx->d_img, &ctx->img_cap, img_bytes)) return RAPID_ENOMEM;
+  for (int l = 0; l < ctx->nsf; l++)
+    if (!grow(&ctx->d_pyr[l], &ctx->pyr_cap[l], pyr_n[l] * sizeof(int4))) return RAPID_ENOMEM;
+  for (int b = 0; b < 2; b++)
+    if (!grow(&ctx->d_lab[b], &ctx->lab_cap[b], lab_n * sizeof(int))) return RAPID_ENOMEM;
+  if (!grow(&ctx->d_trec, &ctx->trec_cap, (size_t)tiles_last * 9 * kRecInts * sizeof(int))) return RAPID_ENOMEM;
+  if (!grow(&ctx->d_full, &ctx->full_cap, (size_t)npx_max * sizeof(int))) return RAPID_ENOMEM;
+  if (!grow(&ctx->d_pack, &ctx->pack_cap, (size_t)max_M * sizeof(rapid_sp_stats))) return RAPID_ENOMEM;
+  rs = ensure_label_arrays(ctx, ctx->M_total);
+  if (rs != RAPID_OK) return rs;
+  rs = build_descriptors(ctx);
+  if (rs != RAPID_OK) return rs;
+  for (int i = 0; i < n; i++) {
+    const ImgHost &h = ctx->im[i];
+    CK(cudaMemcpy2DAsync(ctx->d_img + h.img_off, h.pitch, rgb[i], row_pitch_bytes[i], 3ull * h.W, h.H,
+                         rgb_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  }
+  if (!rgb_is_device) CK(cudaStreamSynchronize(ctx->stream));  // the host buffers may be reused at return
+  ctx->image_set = true;
+  return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_set_image(rapid_ctx *ctx, const uint8_t *rgb, int32_t H, int32_t W,
+                                        int64_t row_pitch_bytes, int32_t rgb_is_device) {
+  if (!ctx) return RAPID_EINVAL;
+  const uint8_t *imgs[1] = {rgb};
+  const int64_t pitch[1] = {row_pitch_bytes};
+  return rapid_set_images(ctx, 1, imgs, &H, &W, pitch, nullptr, rgb_is_device);
+}
+
+// Launch arguments of stage s (all images).
+static StageArgs stage_args(rapid_ctx *ctx, int s) {
+  StageArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.side = ctx->st_side[s];
+  a.level = ctx->st_level[s];
+  a.f = stage_sum_factor(ctx, a.side);
+  a.k = a.side / a.f;
+  a.imgs = ctx->d_desc + (size_t)s * ctx->nimg;
+  a.img0 = ctx->h_desc[(size_t)s * ctx->nimg];
+  a.nimg = ctx->nimg;
+  a.ntiles = ctx->ntiles[s];
+  a.trec = ctx->d_trec;
+  a.st = ctx->st;
+  a.st.M = ctx->M_total;
+  a.mg = ctx->mg;
+  a.ctl = ctx->ctl;
+  a.ctl.cnt = ctx->ctl.cnt + (long long)CNT_N * s;
+  a.ctl.prof = ctx->profiling ? ctx->prof + (long long)PROF_N * s : nullptr;
+  a.imp_on = ctx->imp_on;
+  a.imp_rule = ctx->p.importance_rule;
+  a.lam_b2 = ctx->lam_b2;
+  a.lam_b2_f = (float)ctx->lam_b2;
+  a.size_mode = ctx->p.size_mode;
+  a.lo_num = ctx->p.lo_num;
+  a.lo_den = ctx->p.lo_den;
+  a.hi_num = ctx->p.hi_num;
+  a.hi_den = ctx->p.hi_den;
+  a.max_sweeps = ctx->p.max_sweeps;
+  a.verify_filter = ctx->p.verify_filter;
+  a.skip_tiles = ctx->p.skip_tiles;
+  return a;
+}
+
+static const ImageDesc *host_desc(const rapid_ctx *ctx, int s) { return ctx->h_desc + (size_t)s * ctx->nimg; }
 
 extern "C" rapid_status rapid_seed_grid(rapid_ctx *ctx, int32_t *M_out) {
   if (!ctx) return RAPID_EINVAL;
   if (ctx->sticky != RAPID_OK) return ctx->sticky;
   if (!ctx->image_set) return RAPID_ESTATE;
   // level images (exact box sums, Sec. 2.2) and the extra box-sum levels for block sums
-  for (int l = 0; l < ctx->nsf; l++) {
-    CK(launch_pyramid(ctx->d_img, ctx->pitch, ctx->H, ctx->W, ctx->sf[l], ctx->sfW[l], ctx->sfH[l], ctx->d_pyr[l],
-                      ctx->stream));
-    ctx->launches++;
+  for (int i = 0; i < ctx->nimg; i++) {
+    const ImgHost &h = ctx->im[i];
+    for (int l = 0; l < ctx->nsf; l++) {
+      const int sf = ctx->sf[l];
+      CK(launch_pyramid(ctx->d_img + h.img_off, h.pitch, h.H, h.W, sf, ceil_div(h.W, sf), ceil_div(h.H, sf),
+                        ctx->d_pyr[l] + h.pyr_off[l], ctx->stream));
+      ctx->launches++;
+    }
   }
-
   ctx->cur = 0;
   ctx->cur_buf = 0;
-  const int s0 = ctx->st_side[0];
-  ctx->nbx = ceil_div(ctx->W, s0);
-  ctx->nby = ceil_div(ctx->H, s0);
-  // seed grid gx x gy (same rounding as the stated formula)
-  double gxd = std::sqrt((double)ctx->p.K * (double)ctx->W / (double)ctx->H);
-  int gx = (int)std::floor(gxd + 0.5);
-  if (gx < 1) gx = 1;
-  int gy = (int)std::floor((double)ctx->p.K / (double)gx + 0.5);
-  if (gy < 1) gy = 1;
-  if (gx > ctx->nbx) gx = ctx->nbx;
-  if (gy > ctx->nby) gy = ctx->nby;
-  const int M = gx * gy;
-  rapid_status rs = ensure_label_arrays(ctx, M);
-  if (rs != RAPID_OK) return rs;
-  ctx->M = M;
-  ctx->st.M = M;
   ctx->imp_on = 0;
-  ctx->lam_pos = ctx->p.lambda_pos0 * ((double)M / ((double)ctx->H * (double)ctx->W));
-  ctx->lam_b2 = 2.0 * ctx->p.lambda_b;
   // counters: level and side of every stage, the rest zero; no device error pending
   Schedule sch;
   std::memset(&sch, 0, sizeof sch);
@@ -439,14 +542,20 @@ extern "C" rapid_status rapid_seed_grid(rapid_ctx *ctx, int32_t *M_out) {
     sch.level[i] = ctx->st_level[i];
     sch.side[i] = ctx->st_side[i];
   }
-  CK(launch_init_counters(ctx->ctl.cnt, sch, ctx->stream));
+  CK(launch_init_counters(ctx->ctl.cnt, sch, ctx->nimg, ctx->stream));
   CK(cudaMemsetAsync(ctx->prof, 0, sizeof(long long) * PROF_N * RAPID_MAX_STAGES, ctx->stream));
   CK(cudaMemsetAsync(ctx->mg.req_count, 0, 4 * sizeof(int), ctx->stream));
-  int nl = 1;
-  StageArgs a = stage_args(ctx);
-  CK(launch_seed(a, gx, gy, ctx->stream, &nl));
+  ctx->launches++;
+  int gx[kMaxBatch], gy[kMaxBatch];
+  for (int i = 0; i < ctx->nimg; i++) {
+    gx[i] = ctx->im[i].gx;
+    gy[i] = ctx->im[i].gy;
+  }
+  int nl = 0;
+  StageArgs a = stage_args(ctx, 0);
+  CK(launch_seed(a, host_desc(ctx, 0), gx, gy, ctx->nimg, ctx->stream, &nl));
   ctx->launches += nl;
-  if (M_out) *M_out = M;
+  if (M_out) *M_out = ctx->im[0].M;
   return RAPID_OK;
 }
 
@@ -473,23 +582,24 @@ extern "C" rapid_status rapid_refine_stage(rapid_ctx *ctx, int32_t *sweeps_out, 
   if (ctx->sticky != RAPID_OK) return ctx->sticky;
   if (ctx->cur < 0) return RAPID_ESTATE;
   const int i = ctx->cur;
-  // fresh barrier words and sweep-change slots for the launch
+  // fresh barrier words; merge stamps, request / found counts and sweep-change slots
   CK(cudaMemsetAsync(ctx->ctl.bar, 0, 8, ctx->stream));
-  // last merge, request / found counts, sweep changes, tile counters
-  CK(cudaMemsetAsync((char *)ctx->d_ctl_block + 12, 0, 116, ctx->stream));
-
-  StageArgs a = stage_args(ctx);
+  CK(cudaMemsetAsync((char *)ctx->d_ctl_block + 16, 0, ctx->cl.reset_end - 16, ctx->stream));
+  StageArgs a = stage_args(ctx, i);
+  // events around the launch (inside a captured graph as event-record nodes)
+  const unsigned evflags = ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (ctx->profiling) {
     if (!ctx->ev_ok[i]) {
       CK(cudaEventCreate(&ctx->ev[i][0]));
       CK(cudaEventCreate(&ctx->ev[i][1]));
       ctx->ev_ok[i] = 1;
     }
-    CK(cudaEventRecord(ctx->ev[i][0], ctx->stream));
+    CK(cudaEventRecordWithFlags(ctx->ev[i][0], ctx->stream, evflags));
   }
-  CK(launch_stage(a, ctx->coop_grid, ctx->coop_block, ctx->stream));
+  const int grid = ctx->stage_grid[i] > 0 ? std::min(ctx->stage_grid[i], ctx->coop_grid) : ctx->coop_grid;
+  CK(launch_stage(a, grid, ctx->coop_block, ctx->stream));
   ctx->launches++;
-  if (ctx->profiling) CK(cudaEventRecord(ctx->ev[i][1], ctx->stream));
+  if (ctx->profiling) CK(cudaEventRecordWithFlags(ctx->ev[i][1], ctx->stream, evflags));
   if (sweeps_out || moves_out || merges_out) {
     CK(cudaStreamSynchronize(ctx->stream));
     rapid_status rs = read_device_error(ctx);
@@ -511,27 +621,26 @@ extern "C" rapid_status rapid_split(rapid_ctx *ctx) {
   const int nxt = ctx->cur + 1;
   int nl = 0;
   if (ctx->p.predict && ctx->st_level[nxt] >= 2 && prev_level < 2) {
-    CK(launch_predict(ctx->d_lab[ctx->cur_buf], ctx->nbx, ctx->nby, ctx->st, ctx->p.h_T, ctx->stream, &nl));
+    StageArgs a = stage_args(ctx, ctx->cur);
+    CK(launch_predict(host_desc(ctx, ctx->cur), ctx->nimg, a.st, ctx->p.h_T, ctx->stream, &nl));
     ctx->imp_on = 1;
   }
-  const int s = ctx->st_side[nxt];
-  const int dnbx = ceil_div(ctx->W, s), dnby = ceil_div(ctx->H, s);
-  CK(launch_split(ctx->d_lab[ctx->cur_buf], ctx->nbx, ctx->d_lab[ctx->cur_buf ^ 1], dnbx, dnby, ctx->stream));
-  nl++;
+  const ImageDesc *src = host_desc(ctx, ctx->cur), *dst = host_desc(ctx, nxt);
+  for (int i = 0; i < ctx->nimg; i++) {
+    CK(launch_split(src[i].lab, src[i].nbx, dst[i].lab, dst[i].nbx, dst[i].nby, ctx->stream));
+    nl++;
+  }
   ctx->cur_buf ^= 1;
   ctx->cur = nxt;
-  ctx->nbx = dnbx;
-  ctx->nby = dnby;
   if (!ctx->p.reuse && ctx->st_level[nxt] != prev_level) {
-    StageArgs a = stage_args(ctx);
-    CK(launch_recompute(a, ctx->stream, &nl));
+    StageArgs a = stage_args(ctx, nxt);
+    CK(launch_recompute(a, dst, ctx->nimg, ctx->stream, &nl));
   }
   ctx->launches += nl;
   return RAPID_OK;
 }
 
-extern "C" rapid_status rapid_run(rapid_ctx *ctx) {
-  if (!ctx) return RAPID_EINVAL;
+static rapid_status run_sequence(rapid_ctx *ctx) {
   rapid_status rs = rapid_seed_grid(ctx, nullptr);
   if (rs != RAPID_OK) return rs;
   rs = rapid_refine_stage(ctx, nullptr, nullptr, nullptr);
@@ -545,46 +654,163 @@ extern "C" rapid_status rapid_run(rapid_ctx *ctx) {
   return RAPID_OK;
 }
 
+// Capture the whole schedule once into a CUDA graph (stream capture of the launches
+// rapid_run makes) and instantiate it.
+static rapid_status capture_run(rapid_ctx *ctx) {
+  const long long l0 = ctx->launches;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  ctx->capturing = 1;
+  rapid_status rs = run_sequence(ctx);
+  ctx->capturing = 0;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+  if (rs != RAPID_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return rs != RAPID_OK ? rs : cuda_fail(ctx);
+  }
+  ctx->graph = g;
+  CK(cudaGraphInstantiate(&ctx->gexec, g, 0));
+  ctx->graph_launches = ctx->launches - l0;
+  ctx->launches = l0;
+  ctx->graph_ok = 1;
+  return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_run(rapid_ctx *ctx) {
+  if (!ctx) return RAPID_EINVAL;
+  if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  if (!ctx->graph_on) return run_sequence(ctx);
+  if (!ctx->image_set) return RAPID_ESTATE;
+  if (!ctx->graph_ok) {
+    rapid_status rs = capture_run(ctx);
+    if (rs != RAPID_OK) return rs;
+  }
+  CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+  ctx->launches += ctx->graph_launches;
+  // the host-side position after a whole run
+  ctx->cur = ctx->nstages - 1;
+  ctx->cur_buf = (ctx->nstages - 1) & 1;
+  ctx->imp_on = 0;
+  for (int s = 1; s < ctx->nstages; s++)
+    if (ctx->p.predict && ctx->st_level[s] >= 2 && ctx->st_level[s - 1] < 2) ctx->imp_on = 1;
+  return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_set_graph(rapid_ctx *ctx, int32_t on) {
+  if (!ctx) return RAPID_EINVAL;
+  if (on && ctx->stream == 0) return RAPID_EINVAL;  // the legacy stream cannot be captured
+  if (!on) drop_graph(ctx);
+  ctx->graph_on = on ? 1 : 0;
+  return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_set_stage_grids(rapid_ctx *ctx, const int32_t *grids, int32_t n) {
+  if (!ctx || n < 0 || n > RAPID_MAX_STAGES || (n > 0 && !grids)) return RAPID_EINVAL;
+  for (int i = 0; i < n; i++)
+    if (grids[i] < 0) return RAPID_EINVAL;
+  for (int i = 0; i < RAPID_MAX_STAGES; i++) ctx->stage_grid[i] = i < n ? grids[i] : 0;
+  drop_graph(ctx);
+  return RAPID_OK;
+}
+
+// Grid-size tuner.  A stage's result does not depend on how many CTAs share its work (the
+// decisions of a phase are independent, merges are ordered by block index), only its time
+// does: coarse stages with few tiles lose more to the grid barrier than they gain from
+// more SMs.  Run the whole schedule once per candidate grid (the full co-resident grid,
+// then halvings down to one CTA), time every stage with events, and keep per stage the
+// fastest candidate (ties to the larger grid).
+extern "C" rapid_status rapid_autotune(rapid_ctx *ctx, int32_t *grids_out) {
+  if (!ctx) return RAPID_EINVAL;
+  if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  if (!ctx->image_set) return RAPID_ESTATE;
+  const int saved_prof = ctx->profiling, saved_graph = ctx->graph_on;
+  ctx->profiling = 1;
+  ctx->graph_on = 0;
+  drop_graph(ctx);
+  int cand[16], nc = 0;
+  for (int g = ctx->coop_grid; g >= 1 && nc < 16; g /= 2) cand[nc++] = g;
+  float best_ms[RAPID_MAX_STAGES];
+  int best_g[RAPID_MAX_STAGES];
+  for (int s = 0; s < RAPID_MAX_STAGES; s++) {
+    best_ms[s] = 3.4e38f;
+    best_g[s] = ctx->coop_grid;
+  }
+  rapid_status rs = RAPID_OK;
+  for (int c = 0; c < nc && rs == RAPID_OK; c++) {
+    for (int s = 0; s < RAPID_MAX_STAGES; s++) ctx->stage_grid[s] = cand[c];
+    for (int rep = 0; rep < 2 && rs == RAPID_OK; rep++) {  // the first pass warms up
+      rs = run_sequence(ctx);
+      if (rs != RAPID_OK) break;
+      rs = rapid_sync(ctx);
+      if (rs != RAPID_OK || rep == 0) continue;
+      for (int s = 0; s < ctx->nstages; s++) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev[s][0], ctx->ev[s][1]) != cudaSuccess) {
+          rs = cuda_fail(ctx);
+          break;
+        }
+        if (ms < best_ms[s]) {
+          best_ms[s] = ms;
+          best_g[s] = cand[c];
+        }
+      }
+    }
+  }
+  for (int s = 0; s < RAPID_MAX_STAGES; s++) ctx->stage_grid[s] = s < ctx->nstages ? best_g[s] : 0;
+  if (grids_out)
+    for (int s = 0; s < ctx->nstages; s++) grids_out[s] = best_g[s];
+  ctx->profiling = saved_prof;
+  ctx->graph_on = saved_graph;
+  return rs;
+}
+
 extern "C" rapid_status rapid_get_state(rapid_ctx *ctx, int32_t *stage, int32_t *level, int32_t *block,
                                         int32_t *M) {
   if (!ctx) return RAPID_EINVAL;
   if (stage) *stage = ctx->cur;
   if (level) *level = ctx->cur >= 0 ? ctx->st_level[ctx->cur] : 0;
   if (block) *block = ctx->cur >= 0 ? ctx->st_side[ctx->cur] : 0;
-  if (M) *M = ctx->cur >= 0 ? ctx->M : 0;
+  if (M) *M = ctx->cur >= 0 ? ctx->im[0].M : 0;
   return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_get_image_info(rapid_ctx *ctx, int32_t i, int32_t *H, int32_t *W, int32_t *M) {
+  if (!ctx || !ctx->image_set || i < 0 || i >= ctx->nimg) return RAPID_EINVAL;
+  if (H) *H = ctx->im[i].H;
+  if (W) *W = ctx->im[i].W;
+  if (M) *M = ctx->im[i].M;
+  return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_read_image_labels(rapid_ctx *ctx, int32_t i, int32_t *dst, int64_t row_pitch_bytes,
+                                                int32_t dst_is_device) {
+  if (!ctx || !dst) return RAPID_EINVAL;
+  if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  if (ctx->cur < 0) return RAPID_ESTATE;
+  if (i < 0 || i >= ctx->nimg) return RAPID_EINVAL;
+  const ImgHost &h = ctx->im[i];
+  const ImageDesc &d = host_desc(ctx, ctx->cur)[i];
+  if (row_pitch_bytes < 4ll * h.W || (row_pitch_bytes % 4) != 0) return RAPID_EINVAL;
+  const int side = ctx->st_side[ctx->cur];
+  if (side == 1 && h.label0 == 0) {
+    CK(cudaMemcpy2DAsync(dst, row_pitch_bytes, d.lab, 4ull * h.W, 4ull * h.W, h.H,
+                         dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  } else if (dst_is_device) {
+    CK(launch_upsample(d.lab, d.nbx, side, h.H, h.W, h.label0, dst, row_pitch_bytes / 4, ctx->stream));
+    ctx->launches++;
+  } else {
+    CK(launch_upsample(d.lab, d.nbx, side, h.H, h.W, h.label0, ctx->d_full, h.W, ctx->stream));
+    ctx->launches++;
+    CK(cudaMemcpy2DAsync(dst, row_pitch_bytes, ctx->d_full, 4ull * h.W, 4ull * h.W, h.H, cudaMemcpyDeviceToHost,
+                         ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return read_device_error(ctx);
 }
 
 extern "C" rapid_status rapid_read_labels(rapid_ctx *ctx, int32_t *dst, int64_t row_pitch_bytes,
                                           int32_t dst_is_device) {
-  if (!ctx || !dst) return RAPID_EINVAL;
-  if (ctx->sticky != RAPID_OK) return ctx->sticky;
-  if (ctx->cur < 0) return RAPID_ESTATE;
-  if (row_pitch_bytes < 4ll * ctx->W || (row_pitch_bytes % 4) != 0) return RAPID_EINVAL;
-  const int side = ctx->st_side[ctx->cur];
-  const int *lab = ctx->d_lab[ctx->cur_buf];
-  if (side == 1) {
-    CK(cudaMemcpy2DAsync(dst, row_pitch_bytes, lab, 4ull * ctx->W, 4ull * ctx->W, ctx->H,
-                         dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
-  } else if (dst_is_device) {
-    CK(launch_upsample(lab, ctx->nbx, side, ctx->H, ctx->W, dst, row_pitch_bytes / 4, ctx->stream));
-    ctx->launches++;
-  } else {
-    const long long n = (long long)ctx->H * ctx->W;
-    if (n > ctx->full_cap) {
-      cudaFree(ctx->d_full);
-      ctx->d_full = nullptr;
-      ctx->full_cap = 0;
-      if (cudaMalloc(&ctx->d_full, n * sizeof(int)) != cudaSuccess) return RAPID_ENOMEM;
-      ctx->full_cap = n;
-    }
-    CK(launch_upsample(lab, ctx->nbx, side, ctx->H, ctx->W, ctx->d_full, ctx->W, ctx->stream));
-    ctx->launches++;
-    CK(cudaMemcpy2DAsync(dst, row_pitch_bytes, ctx->d_full, 4ull * ctx->W, 4ull * ctx->W, ctx->H,
-                         cudaMemcpyDeviceToHost, ctx->stream));
-  }
-  CK(cudaStreamSynchronize(ctx->stream));
-  return read_device_error(ctx);
+  return rapid_read_image_labels(ctx, 0, dst, row_pitch_bytes, dst_is_device);
 }
 
 extern "C" rapid_status rapid_read_block_labels(rapid_ctx *ctx, int32_t *dst, int64_t capacity, int32_t *nbx_out,
@@ -592,46 +818,55 @@ extern "C" rapid_status rapid_read_block_labels(rapid_ctx *ctx, int32_t *dst, in
   if (!ctx || !dst) return RAPID_EINVAL;
   if (ctx->sticky != RAPID_OK) return ctx->sticky;
   if (ctx->cur < 0) return RAPID_ESTATE;
-  const long long n = (long long)ctx->nbx * ctx->nby;
+  const ImageDesc &d = host_desc(ctx, ctx->cur)[0];  // image 0: its global ids are its own ids
+  const long long n = (long long)d.nbx * d.nby;
   if (capacity < n) return RAPID_EINVAL;
-  CK(cudaMemcpyAsync(dst, ctx->d_lab[ctx->cur_buf], n * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(dst, d.lab, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  if (nbx_out) *nbx_out = ctx->nbx;
-  if (nby_out) *nby_out = ctx->nby;
+  if (nbx_out) *nbx_out = d.nbx;
+  if (nby_out) *nby_out = d.nby;
+  return read_device_error(ctx);
+}
+
+extern "C" rapid_status rapid_read_image_stats(rapid_ctx *ctx, int32_t i, rapid_sp_stats *dst, int64_t capacity,
+                                               int64_t *M_out) {
+  if (!ctx || !dst) return RAPID_EINVAL;
+  if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  if (ctx->cur < 0) return RAPID_ESTATE;
+  if (i < 0 || i >= ctx->nimg) return RAPID_EINVAL;
+  const ImgHost &h = ctx->im[i];
+  if (capacity < h.M) return RAPID_EINVAL;
+  CK(launch_pack_stats(ctx->st, h.label0, h.M, ctx->d_pack, ctx->stream));
+  ctx->launches++;
+  CK(cudaMemcpyAsync(dst, ctx->d_pack, (size_t)h.M * sizeof(rapid_sp_stats), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (M_out) *M_out = h.M;
   return read_device_error(ctx);
 }
 
 extern "C" rapid_status rapid_read_stats(rapid_ctx *ctx, rapid_sp_stats *dst, int64_t capacity, int64_t *M_out) {
-  if (!ctx || !dst) return RAPID_EINVAL;
-  if (ctx->sticky != RAPID_OK) return ctx->sticky;
-  if (ctx->cur < 0) return RAPID_ESTATE;
-  if (capacity < ctx->M) return RAPID_EINVAL;
-  CK(launch_pack_stats(ctx->st, ctx->d_pack, ctx->stream));
-  ctx->launches++;
-  CK(cudaMemcpyAsync(dst, ctx->d_pack, (size_t)ctx->M * sizeof(rapid_sp_stats), cudaMemcpyDeviceToHost,
-                     ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  if (M_out) *M_out = ctx->M;
-  return read_device_error(ctx);
+  return rapid_read_image_stats(ctx, 0, dst, capacity, M_out);
 }
 
-extern "C" rapid_status rapid_read_counters(rapid_ctx *ctx, rapid_counters *dst) {
+extern "C" rapid_status rapid_read_image_counters(rapid_ctx *ctx, int32_t i, rapid_counters *dst) {
   if (!ctx || !dst) return RAPID_EINVAL;
   if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  if (i < 0 || i >= (ctx->image_set ? ctx->nimg : 1)) return RAPID_EINVAL;
   std::memset(dst, 0, sizeof *dst);
   CK(cudaStreamSynchronize(ctx->stream));
   rapid_status rs = read_device_error(ctx);
   if (rs != RAPID_OK) return rs;
   long long c[CNT_N * RAPID_MAX_STAGES];
-  CK(cudaMemcpy(c, ctx->ctl.cnt, sizeof c, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(c, ctx->ctl.cnt + (long long)i * kCntStride, sizeof c, cudaMemcpyDeviceToHost));
   long long pr[PROF_N * RAPID_MAX_STAGES];
   CK(cudaMemcpy(pr, ctx->prof, sizeof pr, cudaMemcpyDeviceToHost));
   dst->num_stages = ctx->cur >= 0 ? ctx->nstages : 0;
-  dst->M = ctx->cur >= 0 ? ctx->M : 0;
+  dst->M = ctx->cur >= 0 ? ctx->im[i].M : 0;
   dst->launches = ctx->launches;
-  for (int i = 0; i < dst->num_stages; i++) {
-    rapid_stage_counters &o = dst->stage[i];
-    const long long *ci = c + (long long)CNT_N * i;
+  for (int s = 0; s < dst->num_stages; s++) {
+    rapid_stage_counters &o = dst->stage[s];
+    const long long *ci = c + (long long)CNT_N * s;
     o.level = (int32_t)ci[CNT_LEVEL];
     o.block = (int32_t)ci[CNT_SIDE];
     o.sweeps = (int32_t)ci[CNT_SWEEPS];
@@ -647,13 +882,17 @@ extern "C" rapid_status rapid_read_counters(rapid_ctx *ctx, rapid_counters *dst)
     o.merge_searches = ci[CNT_SEARCHES];
     o.merge_cache_hits = ci[CNT_CACHE_HITS];
     o.kernel_ms = -1.0f;
-    for (int j = 0; j < PROF_N; j++) o.section_ms[j] = ctx->profiling ? (float)(pr[i * PROF_N + j] * 1e-6) : 0.0f;
-    if (ctx->profiling && ctx->ev_ok[i] && i <= ctx->cur) {
+    for (int j = 0; j < PROF_N; j++) o.section_ms[j] = ctx->profiling ? (float)(pr[s * PROF_N + j] * 1e-6) : 0.0f;
+    if (ctx->profiling && ctx->ev_ok[s] && s <= ctx->cur) {
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, ctx->ev[i][0], ctx->ev[i][1]) == cudaSuccess) o.kernel_ms = ms;
+      if (cudaEventElapsedTime(&ms, ctx->ev[s][0], ctx->ev[s][1]) == cudaSuccess) o.kernel_ms = ms;
     }
   }
   return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_read_counters(rapid_ctx *ctx, rapid_counters *dst) {
+  return rapid_read_image_counters(ctx, 0, dst);
 }
 
 extern "C" rapid_status rapid_set_profiling(rapid_ctx *ctx, int32_t on) {

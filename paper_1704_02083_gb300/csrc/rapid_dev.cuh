@@ -13,6 +13,12 @@
 //   tiles   per (tile, phase class) scan record: stamp, label set, counts
 // Position sums of a block are not stored: a block is an axis-aligned rectangle of
 // full-res pixels, so its count and x/y sums follow from its corners.
+//
+// A context refines a batch of images together (a single image is a batch of one): every
+// image keeps its own block grid, label map and sum levels, its labels are a contiguous
+// range of one global id space (so S and the merge state are shared arrays), and its
+// tiles are a contiguous range of one global tile index space.  Images never share a
+// label, so each evolves exactly as it would alone.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -70,35 +76,71 @@ struct DevMerge {
   int *cache_nb;    // [M * kCacheLabels] those neighbour labels
 };
 
+// Images one context refines together (one launch per stage covers all of them).
+constexpr int kMaxBatch = 64;
+
 struct DevCtl {
   unsigned int *bar;             // [0] arrivals (monotone within a launch)
   int *err;                      // first device error (0 = none)
   long long spin_ns;             // give-up time of one barrier wait
-  unsigned long long *changes;   // [3] moves + merges of the sweep, rotating slots
-  int *last_merge;               // stamp (2g + 1) of the last accepted merge of the launch
-  long long *cnt;                // this stage's counters [CNT_N]
+  unsigned long long *changes;   // [nimg][3] moves + merges of the sweep per image, rotating slots
+  int *last_merge;               // [nimg] stamp (2g + 1) of the image's last accepted merge
+  long long *cnt;                // image 0's counters of this stage [CNT_N]; image i at + i * cnt_stride
   long long *prof;               // this stage's section times [PROF_N] in ns, or null
 };
 
-struct StageArgs {
+// Control block of a context: barrier, error word, merge counts, per-image merge stamps and
+// sweep changes, per-(image, stage) counters, per-stage section times.  Every launch
+// clears [0, 8) and [16, reset_end); the error word persists.
+struct CtlLayout {
+  size_t last_merge, changes, cnt, prof, reset_end, total;
+};
+inline CtlLayout ctl_layout(int nimg) {
+  CtlLayout c;
+  c.last_merge = 64;
+  c.changes = (c.last_merge + 4 * (size_t)nimg + 7) / 8 * 8;
+  c.reset_end = c.changes + 24 * (size_t)nimg;
+  c.cnt = (c.reset_end + 255) / 256 * 256;
+  c.prof = c.cnt + sizeof(long long) * CNT_N * 32 * (size_t)nimg;
+  c.total = c.prof + sizeof(long long) * PROF_N * 32;
+  return c;
+}
+constexpr int kCntStride = CNT_N * 32;  // counters of one image: 32 stages x CNT_N
+
+// One image of a stage launch.
+struct ImageDesc {
   int H, W;           // full-res image
-  int side;           // block side s (full-res px)
   int nbx, nby;       // block grid ceil(W/s) x ceil(H/s)
-  int level, f, k;    // level, its factor, coarse cells per block side (s / f)
-  int Wl, Hl;         // level dims
+  int ntx, nty;       // tile grid
+  int Wl, Hl;         // dims of the sum level the stage reads
+  int tile0;          // first global tile index
+  int label0, M;      // global label ids label0 .. label0 + M - 1
+  int blk0;           // first global block index (orders merge requests)
+  int use_filter;     // 1: single-precision decisions with certified bounds, binary64 when undecided
+  int pad;
   const unsigned char *img;
   long long img_pitch;
-  const int4 *pyr;    // level sums (f > 1), else unused
-  int *lab;           // nby x nbx labels
+  const int4 *pyr;    // sum level (f > 1), else unused
+  int *lab;           // nby x nbx labels (global ids)
+  double lam_pos;
+  float lam_pos_f;
+  float pad2;
+};
+
+struct StageArgs {
+  int side;           // block side s (full-res px)
+  int level, f, k;    // level, the sum level's factor, its cells per block side (s / f)
+  const ImageDesc *imgs;  // [nimg] in device memory
+  ImageDesc img0;         // imgs[0] (a launch over one image reads it from here)
+  int nimg;
+  int ntiles;         // tiles of all images
   int *trec;          // tile records [ntiles * 9 * kRecInts]
-  int ntx, nty;       // tile grid
   DevStats st;
   DevMerge mg;
   DevCtl ctl;
   int imp_on, imp_rule;
-  double lam_pos, lam_b2;
-  float lam_pos_f, lam_b2_f;
-  int use_filter;     // 1: single-precision decisions with certified bounds, binary64 when undecided
+  double lam_b2;
+  float lam_b2_f;
   int verify_filter;  // 1: also decide every block in binary64 and count disagreements
   int skip_tiles;     // 1: skip tiles whose inputs did not change since their last scan
   int size_mode, lo_num, lo_den, hi_num, hi_den;
@@ -220,18 +262,29 @@ __device__ inline bool grid_sync(const DevCtl &c, unsigned &epoch) {
 }
 
 // ---------------------------------------------------------------- block sums
+__device__ __forceinline__ unsigned long long l2_evict_first_policy() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ unsigned ld_u8_hint(const unsigned char *p, unsigned long long pol) {
+  unsigned v;
+  asm volatile("ld.global.L2::cache_hint.u8 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
 struct BlockSums {
   long long w, r, g, b, x, y;
   int bw, bh;
 };
 
-// Sums of block (bx, by) at the current stage: colour from the level's coarse cells
-// (or the image at f = 1), count and position from the block rectangle
+// Sums of block (bx, by) of image im at the current stage: colour from the sum level's
+// cells (or the image at f = 1), count and position from the block rectangle
 // [s bx, min(s bx + s, W)) x [s by, min(s by + s, H)).
-__device__ inline BlockSums block_sums(const StageArgs &a, int bx, int by) {
+__device__ inline BlockSums block_sums(const StageArgs &a, const ImageDesc &im, int bx, int by) {
   BlockSums o;
   int x0 = bx * a.side, y0 = by * a.side;
-  int x1 = min(x0 + a.side, a.W), y1 = min(y0 + a.side, a.H);
+  int x1 = min(x0 + a.side, im.W), y1 = min(y0 + a.side, im.H);
   o.bw = x1 - x0;
   o.bh = y1 - y0;
   o.w = (long long)o.bw * o.bh;
@@ -239,20 +292,23 @@ __device__ inline BlockSums block_sums(const StageArgs &a, int bx, int by) {
   o.y = (long long)o.bw * (((long long)(y0 + y1 - 1) * o.bh) >> 1);
   long long r = 0, g = 0, b = 0;
   if (a.f == 1) {
+    // the image is read sparsely (boundary blocks only): mark its lines first to leave L2,
+    // ahead of the label map and tile records that every phase re-reads
+    const unsigned long long pol = l2_evict_first_policy();
     for (int yy = y0; yy < y1; yy++) {
-      const unsigned char *row = a.img + (long long)yy * a.img_pitch + 3ll * x0;
+      const unsigned char *row = im.img + (long long)yy * im.img_pitch + 3ll * x0;
       for (int xx = 0; xx < o.bw; xx++) {
-        r += row[3 * xx];
-        g += row[3 * xx + 1];
-        b += row[3 * xx + 2];
+        r += ld_u8_hint(row + 3 * xx, pol);
+        g += ld_u8_hint(row + 3 * xx + 1, pol);
+        b += ld_u8_hint(row + 3 * xx + 2, pol);
       }
     }
   } else {
     int X0 = bx * a.k, Y0 = by * a.k;
-    int X1 = min(X0 + a.k, a.Wl), Y1 = min(Y0 + a.k, a.Hl);
+    int X1 = min(X0 + a.k, im.Wl), Y1 = min(Y0 + a.k, im.Hl);
     for (int Y = Y0; Y < Y1; Y++)
       for (int X = X0; X < X1; X++) {
-        int4 c = a.pyr[(long long)Y * a.Wl + X];
+        int4 c = im.pyr[(long long)Y * im.Wl + X];
         r += c.x;
         g += c.y;
         b += c.z;
@@ -341,7 +397,7 @@ __device__ __forceinline__ void atomic_add_i64(long long *p, long long v) {
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_stage(const StageArgs &a, int grid, int block, cudaStream_t s);
 int stage_block_threads();
-const void *stage_kernel_ptr();
+const void *stage_kernel_ptr(bool batch);
 
 // Carve the per-label arrays of M labels from `base` (256-byte aligned pieces); returns the
 // bytes used, or 0 when they do not fit in `cap` bytes.  label_arrays_bytes(M) is the size.

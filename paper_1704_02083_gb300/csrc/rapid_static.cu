@@ -25,15 +25,16 @@
 namespace rapid {
 cudaError_t launch_pyramid(const unsigned char *img, long long pitch, int H, int W, int f, int Wl, int Hl,
                            int4 *out, cudaStream_t s);
-cudaError_t launch_seed(const StageArgs &a, int gx, int gy, cudaStream_t s, int *launches);
-cudaError_t launch_recompute(const StageArgs &a, cudaStream_t s, int *launches);
+cudaError_t launch_seed(const StageArgs &a, const ImageDesc *ims, const int *gx, const int *gy, int n,
+                        cudaStream_t s, int *launches);
+cudaError_t launch_recompute(const StageArgs &a, const ImageDesc *ims, int n, cudaStream_t s, int *launches);
 cudaError_t launch_split(const int *src, int snbx, int *dst, int dnbx, int dnby, cudaStream_t s);
-cudaError_t launch_predict(const int *lab, int nbx, int nby, const DevStats &st, long long hT, cudaStream_t s,
+cudaError_t launch_predict(const ImageDesc *ims, int n, const DevStats &st, long long hT, cudaStream_t s,
                            int *launches);
-cudaError_t launch_upsample(const int *lab, int nbx, int side, int H, int W, int *dst, long long pitch_elems,
-                            cudaStream_t s);
-cudaError_t launch_pack_stats(const DevStats &st, rapid_sp_stats *out, cudaStream_t s);
-cudaError_t launch_init_counters(long long *cnt, const Schedule &sch, cudaStream_t s);
+cudaError_t launch_upsample(const int *lab, int nbx, int side, int H, int W, int label0, int *dst,
+                            long long pitch_elems, cudaStream_t s);
+cudaError_t launch_pack_stats(const DevStats &st, int label0, int M, rapid_sp_stats *out, cudaStream_t s);
+cudaError_t launch_init_counters(long long *cnt, const Schedule &sch, int n, cudaStream_t s);
 }  // namespace rapid
 
 using namespace rapid;
@@ -103,14 +104,12 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
 
   // Levels and stages (same schedule as rapid_run).
   const int L = p->num_levels;
-  int f[kMaxLevelsStatic + 1], Wl[kMaxLevelsStatic + 1], Hl[kMaxLevelsStatic + 1];
+  int f[kMaxLevelsStatic + 1];
   for (int l = 1; l <= L; l++) {
     long long ff = 1;
     for (int i = 0; i < L - l; i++) ff *= p->ratio_C;
     if (ff > (1 << 20)) return RAPID_EINVAL;
     f[l] = (int)ff;
-    Wl[l] = cdiv(W, f[l]);
-    Hl[l] = cdiv(H, f[l]);
   }
   int nst = 0, lev[RAPID_MAX_STAGES], side[RAPID_MAX_STAGES];
   int s = p->init_block < f[1] ? f[1] : p->init_block;
@@ -149,8 +148,8 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   rapid_status rs = scratch_on_current_device(&base);
   if (rs != RAPID_OK) return rs;
   Carve cv{base, 0, kStaticScratchBytes};
-  const size_t ctl_bytes = 128 + sizeof(long long) * CNT_N * RAPID_MAX_STAGES;
-  unsigned char *ctl = (unsigned char *)cv.take(ctl_bytes);
+  const CtlLayout cl = ctl_layout(1);
+  unsigned char *ctl = (unsigned char *)cv.take(cl.total);
   int sf[kMaxSumLevels];
   const int nsf = sum_factors(f, L, side[0], sf);
   int4 *pyr[kMaxSumLevels] = {nullptr};
@@ -160,33 +159,66 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   const int ntx_max = (cdiv(W, side[nst - 1]) + kTileW - 1) / kTileW;
   const int nty_max = (cdiv(H, side[nst - 1]) + kTileH - 1) / kTileH;
   int *trec = (int *)cv.take((size_t)ntx_max * nty_max * 9 * kRecInts * sizeof(int));
+  ImageDesc *d_desc = (ImageDesc *)cv.take((size_t)nst * sizeof(ImageDesc));
   DevStats st;
   DevMerge mg;
   std::memset(&st, 0, sizeof st);
   std::memset(&mg, 0, sizeof mg);
   const size_t lbytes = label_arrays_bytes(M);
   void *lblock = cv.take(lbytes);
-  bool ok = ctl && lab[0] && lab[1] && trec && lblock;
+  bool ok = ctl && lab[0] && lab[1] && trec && d_desc && lblock;
   for (int l = 0; l < nsf; l++) ok = ok && pyr[l];
   if (!ok) return RAPID_ERANGE;  // this image and parameter set need more than the fixed array
   carve_label_arrays(lblock, lbytes, M, &st, &mg);
   DevCtl c;
   c.bar = (unsigned *)(ctl + 0);
   c.err = (int *)(ctl + 8);
-  c.last_merge = (int *)(ctl + 12);
   mg.req_count = (int *)(ctl + 16);
   mg.found_count = (int *)(ctl + 24);
   mg.acc_count = (int *)(ctl + 32);
-  c.changes = (unsigned long long *)(ctl + 40);
-  c.cnt = (long long *)(ctl + 128);
+  c.last_merge = (int *)(ctl + cl.last_merge);
+  c.changes = (unsigned long long *)(ctl + cl.changes);
+  c.cnt = (long long *)(ctl + cl.cnt);
   c.prof = nullptr;
   c.spin_ns = p->spin_limit_ns;
+
+  // One image descriptor per stage (the stage kernel handles batches; this is a batch of one).
+  const double lam_pos = p->lambda_pos0 * ((double)M / ((double)H * (double)W));
+  ImageDesc desc[RAPID_MAX_STAGES];
+  std::memset(desc, 0, sizeof desc);
+  int stage_f[RAPID_MAX_STAGES];
+  for (int i = 0; i < nst; i++) {
+    ImageDesc &d = desc[i];
+    int fi = 1, li = -1;
+    for (int l = 0; l < nsf; l++)
+      if (sf[l] <= side[i]) {
+        fi = sf[l];
+        li = l;
+      }
+    stage_f[i] = fi;
+    d.H = H;
+    d.W = W;
+    d.nbx = cdiv(W, side[i]);
+    d.nby = cdiv(H, side[i]);
+    d.ntx = (d.nbx + kTileW - 1) / kTileW;
+    d.nty = (d.nby + kTileH - 1) / kTileH;
+    d.Wl = cdiv(W, fi);
+    d.Hl = cdiv(H, fi);
+    d.M = M;
+    d.use_filter = p->use_filter && side[i] <= 4096 && W < (1 << 22) && H < (1 << 22);
+    d.img = rgb_dev;
+    d.img_pitch = rgb_pitch_bytes;
+    d.pyr = li >= 0 ? pyr[li] : nullptr;
+    d.lab = lab[i & 1];
+    d.lam_pos = lam_pos;
+    d.lam_pos_f = (float)lam_pos;
+  }
 
   // Cooperative grid size for the stage kernel (no allocation involved).
   int dev = 0, nsm = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_ptr(), stage_block_threads(), 0) !=
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_ptr(false), stage_block_threads(), 0) !=
           cudaSuccess ||
       per_sm < 1)
     return RAPID_ECUDA;
@@ -197,7 +229,8 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   } while (0)
 
   // Start from a clean control block: barrier, error word, request counts, counters.
-  CKS(cudaMemsetAsync(ctl, 0, ctl_bytes, stream));
+  CKS(cudaMemsetAsync(ctl, 0, cl.total, stream));
+  CKS(cudaMemcpyAsync(d_desc, desc, (size_t)nst * sizeof(ImageDesc), cudaMemcpyHostToDevice, stream));
   for (int l = 0; l < nsf; l++)
     CKS(launch_pyramid(rgb_dev, rgb_pitch_bytes, H, W, sf[l], cdiv(W, sf[l]), cdiv(H, sf[l]), pyr[l], stream));
   Schedule sch;
@@ -207,18 +240,15 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
     sch.level[i] = lev[i];
     sch.side[i] = side[i];
   }
-  CKS(launch_init_counters(c.cnt, sch, stream));
+  CKS(launch_init_counters(c.cnt, sch, 1, stream));
 
   StageArgs a;
   std::memset(&a, 0, sizeof a);
-  a.H = H;
-  a.W = W;
-  a.img = rgb_dev;
-  a.img_pitch = rgb_pitch_bytes;
+  a.nimg = 1;
   a.st = st;
   a.mg = mg;
-  a.lam_pos = p->lambda_pos0 * ((double)M / ((double)H * (double)W));
   a.lam_b2 = 2.0 * p->lambda_b;
+  a.lam_b2_f = (float)a.lam_b2;
   a.imp_rule = p->importance_rule;
   a.size_mode = p->size_mode;
   a.lo_num = p->lo_num;
@@ -227,63 +257,45 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   a.hi_den = p->hi_den;
   a.max_sweeps = p->max_sweeps;
   a.trec = trec;
-  a.lam_pos_f = (float)a.lam_pos;
-  a.lam_b2_f = (float)a.lam_b2;
   a.verify_filter = p->verify_filter;
   a.skip_tiles = p->skip_tiles;
-  int buf = 0, nbx = nbx0, nby = nby0, launches = 0;
+  int launches = 0;
   auto set_stage = [&](int i) {
     a.side = side[i];
-    a.nbx = nbx;
-    a.nby = nby;
     a.level = lev[i];
-    a.f = 1;
-    a.pyr = nullptr;
-    for (int l = 0; l < nsf; l++)
-      if (sf[l] <= a.side) {
-        a.f = sf[l];
-        a.pyr = pyr[l];
-      }
+    a.f = stage_f[i];
     a.k = a.side / a.f;
-    a.Wl = cdiv(W, a.f);
-    a.Hl = cdiv(H, a.f);
-
-    a.lab = lab[buf];
+    a.imgs = d_desc + i;
+    a.img0 = desc[i];
+    a.ntiles = desc[i].ntx * desc[i].nty;
     a.ctl = c;
     a.ctl.cnt = c.cnt + (long long)CNT_N * i;
-    a.ntx = (nbx + kTileW - 1) / kTileW;
-    a.nty = (nby + kTileH - 1) / kTileH;
-    a.use_filter = p->use_filter && a.side <= 4096 && W < (1 << 22) && H < (1 << 22);
   };
   set_stage(0);
-  CKS(launch_seed(a, gx, gy, stream, &launches));
+  const int gxa[1] = {gx}, gya[1] = {gy};
+  CKS(launch_seed(a, &desc[0], gxa, gya, 1, stream, &launches));
   for (int i = 0; i < nst; i++) {
     if (i > 0) {
       if (p->predict && lev[i] >= 2 && lev[i - 1] < 2) {
-        CKS(launch_predict(lab[buf], nbx, nby, st, p->h_T, stream, &launches));
+        CKS(launch_predict(&desc[i - 1], 1, st, p->h_T, stream, &launches));
         a.imp_on = 1;
       }
-      const int dnbx = cdiv(W, side[i]), dnby = cdiv(H, side[i]);
-      CKS(launch_split(lab[buf], nbx, lab[buf ^ 1], dnbx, dnby, stream));
-      buf ^= 1;
-      nbx = dnbx;
-      nby = dnby;
+      CKS(launch_split(desc[i - 1].lab, desc[i - 1].nbx, desc[i].lab, desc[i].nbx, desc[i].nby, stream));
       set_stage(i);
-      if (!p->reuse && lev[i] != lev[i - 1]) CKS(launch_recompute(a, stream, &launches));
+      if (!p->reuse && lev[i] != lev[i - 1]) CKS(launch_recompute(a, &desc[i], 1, stream, &launches));
     }
     CKS(cudaMemsetAsync(c.bar, 0, 8, stream));
-    CKS(cudaMemsetAsync(ctl + 12, 0, 116, stream));  // last merge, request / found counts, sweep changes, tile counters
-
+    CKS(cudaMemsetAsync(ctl + 16, 0, cl.reset_end - 16, stream));  // merge stamps, counts, sweep changes
     CKS(launch_stage(a, nsm * per_sm, stage_block_threads(), stream));
   }
   // Outputs into the caller's buffers.
-  const int sl = side[nst - 1];
-  if (sl == 1)
-    CKS(cudaMemcpy2DAsync(labels_dev, labels_pitch_bytes, lab[buf], 4ull * W, 4ull * W, H,
-                          cudaMemcpyDeviceToDevice, stream));
+  const ImageDesc &dl = desc[nst - 1];
+  if (side[nst - 1] == 1)
+    CKS(cudaMemcpy2DAsync(labels_dev, labels_pitch_bytes, dl.lab, 4ull * W, 4ull * W, H, cudaMemcpyDeviceToDevice,
+                          stream));
   else
-    CKS(launch_upsample(lab[buf], nbx, sl, H, W, labels_dev, labels_pitch_bytes / 4, stream));
-  CKS(launch_pack_stats(st, stats_dev, stream));
+    CKS(launch_upsample(dl.lab, dl.nbx, side[nst - 1], H, W, 0, labels_dev, labels_pitch_bytes / 4, stream));
+  CKS(launch_pack_stats(st, 0, M, stats_dev, stream));
   int err = 0;
   CKS(cudaMemcpyAsync(&err, c.err, sizeof err, cudaMemcpyDeviceToHost, stream));
   CKS(cudaStreamSynchronize(stream));

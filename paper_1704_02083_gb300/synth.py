@@ -166,6 +166,47 @@ WORKLOADS = {
 }
 
 
+# Batches of uneven tiles (the adaptive data partitioning of whole slides, Sec. 3.3): tile
+# sizes, one generator call per tile with cell count and superpixel count proportional to
+# its area.
+BATCHES = {
+    # 64 tiles, long side from {512, 1024, 2048, 3072, 4096}, aspect U[1, 2] with the short
+    # side rounded down to a multiple of 32, 1 Voronoi cell per 8192 px and 1 superpixel per
+    # 4096 px; the 4096^2 tile's 3-level schedule.
+    "batch64_l3": dict(n=64, seed=3, px_per_cell=8192, px_per_superpixel=4096,
+                       params=dict(num_levels=3, ratio_C=4, init_block=32, final_grain=1,
+                                   size_mode=2, predict=1, reuse=1)),
+}
+
+
+def batch_sizes(n: int, seed: int):
+    """(H, W) of each tile of a batch, from the seed alone."""
+    rng = np.random.default_rng(seed)
+    sizes = []
+    for _ in range(n):
+        long_side = int(rng.choice(np.array([512, 1024, 2048, 3072, 4096])))
+        aspect = 1.0 + float(rng.integers(0, 1 << 20)) / float(1 << 20)  # U[1, 2)
+        short_side = max(32, int(long_side / aspect) // 32 * 32)
+        if rng.integers(0, 2):
+            sizes.append((short_side, long_side))
+        else:
+            sizes.append((long_side, short_side))
+    return sizes
+
+
+def batch_workload(name: str, count: int | None = None):
+    """The tiles of a batch workload (the first ``count`` when given): RGB arrays and the
+    superpixel count K of each."""
+    b = BATCHES[name]
+    sizes = batch_sizes(b["n"], b["seed"])[:count]
+    imgs, K = [], []
+    for i, (H, W) in enumerate(sizes):
+        cells = max(1, (H * W) // b["px_per_cell"])
+        imgs.append(he_image(H, W, cells, b["seed"] * 1000 + i).rgb)
+        K.append(max(1, (H * W) // b["px_per_superpixel"]))
+    return imgs, K
+
+
 def workload_image(name: str) -> SynthImage:
     w = WORKLOADS[name]
     return he_image(w["H"], w["W"], w["n_cells"], w["seed"])

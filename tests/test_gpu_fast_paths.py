@@ -58,3 +58,42 @@ def test_tiles_are_skipped_on_long_stages():
     stages, _ = gpu_counters(img, num_levels=3, ratio_C=4, init_block=32, K=320, predict=1)
     last = stages[-1]
     assert last.tiles_skipped > 0 and last.tiles_scanned > 0
+
+
+def _run_with_grids(rgb, grids, autotune=False, **params):
+    import torch
+
+    import paper_1704_02083_gb300 as pkg
+
+    with pkg.Context(stream=torch.cuda.current_stream(), **params) as ctx:
+        ctx.set_image(torch.from_numpy(np.ascontiguousarray(rgb)).cuda())
+        chosen = ctx.autotune() if autotune else None
+        if grids is not None:
+            ctx.set_stage_grids(grids)
+        ctx.run()
+        st = ctx.stats()
+        return ctx.labels(), np.stack([st[f] for f in ("n", "sum_r", "sum_x")], 1), ctx.counters_array(), chosen
+
+
+@pytest.mark.parametrize("name,rgb,params", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_launch_grid_changes_nothing(name, rgb, params):
+    """Any number of CTAs per stage (one, odd counts, the full grid) gives the same run."""
+    ref = _run_with_grids(rgb, None, **params)
+    for grids in ([1] * 8, [3, 1, 7, 2, 5, 152, 9, 4], [2 ** i for i in range(8)]):
+        got = _run_with_grids(rgb, grids, **params)
+        for x, y in zip(got[:3], ref[:3]):
+            np.testing.assert_array_equal(x, y, err_msg=f"grids={grids}")
+
+
+def test_autotune_picks_valid_grids_and_keeps_results():
+    import torch
+
+    rgb, params = CASES[1][1], CASES[1][2]
+    ref = _run_with_grids(rgb, None, **params)
+    lab, st, cnt, chosen = _run_with_grids(rgb, None, autotune=True, **params)
+    full = torch.cuda.get_device_properties(0).multi_processor_count
+    assert len(chosen) == cnt.shape[0]
+    assert all(1 <= g <= full for g in chosen)
+    np.testing.assert_array_equal(lab, ref[0])
+    np.testing.assert_array_equal(st, ref[1])
+    np.testing.assert_array_equal(cnt, ref[2])
