@@ -193,6 +193,25 @@ def kernel_source_sha256():
     return h.hexdigest()
 
 
+# ---------------------------------------------------------------- replicas
+def max_over_ranks(v: float, dist) -> float:
+    """The largest value over all ranks (the slowest replica's time); v itself with one rank."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return v
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, steps: int, seconds_local: float, dist) -> float:
+    """Units per second of the whole job: every rank's units over the slowest rank's time
+    (replicas do the same work, so the job ends when the slowest one does)."""
+    world = dist.get_world_size() if dist is not None and dist.is_initialized() else 1
+    return world * units_per_rank * steps / max_over_ranks(seconds_local, dist)
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -284,12 +303,8 @@ def run_rapid(args, rank, world, local):
     c1 = ctx.counters(0)
     launches_per_step = (c1.launches - c0.launches) / max(1, args.steps)
 
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * npx * args.steps / (total_ms / 1e3) / 1e6
+    total_ms = max_over_ranks(sum(step_ms), dist)
+    value = whole_job_rate(npx, args.steps, total_ms / 1e3, dist) / 1e6
 
     # end to end through the C ABI from pinned host memory: H2D images, run, D2H labels + stats
     e2e = None
@@ -315,12 +330,8 @@ def run_rapid(args, rank, world, local):
             if it >= args.warmup:
                 times.append(time.perf_counter() - t)
         e2e_ctx.close()
-        tot = sum(times)
-        if world > 1:
-            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        e2e = {"value": world * npx * len(times) / tot / 1e6, "unit": UNIT, "h2d_bytes_per_step": 3 * npx,
+        e2e = {"value": whole_job_rate(npx, len(times), sum(times), dist) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * npx,
                "d2h_bytes_per_step": 4 * npx + sum(Ms) * pkg.SP_STATS_DTYPE.itemsize}
 
     cpu = None
