@@ -215,6 +215,51 @@ rapid_status rapid_read_image_counters(rapid_ctx *ctx, int32_t i, rapid_counters
 rapid_status rapid_set_stage_grids(rapid_ctx *ctx, const int32_t *grids, int32_t n);
 rapid_status rapid_autotune(rapid_ctx *ctx, int32_t *grids_out);
 
+/* ---- Learned block scorer (pruning of the boundary-block queue) ----
+ * A 3-layer 3x3 convolutional net over 9 per-block features (colour gain of moving to each
+ * of the up to 4 neighbour labels, boundary count, level, coarse importance, block side,
+ * misfit to the own label) predicts which boundary blocks will move in a stage.  It only
+ * prunes which eligible blocks the exact topology and energy tests evaluate; every move is
+ * still decided by the exact test (Eq. operation).  Weights and activations are bf16 with
+ * fp32 sums.  Weights are RAPID_SCORER_PARAMS floats in the order W1[16][9][3][3], b1[16],
+ * W2[16][16][3][3], b2[16], W3[16][3][3], b3 (conv weights [out][in][ky][kx], zero padding
+ * outside the image at every layer). */
+#define RAPID_SCORER_PARAMS 3777
+#define RAPID_SCORER_FEATURES 9
+
+/* Pruned refinement: with weights (host, RAPID_SCORER_PARAMS floats; NULL = off) every stage
+ * first scores its blocks (score = sigmoid of the net's output) and sweeps only over the
+ * eligible blocks scoring >= threshold until a sweep changes nothing; then it sweeps over
+ * every block until a sweep changes nothing (the full sweep is the fallback), within
+ * max_sweeps in all.  Results then differ from the plain method's (quality is judged
+ * against it); with threshold 0 they are the same.  Synchronises. */
+rapid_status rapid_set_scorer(rapid_ctx *ctx, const float *weights, float threshold);
+
+/* The current stage's features of image i ([nby][nbx][RAPID_SCORER_FEATURES] fp32, device
+ * buffer dst of nby*nbx*9 floats), and scores ([nby][nbx] fp32, device buffer) under the
+ * given weights (host).  Stream-ordered.  ESTATE before seeding. */
+rapid_status rapid_scorer_features(rapid_ctx *ctx, int32_t i, float *dst_dev);
+rapid_status rapid_scorer_scores(rapid_ctx *ctx, int32_t i, const float *weights, float *dst_dev);
+
+/* Training data and training.  A trainer holds up to `capacity` samples on the device.
+ * While a context logs into it (rapid_set_logging), every stage appends one sample per
+ * block that was a boundary block at the stage start: its 7x7 patch of features (the net's
+ * receptive field) and y = 1 when the block's label changed during the stage.  Blocks with
+ * y = 0 are kept with probability neg_rate (a hash of image, stage and block decides).
+ * rapid_trainer_fit trains the net on the samples with Adam (fp32 master weights, bf16
+ * forward) on the loss pos_weight * y * -log p + (1 - y) * -log(1 - p), in minibatches of
+ * `batch` over `epochs` shuffled passes (shuffle seeded by `seed`), starting from `init`
+ * (host, NULL = a seeded random start) and writes the weights to `weights_out` (host) and
+ * the mean loss of each epoch to `epoch_loss` (host, `epochs` floats, may be NULL).
+ * Synchronises. */
+typedef struct rapid_trainer rapid_trainer;
+rapid_status rapid_trainer_create(int64_t capacity, float neg_rate, rapid_trainer **out);
+rapid_status rapid_set_logging(rapid_ctx *ctx, rapid_trainer *t);
+rapid_status rapid_trainer_count(rapid_trainer *t, int64_t *samples, int64_t *positives);
+rapid_status rapid_trainer_fit(rapid_trainer *t, int32_t epochs, int32_t batch, float lr, float pos_weight,
+                               uint64_t seed, const float *init, float *weights_out, float *epoch_loss);
+void rapid_trainer_destroy(rapid_trainer *t);
+
 /* Graph mode (0 = off, the default): rapid_run captures the schedule into a CUDA graph on
  * its first call after rapid_set_images and replays it afterwards (profiling events are
  * captured as event-record nodes, so kernel_ms keeps working).  Needs a non-default stream

@@ -104,6 +104,14 @@ def lib() -> C.CDLL:
         "rapid_read_image_counters": (i32, [P, i32, C.POINTER(rapid_counters)]),
         "rapid_set_graph": (i32, [P, i32]),
         "rapid_set_stage_grids": (i32, [P, pi32, i32]),
+        "rapid_set_scorer": (i32, [P, P, C.c_float]),
+        "rapid_scorer_features": (i32, [P, i32, P]),
+        "rapid_scorer_scores": (i32, [P, i32, P, P]),
+        "rapid_trainer_create": (i32, [i64, C.c_float, C.POINTER(P)]),
+        "rapid_set_logging": (i32, [P, P]),
+        "rapid_trainer_count": (i32, [P, pi64, pi64]),
+        "rapid_trainer_fit": (i32, [P, i32, i32, C.c_float, C.c_float, C.c_uint64, P, P, P]),
+        "rapid_trainer_destroy": (None, [P]),
         "rapid_autotune": (i32, [P, pi32]),
         "rapid_status_string": (C.c_char_p, [i32]),
         "rapid_destroy": (None, [P]),
@@ -250,6 +258,69 @@ def rapid_autotune(ctx: int):
     out = (C.c_int32 * RAPID_MAX_STAGES)()
     _check(lib().rapid_autotune(ctx, out), "rapid_autotune")
     return list(out)
+
+
+RAPID_SCORER_PARAMS = 3777
+RAPID_SCORER_FEATURES = 9
+
+
+def _f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.size != RAPID_SCORER_PARAMS:
+        raise ValueError(f"expected {RAPID_SCORER_PARAMS} scorer parameters")
+    return a
+
+
+def rapid_set_scorer(ctx: int, weights, threshold: float):
+    """Pruned refinement with the learned scorer (weights None = off)."""
+    if weights is None:
+        _check(lib().rapid_set_scorer(ctx, None, 0.0), "rapid_set_scorer")
+        return
+    w = _f32(weights)
+    _check(lib().rapid_set_scorer(ctx, w.ctypes.data, float(threshold)), "rapid_set_scorer")
+
+
+def rapid_scorer_features(ctx: int, i: int, dst_dev_ptr: int):
+    _check(lib().rapid_scorer_features(ctx, i, dst_dev_ptr), "rapid_scorer_features")
+
+
+def rapid_scorer_scores(ctx: int, i: int, weights, dst_dev_ptr: int):
+    w = _f32(weights)
+    _check(lib().rapid_scorer_scores(ctx, i, w.ctypes.data, dst_dev_ptr), "rapid_scorer_scores")
+
+
+def rapid_trainer_create(capacity: int, neg_rate: float) -> int:
+    h = C.c_void_p()
+    _check(lib().rapid_trainer_create(capacity, float(neg_rate), C.byref(h)), "rapid_trainer_create")
+    return h.value
+
+
+def rapid_set_logging(ctx: int, trainer: int | None):
+    _check(lib().rapid_set_logging(ctx, trainer), "rapid_set_logging")
+
+
+def rapid_trainer_count(trainer: int):
+    n, p = C.c_int64(), C.c_int64()
+    _check(lib().rapid_trainer_count(trainer, C.byref(n), C.byref(p)), "rapid_trainer_count")
+    return n.value, p.value
+
+
+def rapid_trainer_fit(trainer: int, epochs: int, batch: int, lr: float, pos_weight: float, seed: int,
+                      init=None):
+    """Returns (weights, per-epoch mean loss)."""
+    w = np.zeros(RAPID_SCORER_PARAMS, np.float32)
+    loss = np.zeros(epochs, np.float32)
+    ip = _f32(init).ctypes.data if init is not None else None
+    keep = init
+    _check(lib().rapid_trainer_fit(trainer, epochs, batch, float(lr), float(pos_weight), seed, ip, w.ctypes.data,
+                                   loss.ctypes.data), "rapid_trainer_fit")
+    del keep
+    return w, loss
+
+
+def rapid_trainer_destroy(trainer: int):
+    if trainer:
+        lib().rapid_trainer_destroy(trainer)
 
 
 def rapid_set_profiling(ctx: int, on: bool):
@@ -446,6 +517,12 @@ class Context:
     def set_graph(self, on: bool = True):
         rapid_set_graph(self.h, on)
 
+    def set_scorer(self, weights, threshold: float = 0.3):
+        rapid_set_scorer(self.h, weights, threshold)
+
+    def set_logging(self, trainer):
+        rapid_set_logging(self.h, trainer.h if trainer is not None else None)
+
     def set_stage_grids(self, grids):
         rapid_set_stage_grids(self.h, grids)
 
@@ -455,3 +532,30 @@ class Context:
 
     def sync(self):
         rapid_sync(self.h)
+
+
+class Trainer:
+    """Training samples of the learned block scorer (rapid_trainer) on the device."""
+
+    def __init__(self, capacity: int, neg_rate: float = 0.1):
+        self.h = rapid_trainer_create(capacity, neg_rate)
+
+    def count(self):
+        return rapid_trainer_count(self.h)
+
+    def fit(self, epochs=8, batch=2048, lr=3e-3, pos_weight=4.0, seed=0, init=None):
+        return rapid_trainer_fit(self.h, epochs, batch, lr, pos_weight, seed, init)
+
+    def close(self):
+        if getattr(self, "h", 0):
+            rapid_trainer_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -158,7 +158,8 @@ __device__ __forceinline__ int decide(const StageArgs &a, const ImageDesc &im, c
 // class and its label set is complete), its label or a neighbour label changed since, or
 // it requested a merge then.  Otherwise it decides as at the previous scan: no move.
 __device__ __forceinline__ bool block_needs_decision(const StageArgs &a, const WarpTile &W, int c, int j,
-                                                     bool block_skip, Local &lc) {
+                                                     bool block_skip, const unsigned char *mask, long long blk,
+                                                     Local &lc) {
   const int *win = W.win;
   const int lbl = win[c];
   const int nN = win[c - kWinW], nW = win[c - 1], nE = win[c + 1], nS = win[c + kWinW];
@@ -177,6 +178,8 @@ __device__ __forceinline__ bool block_needs_decision(const StageArgs &a, const W
     }
   }
   lc.elig++;
+  // pruned sweeps: the learned scorer decides which eligible blocks get the exact tests
+  if (mask && !mask[blk]) return false;
   const int nNW = win[c - kWinW - 1], nNE = win[c - kWinW + 1], nSE = win[c + kWinW + 1], nSW = win[c + kWinW - 1];
   const unsigned m = (unsigned)(nNW == lbl) | ((unsigned)(nN == lbl) << 1) | ((unsigned)(nNE == lbl) << 2) |
                      ((unsigned)(nE == lbl) << 3) | ((unsigned)(nSE == lbl) << 4) | ((unsigned)(nS == lbl) << 5) |
@@ -302,8 +305,9 @@ __device__ __forceinline__ void flush_counts(const StageArgs &a, int ii, int slo
 // whether each still refines in this stage.
 template <bool kBatch>
 __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *imgs, const int *tile0,
-                                           const unsigned char *active, WarpTile *wts, int *s_draw, int phase,
-                                           int g, int slot) {
+                                           const unsigned char *active, const unsigned char *pruned,
+                                           const int *valid_from, WarpTile *wts, int *s_draw, int phase, int g,
+                                           int slot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpTile &W = wts[warp];
   const int py = phase / 3, px = phase % 3;
@@ -339,7 +343,10 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
     const int bx0 = tx * kTileW, by0 = ty * kTileH;
     int *rec = a.trec + ((long long)t * 9 + phase) * kRecInts;
     const int rv = lane < kRecInts ? rec[lane] : 0;
-    const int stamp = __shfl_sync(0xffffffffu, rv, 0), nlab = __shfl_sync(0xffffffffu, rv, 1);
+    // a record from before the image's switch from pruned to full sweeps counts as none
+    const int stamp_rec = __shfl_sync(0xffffffffu, rv, 0), nlab = __shfl_sync(0xffffffffu, rv, 1);
+    const int stamp = stamp_rec >= valid_from[cur] ? stamp_rec : 0;
+    const unsigned char *mask = pruned[cur] ? im.mask : nullptr;
     const unsigned pm0 = (unsigned)__shfl_sync(0xffffffffu, rv, 4 + kTileLabels);
     const unsigned pm1 = (unsigned)__shfl_sync(0xffffffffu, rv, 5 + kTileLabels);
     const unsigned pm2 = (unsigned)__shfl_sync(0xffffffffu, rv, 6 + kTileLabels);
@@ -405,7 +412,8 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
       bool need = false;
       if (j < nx * ny) {
         const int lx = lx0 + 3 * (j % nx), ly = ly0 + 3 * (j / nx);
-        need = block_needs_decision(a, W, (ly + 1) * kWinW + (lx + 1), j, block_skip, lc);
+        need = block_needs_decision(a, W, (ly + 1) * kWinW + (lx + 1), j, block_skip, mask,
+                                    (long long)(by0 + ly) * im.nbx + (bx0 + lx), lc);
       }
       const unsigned ball = __ballot_sync(0xffffffffu, need);
       if (need) W.items[nitems + __popc(ball & ((1u << lane) - 1u))] = j;

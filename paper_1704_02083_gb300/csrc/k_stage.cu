@@ -490,7 +490,8 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
   __shared__ int2 s_acc[kAcceptSmem];
   __shared__ ImageDesc s_img[kImgs];
   __shared__ int s_tile0[kImgs], s_label0[kImgs];
-  __shared__ unsigned char s_active[kImgs];
+  __shared__ unsigned char s_active[kImgs], s_pruned[kImgs];
+  __shared__ int s_valid_from[kImgs];
   __shared__ int s_draw, s_any;
   unsigned epoch = 0;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
@@ -501,6 +502,8 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
       s_label0[i] = a.imgs[i].label0;
     }
     s_active[i] = 1;
+    s_pruned[i] = a.prune ? 1 : 0;
+    s_valid_from[i] = 0;
   }
   for (int k = blockIdx.x + gridDim.x * threadIdx.x; k < a.st.M; k += gstride) {
     set_means(a.st, k);
@@ -519,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
       for (int i = threadIdx.x; i < a.nimg; i += blockDim.x) a.ctl.changes[3 * i + (sweep + 1) % 3] = 0;
     for (int ph = 0; ph < 9; ph++) {
       g++;
-      eval_phase<kBatch>(a, s_img, s_tile0, s_active, wts, &s_draw, ph, g, slot);
+      eval_phase<kBatch>(a, s_img, s_tile0, s_active, s_pruned, s_valid_from, wts, &s_draw, ph, g, slot);
 
       tm.lap(PROF_EVAL);
       if (!grid_sync(a.ctl, epoch)) return;
@@ -553,16 +556,23 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
       }
     }
     // End of the sweep (every CTA decides the same from the same counts): an image whose
-    // sweep changed nothing has finished this stage, and its tiles are no longer visited.
+    // sweep changed nothing has finished this stage, and its tiles are no longer visited --
+    // unless that sweep was pruned: then it goes on with full sweeps, and tile records made
+    // before (phase numbers <= g) no longer count.
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
     for (int i = threadIdx.x; i < (kBatch ? a.nimg : 1); i += blockDim.x) {
       if (!s_active[i]) continue;
       if (blockIdx.x == 0) a.ctl.cnt[(long long)i * kCntStride + CNT_SWEEPS] += 1;
-      if (ld_volatile_u64(&a.ctl.changes[3 * i + slot]) == 0)
-        s_active[i] = 0;
-      else
+      if (ld_volatile_u64(&a.ctl.changes[3 * i + slot]) != 0) {
         s_any = 1;
+      } else if (s_pruned[i]) {
+        s_pruned[i] = 0;
+        s_valid_from[i] = g + 1;
+        s_any = 1;
+      } else {
+        s_active[i] = 0;
+      }
     }
     __syncthreads();
     if (!s_any) break;

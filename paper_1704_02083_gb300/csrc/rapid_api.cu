@@ -101,6 +101,30 @@ struct rapid_ctx {
   cudaGraph_t graph;
   cudaGraphExec_t gexec;
   long long graph_launches;
+  // learned scorer: pruning weights, per-image masks (at the label maps' offsets)
+  size_t lab_total;  // ints of one label-map buffer (all images)
+  int scorer_on;
+  float scorer_thr;
+  void *d_scorer, *d_scorer_tmp;
+  ScorerDev sdev;
+  unsigned char *d_mask;
+  size_t mask_cap;
+  // training-data logging
+  rapid_trainer *logger;
+  float *d_feat;
+  size_t feat_cap;
+  int *d_before;
+  size_t before_cap;
+};
+
+struct rapid_trainer {
+  TrainSet ts;
+  float neg_rate;
+  int runs;  // logged runs (seedings), part of the sampling hash
+  float *buf_x;
+  unsigned long long *buf_inb;
+  float *buf_y;
+  int *buf_count;
 };
 
 static rapid_status cuda_fail(rapid_ctx *c) {
@@ -115,6 +139,7 @@ static rapid_status cuda_fail(rapid_ctx *c) {
   } while (0)
 
 static bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+static constexpr size_t kScorerFeatures() { return RAPID_SCORER_FEATURES; }
 static int ceil_div(int a, int b) { return (a + b - 1) / b; }
 static size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
@@ -248,6 +273,15 @@ static void free_image_buffers(rapid_ctx *ctx) {
   ctx->desc_cap = 0;
   std::free(ctx->h_desc);
   ctx->h_desc = nullptr;
+  cudaFree(ctx->d_mask);
+  ctx->d_mask = nullptr;
+  ctx->mask_cap = 0;
+  cudaFree(ctx->d_feat);
+  ctx->d_feat = nullptr;
+  ctx->feat_cap = 0;
+  cudaFree(ctx->d_before);
+  ctx->d_before = nullptr;
+  ctx->before_cap = 0;
 }
 
 extern "C" void rapid_destroy(rapid_ctx *ctx) {
@@ -258,6 +292,8 @@ extern "C" void rapid_destroy(rapid_ctx *ctx) {
   cudaFree(ctx->d_label_block);
   cudaFree(ctx->d_pack);
   cudaFree(ctx->d_ctl_block);
+  cudaFree(ctx->d_scorer);
+  cudaFree(ctx->d_scorer_tmp);
   for (int i = 0; i < RAPID_MAX_STAGES; i++)
     if (ctx->ev_ok[i]) {
       cudaEventDestroy(ctx->ev[i][0]);
@@ -373,6 +409,7 @@ static rapid_status build_descriptors(rapid_ctx *ctx) {
       d.img_pitch = h.pitch;
       d.pyr = li >= 0 ? ctx->d_pyr[li] + h.pyr_off[li] : nullptr;
       d.lab = ctx->d_lab[s & 1] + h.lab_off;
+      d.mask = ctx->d_mask ? ctx->d_mask + h.lab_off : nullptr;
       d.lam_pos = h.lam_pos;
       d.lam_pos_f = (float)h.lam_pos;
       tile0 += (long long)d.ntx * d.nty;
@@ -449,6 +486,7 @@ extern "C" rapid_status rapid_set_images(rapid_ctx *ctx, int32_t n, const uint8_
   }
   if (M_total >= INT_MAX || lab_n >= (size_t)INT_MAX) return RAPID_ERANGE;
   ctx->nimg = n;
+  ctx->lab_total = lab_n;
   ctx->M_total = (int)M_total;
   ctx->lam_b2 = 2.0 * ctx->p.lambda_b;
   if (!grow(&ctx->d_img, &ctx->img_cap, img_bytes)) return RAPID_ENOMEM;
@@ -461,6 +499,11 @@ extern "C" rapid_status rapid_set_images(rapid_ctx *ctx, int32_t n, const uint8_
   if (!grow(&ctx->d_pack, &ctx->pack_cap, (size_t)max_M * sizeof(rapid_sp_stats))) return RAPID_ENOMEM;
   rs = ensure_label_arrays(ctx, ctx->M_total);
   if (rs != RAPID_OK) return rs;
+  if (ctx->scorer_on && !grow(&ctx->d_mask, &ctx->mask_cap, lab_n)) return RAPID_ENOMEM;
+  if (ctx->logger) {
+    if (!grow(&ctx->d_feat, &ctx->feat_cap, lab_n * kScorerFeatures() * sizeof(float))) return RAPID_ENOMEM;
+    if (!grow(&ctx->d_before, &ctx->before_cap, lab_n * sizeof(int))) return RAPID_ENOMEM;
+  }
   rs = build_descriptors(ctx);
   if (rs != RAPID_OK) return rs;
   for (int i = 0; i < n; i++) {
@@ -512,6 +555,7 @@ static StageArgs stage_args(rapid_ctx *ctx, int s) {
   a.max_sweeps = ctx->p.max_sweeps;
   a.verify_filter = ctx->p.verify_filter;
   a.skip_tiles = ctx->p.skip_tiles;
+  a.prune = ctx->scorer_on;
   return a;
 }
 
@@ -554,6 +598,7 @@ extern "C" rapid_status rapid_seed_grid(rapid_ctx *ctx, int32_t *M_out) {
   int nl = 0;
   StageArgs a = stage_args(ctx, 0);
   CK(launch_seed(a, host_desc(ctx, 0), gx, gy, ctx->nimg, ctx->stream, &nl));
+  if (ctx->logger) ctx->logger->runs++;
   ctx->launches += nl;
   if (M_out) *M_out = ctx->im[0].M;
   return RAPID_OK;
@@ -596,10 +641,33 @@ extern "C" rapid_status rapid_refine_stage(rapid_ctx *ctx, int32_t *sweeps_out, 
     }
     CK(cudaEventRecordWithFlags(ctx->ev[i][0], ctx->stream, evflags));
   }
+  const ImageDesc *ds = host_desc(ctx, i);
+  if (ctx->scorer_on)  // the learned scorer's masks for this stage (pruned sweeps)
+    for (int m = 0; m < ctx->nimg; m++) {
+      CK(launch_score(a, ds[m], ctx->L, ctx->sdev, ctx->scorer_thr, nullptr, ctx->d_mask + ctx->im[m].lab_off,
+                      ctx->stream));
+      ctx->launches++;
+    }
+  if (ctx->logger)  // training data: features and labels at the stage start
+    for (int m = 0; m < ctx->nimg; m++) {
+      const size_t off = ctx->im[m].lab_off;
+      CK(launch_features(a, ds[m], ctx->L, ctx->d_feat + off * kScorerFeatures(), ctx->stream));
+      CK(cudaMemcpyAsync(ctx->d_before + off, ds[m].lab, (size_t)ds[m].nbx * ds[m].nby * sizeof(int),
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+      ctx->launches++;
+    }
   const int grid = ctx->stage_grid[i] > 0 ? std::min(ctx->stage_grid[i], ctx->coop_grid) : ctx->coop_grid;
   CK(launch_stage(a, grid, ctx->coop_block, ctx->stream));
   ctx->launches++;
   if (ctx->profiling) CK(cudaEventRecordWithFlags(ctx->ev[i][1], ctx->stream, evflags));
+  if (ctx->logger)  // samples: boundary blocks at the start, moved or not by the end
+    for (int m = 0; m < ctx->nimg; m++) {
+      const size_t off = ctx->im[m].lab_off;
+      CK(launch_collect(ctx->d_feat + off * kScorerFeatures(), ctx->d_before + off, ds[m].lab, ds[m].nbx,
+                        ds[m].nby, ctx->logger->runs * kMaxBatch + m, i, ctx->logger->neg_rate, ctx->logger->ts,
+                        ctx->stream));
+      ctx->launches++;
+    }
   if (sweeps_out || moves_out || merges_out) {
     CK(cudaStreamSynchronize(ctx->stream));
     rapid_status rs = read_device_error(ctx);
@@ -761,6 +829,204 @@ extern "C" rapid_status rapid_autotune(rapid_ctx *ctx, int32_t *grids_out) {
     for (int s = 0; s < ctx->nstages; s++) grids_out[s] = best_g[s];
   ctx->profiling = saved_prof;
   ctx->graph_on = saved_graph;
+  return rs;
+}
+
+// ---------------------------------------------------------------- learned scorer
+extern "C" rapid_status rapid_set_scorer(rapid_ctx *ctx, const float *weights, float threshold) {
+  if (!ctx) return RAPID_EINVAL;
+  if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  drop_graph(ctx);
+  if (!weights) {
+    ctx->scorer_on = 0;
+    return RAPID_OK;
+  }
+  if (!(threshold >= 0.f && threshold <= 1.f)) return RAPID_EINVAL;
+  for (int i = 0; i < RAPID_SCORER_PARAMS; i++)
+    if (!std::isfinite(weights[i])) return RAPID_EINVAL;
+  if (!ctx->d_scorer && cudaMalloc(&ctx->d_scorer, scorer_dev_bytes()) != cudaSuccess) return RAPID_ENOMEM;
+  CK(scorer_upload(weights, ctx->d_scorer, &ctx->sdev, ctx->stream));
+  ctx->scorer_thr = threshold;
+  ctx->scorer_on = 1;
+  if (ctx->image_set) {
+    if (!grow(&ctx->d_mask, &ctx->mask_cap, ctx->lab_total)) return RAPID_ENOMEM;
+    return build_descriptors(ctx);
+  }
+  return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_scorer_features(rapid_ctx *ctx, int32_t i, float *dst_dev) {
+  if (!ctx || !dst_dev) return RAPID_EINVAL;
+  if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  if (ctx->cur < 0) return RAPID_ESTATE;
+  if (i < 0 || i >= ctx->nimg) return RAPID_EINVAL;
+  StageArgs a = stage_args(ctx, ctx->cur);
+  CK(launch_features(a, host_desc(ctx, ctx->cur)[i], ctx->L, dst_dev, ctx->stream));
+  ctx->launches++;
+  return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_scorer_scores(rapid_ctx *ctx, int32_t i, const float *weights, float *dst_dev) {
+  if (!ctx || !weights || !dst_dev) return RAPID_EINVAL;
+  if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  if (ctx->cur < 0) return RAPID_ESTATE;
+  if (i < 0 || i >= ctx->nimg) return RAPID_EINVAL;
+  if (!ctx->d_scorer_tmp && cudaMalloc(&ctx->d_scorer_tmp, scorer_dev_bytes()) != cudaSuccess) return RAPID_ENOMEM;
+  ScorerDev w;
+  CK(scorer_upload(weights, ctx->d_scorer_tmp, &w, ctx->stream));
+  StageArgs a = stage_args(ctx, ctx->cur);
+  CK(launch_score(a, host_desc(ctx, ctx->cur)[i], ctx->L, w, 0.f, dst_dev, nullptr, ctx->stream));
+  ctx->launches++;
+  return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_trainer_create(int64_t capacity, float neg_rate, rapid_trainer **out) {
+  if (!out) return RAPID_EINVAL;
+  *out = nullptr;
+  if (capacity < 1 || capacity > (1ll << 30) || !(neg_rate >= 0.f && neg_rate <= 1.f)) return RAPID_EINVAL;
+  rapid_trainer *t = new (std::nothrow) rapid_trainer;
+  if (!t) return RAPID_ENOMEM;
+  std::memset(t, 0, sizeof *t);
+  t->neg_rate = neg_rate;
+  bool ok = cudaMalloc(&t->buf_x, (size_t)capacity * kScorerPatchFloats * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&t->buf_inb, (size_t)capacity * sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMalloc(&t->buf_y, (size_t)capacity * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&t->buf_count, sizeof(int)) == cudaSuccess &&
+            cudaMemset(t->buf_count, 0, sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    rapid_trainer_destroy(t);
+    return RAPID_ENOMEM;
+  }
+  t->ts.x = t->buf_x;
+  t->ts.inb = t->buf_inb;
+  t->ts.y = t->buf_y;
+  t->ts.count = t->buf_count;
+  t->ts.cap = capacity;
+  *out = t;
+  return RAPID_OK;
+}
+
+extern "C" void rapid_trainer_destroy(rapid_trainer *t) {
+  if (!t) return;
+  cudaDeviceSynchronize();
+  cudaFree(t->buf_x);
+  cudaFree(t->buf_inb);
+  cudaFree(t->buf_y);
+  cudaFree(t->buf_count);
+  delete t;
+}
+
+extern "C" rapid_status rapid_set_logging(rapid_ctx *ctx, rapid_trainer *t) {
+  if (!ctx) return RAPID_EINVAL;
+  if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  drop_graph(ctx);
+  ctx->logger = t;
+  if (t && ctx->image_set) {
+    if (!grow(&ctx->d_feat, &ctx->feat_cap, ctx->lab_total * kScorerFeatures() * sizeof(float))) return RAPID_ENOMEM;
+    if (!grow(&ctx->d_before, &ctx->before_cap, ctx->lab_total * sizeof(int))) return RAPID_ENOMEM;
+  }
+  return RAPID_OK;
+}
+
+static long long trainer_samples(rapid_trainer *t) {
+  int c = 0;
+  if (cudaMemcpy(&c, t->buf_count, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  return std::min<long long>(c, t->ts.cap);
+}
+
+extern "C" rapid_status rapid_trainer_count(rapid_trainer *t, int64_t *samples, int64_t *positives) {
+  if (!t) return RAPID_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return RAPID_ECUDA;
+  const long long n = trainer_samples(t);
+  if (n < 0) return RAPID_ECUDA;
+  if (samples) *samples = n;
+  if (positives) {
+    float *y = (float *)std::malloc((size_t)std::max<long long>(n, 1) * sizeof(float));
+    if (!y) return RAPID_ENOMEM;
+    if (n > 0 && cudaMemcpy(y, t->buf_y, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      std::free(y);
+      return RAPID_ECUDA;
+    }
+    long long p = 0;
+    for (long long i = 0; i < n; i++) p += y[i] > 0.5f;
+    std::free(y);
+    *positives = p;
+  }
+  return RAPID_OK;
+}
+
+// xorshift64* generator for the shuffles and the initial weights
+static unsigned long long next_u64(unsigned long long &s) {
+  s ^= s >> 12;
+  s ^= s << 25;
+  s ^= s >> 27;
+  return s * 2685821657736338717ull;
+}
+
+extern "C" rapid_status rapid_trainer_fit(rapid_trainer *t, int32_t epochs, int32_t batch, float lr, float pos_weight,
+                                          uint64_t seed, const float *init, float *weights_out, float *epoch_loss) {
+  if (!t || !weights_out || epochs < 1 || batch < 1 || !(lr > 0.f) || !(pos_weight > 0.f)) return RAPID_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return RAPID_ECUDA;
+  const long long n = trainer_samples(t);
+  if (n < 1) return RAPID_ESTATE;
+  const int nP = RAPID_SCORER_PARAMS;
+  float w0[RAPID_SCORER_PARAMS];
+  unsigned long long rng = seed * 0x9E3779B97F4A7C15ull + 1;
+  if (init) {
+    std::memcpy(w0, init, sizeof w0);
+  } else {  // uniform Glorot start for the weights, zero biases
+    auto fill = [&](int off, int count, int fan_in, int fan_out) {
+      const float b = std::sqrt(6.f / (float)(fan_in + fan_out));
+      for (int i = 0; i < count; i++)
+        w0[off + i] = b * (2.f * (float)((next_u64(rng) >> 40) / 16777216.0) - 1.f);
+    };
+    std::memset(w0, 0, sizeof w0);
+    fill(0, 16 * 9 * 9, 9 * 9, 16 * 9);
+    fill(16 * 9 * 9 + 16, 16 * 16 * 9, 16 * 9, 16 * 9);
+    fill(16 * 9 * 9 + 16 + 16 * 16 * 9 + 16, 16 * 9, 16 * 9, 9);
+  }
+  float *d = nullptr;  // w, m, v, grad, loss
+  int *order = nullptr;
+  int *horder = (int *)std::malloc((size_t)n * sizeof(int));
+  rapid_status rs = RAPID_OK;
+  if (!horder || cudaMalloc(&d, (4 * (size_t)nP + 1) * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&order, (size_t)n * sizeof(int)) != cudaSuccess)
+    rs = RAPID_ENOMEM;
+  float *w = d, *m = d + nP, *v = d + 2 * nP, *grad = d + 3 * nP, *loss = d + 4 * nP;
+  if (rs == RAPID_OK && (cudaMemcpy(w, w0, nP * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+                         cudaMemset(m, 0, (3 * (size_t)nP + 1) * sizeof(float)) != cudaSuccess))
+    rs = RAPID_ECUDA;
+  for (long long i = 0; i < n && horder; i++) horder[i] = (int)i;
+  long long step = 0;
+  for (int e = 0; e < epochs && rs == RAPID_OK; e++) {
+    for (long long i = n - 1; i > 0; i--) {  // Fisher-Yates shuffle
+      const long long j = (long long)(next_u64(rng) % (unsigned long long)(i + 1));
+      std::swap(horder[i], horder[j]);
+    }
+    if (cudaMemcpy(order, horder, (size_t)n * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(loss, 0, sizeof(float)) != cudaSuccess) {
+      rs = RAPID_ECUDA;
+      break;
+    }
+    for (long long off = 0; off < n; off += batch) {
+      const int bs = (int)std::min<long long>(batch, n - off);
+      step++;
+      const float bc1 = 1.f - std::pow(0.9f, (float)step), bc2 = 1.f - std::pow(0.999f, (float)step);
+      if (launch_train_step(t->ts, (int)n, w, order, (int)off, bs, pos_weight, grad, loss, 0) != cudaSuccess ||
+          launch_adam(w, m, v, grad, lr, bc1, bc2, 1.f / (float)bs, 0) != cudaSuccess) {
+        rs = RAPID_ECUDA;
+        break;
+      }
+    }
+    float l = 0.f;
+    if (rs == RAPID_OK && cudaMemcpy(&l, loss, sizeof l, cudaMemcpyDeviceToHost) != cudaSuccess) rs = RAPID_ECUDA;
+    if (epoch_loss) epoch_loss[e] = l / (float)n;
+  }
+  if (rs == RAPID_OK && cudaMemcpy(weights_out, w, nP * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+    rs = RAPID_ECUDA;
+  cudaFree(d);
+  cudaFree(order);
+  std::free(horder);
   return rs;
 }
 

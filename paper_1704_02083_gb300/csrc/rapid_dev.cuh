@@ -122,6 +122,7 @@ struct ImageDesc {
   long long img_pitch;
   const int4 *pyr;    // sum level (f > 1), else unused
   int *lab;           // nby x nbx labels (global ids)
+  const unsigned char *mask;  // nby x nbx: 1 = the scorer keeps the block (pruned launches only)
   double lam_pos;
   float lam_pos_f;
   float pad2;
@@ -145,6 +146,7 @@ struct StageArgs {
   int skip_tiles;     // 1: skip tiles whose inputs did not change since their last scan
   int size_mode, lo_num, lo_den, hi_num, hi_den;
   int max_sweeps;
+  int prune;          // 1: sweep with the scorer's masks until a sweep changes nothing, then in full
 };
 
 // Box-sum levels kept for block sums: the method's level factors (> 1) plus 4, 16 and 64
@@ -393,6 +395,32 @@ __device__ __forceinline__ void atomic_add_i64(long long *p, long long v) {
 }
 
 #endif  // __CUDACC__
+
+// Learned block scorer (k_scorer.cu): device weights and the training-sample store.
+struct ScorerDev {
+  const void *w1, *w2;  // bf16 [tap][co][ci] (ci padded to 16)
+  const float *w3, *b1, *b2;
+  float b3;
+};
+struct TrainSet {
+  float *x;                 // [cap][7 * 7 * 9] feature patches
+  unsigned long long *inb;  // [cap] bit p: patch position p lies inside the image
+  float *y;                 // [cap] 1 = the block moved in its stage
+  int *count;               // samples appended (may exceed cap: the extra ones are dropped)
+  long long cap;
+};
+constexpr int kScorerPatchFloats = 7 * 7 * 9;
+cudaError_t scorer_upload(const float *weights, void *buf, ScorerDev *out, cudaStream_t s);
+size_t scorer_dev_bytes();
+cudaError_t launch_features(const StageArgs &a, const ImageDesc &im, int L, float *out, cudaStream_t s);
+cudaError_t launch_score(const StageArgs &a, const ImageDesc &im, int L, const ScorerDev &W, float threshold,
+                         float *score, unsigned char *mask, cudaStream_t s);
+cudaError_t launch_collect(const float *feat, const int *before, const int *after, int nbx, int nby, int img,
+                           int stage, float neg_rate, const TrainSet &ts, cudaStream_t s);
+cudaError_t launch_train_step(const TrainSet &ts, int n, const float *w, const int *order, int off, int batch,
+                              float pos_weight, float *grad, float *loss, cudaStream_t s);
+cudaError_t launch_adam(float *w, float *m, float *v, float *grad, float lr, float bc1, float bc2, float inv_batch,
+                        cudaStream_t s);
 
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_stage(const StageArgs &a, int grid, int block, cudaStream_t s);

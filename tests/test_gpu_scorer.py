@@ -1,0 +1,214 @@
+"""The learned block scorer: features and scores against plain NumPy restatements of their
+definitions, pruning that reduces to the plain method at threshold 0, training-data
+logging and training, and pruned batches equal to pruned single runs."""
+import numpy as np
+import pytest
+
+from gpu_common import STAT_FIELDS
+from helpers import count_components_per_label, stats_from_labels
+from paper_1704_02083_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+PARAMS = dict(num_levels=2, ratio_C=4, init_block=16, K=40, size_mode=2, predict=1)
+
+
+def _bf16(x):
+    """Round float32 to bfloat16 (nearest even) and back."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    r = (((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16).astype(np.uint32)
+    return r.view(np.float32)
+
+
+def _net(F, W):
+    """The scorer's net on a feature map F (H x W x 9): three 3x3 convolutions with zero
+    padding, ReLU, sigmoid; bf16 weights and activations."""
+    w1, b1 = _bf16(W[:1296]).reshape(16, 9, 3, 3), W[1296:1312]
+    w2, b2 = _bf16(W[1312:3616]).reshape(16, 16, 3, 3), W[3616:3632]
+    w3, b3 = _bf16(W[3632:3776]).reshape(1, 16, 3, 3), W[3776:3777]
+
+    def conv(x, w, b):
+        H, Wd, _ = x.shape
+        xp = np.pad(x.astype(np.float64), ((1, 1), (1, 1), (0, 0)))
+        out = np.zeros((H, Wd, w.shape[0]))
+        for ky in range(3):
+            for kx in range(3):
+                out += xp[ky:ky + H, kx:kx + Wd, :] @ w[:, :, ky, kx].T.astype(np.float64)
+        return out + b
+
+    h1 = _bf16(np.maximum(conv(_bf16(F), w1, b1), 0).astype(np.float32))
+    h2 = _bf16(np.maximum(conv(h1, w2, b2), 0).astype(np.float32))
+    z = conv(h2, w3, b3)[..., 0]
+    return 1.0 / (1.0 + np.exp(-z))
+
+
+def _features(rgb, blab, side, level, L, stats, imp_on):
+    """The 9 features of every block, from their definitions (float64)."""
+    H, W = rgb.shape[:2]
+    nby, nbx = blab.shape
+    mean = np.zeros((nby, nbx, 3))
+    for by in range(nby):
+        for bx in range(nbx):
+            mean[by, bx] = rgb[by * side:(by + 1) * side, bx * side:(bx + 1) * side].reshape(-1, 3).mean(0)
+    n = stats["n"].astype(np.float64)
+    lm = np.stack([stats["sum_r"], stats["sum_g"], stats["sum_b"]], 1) / np.maximum(n, 1)[:, None]
+    F = np.zeros((nby, nbx, 9))
+    for by in range(nby):
+        for bx in range(nbx):
+            a = blab[by, bx]
+            da = np.linalg.norm(mean[by, bx] - lm[a])
+            nb = [blab[by - 1, bx] if by > 0 else -1, blab[by, bx - 1] if bx > 0 else -1,
+                  blab[by, bx + 1] if bx + 1 < nbx else -1, blab[by + 1, bx] if by + 1 < nby else -1]
+            cnt = 0
+            for j, k in enumerate(nb):
+                if k < 0 or k == a:
+                    continue
+                cnt += 1
+                F[by, bx, j] = (da - np.linalg.norm(mean[by, bx] - lm[k])) / 64
+            F[by, bx, 4] = cnt / 4
+            F[by, bx, 5] = level / L
+            F[by, bx, 6] = stats["important"][a] if imp_on else 1.0
+            F[by, bx, 7] = np.log2(side) / 8
+            F[by, bx, 8] = da / 64
+    return F
+
+
+def _ctx_at_stage(rgb, stage, **params):
+    import torch
+
+    import paper_1704_02083_gb300 as pkg
+
+    ctx = pkg.Context(stream=torch.cuda.current_stream(), **params)
+    ctx.set_image(torch.from_numpy(np.ascontiguousarray(rgb)).cuda())
+    ctx.seed()
+    ctx.refine_stage()
+    for _ in range(stage):
+        ctx.split()
+        ctx.refine_stage()
+    return ctx
+
+
+def _random_weights(seed):
+    rng = np.random.default_rng(seed)
+    w = rng.normal(0, 0.35, 3777).astype(np.float32)
+    w[1296:1312] = 0.1
+    w[3616:3632] = 0.1
+    return w
+
+
+def test_features_and_scores_match_definitions():
+    import torch
+
+    import paper_1704_02083_gb300 as pkg
+
+    rgb = synth.he_image(96, 144, 6, 31).rgb
+    ctx = _ctx_at_stage(rgb, 3, **PARAMS)  # level 2 (after prediction), block side 2
+    st = ctx.state()
+    blab = ctx.block_labels()
+    stats = ctx.stats()
+    nby, nbx = blab.shape
+    feat = torch.zeros(nby * nbx * 9, dtype=torch.float32, device="cuda")
+    pkg.rapid_scorer_features(ctx.h, 0, feat.data_ptr())
+    torch.cuda.synchronize()
+    F = feat.cpu().numpy().reshape(nby, nbx, 9)
+    ref = _features(rgb, blab, st["block"], st["level"], PARAMS["num_levels"], stats, True)
+    np.testing.assert_allclose(F, ref, atol=2e-4)
+    for seed in range(3):
+        W = _random_weights(seed)
+        sc = torch.zeros(nby * nbx, dtype=torch.float32, device="cuda")
+        pkg.rapid_scorer_scores(ctx.h, 0, W, sc.data_ptr())
+        torch.cuda.synchronize()
+        got = sc.cpu().numpy().reshape(nby, nbx)
+        want = _net(F, W)
+        assert 0.01 < want.mean() < 0.99  # the weights exercise the net
+        np.testing.assert_allclose(got, want, atol=3e-3)
+    ctx.close()
+
+
+def _run(rgb, weights=None, thr=0.0, **params):
+    import torch
+
+    import paper_1704_02083_gb300 as pkg
+
+    with pkg.Context(stream=torch.cuda.current_stream(), **params) as ctx:
+        ctx.set_image(torch.from_numpy(np.ascontiguousarray(rgb)).cuda())
+        if weights is not None:
+            ctx.set_scorer(weights, thr)
+        ctx.run()
+        st = ctx.stats()
+        return ctx.labels(), np.stack([st[f] for f in STAT_FIELDS], 1), ctx.counters_array()
+
+
+def test_threshold_zero_keeps_every_block():
+    rgb = synth.he_image(128, 160, 8, 32).rgb
+    lab, st, cnt = _run(rgb, **PARAMS)
+    plab, pst, pcnt = _run(rgb, _random_weights(5), 0.0, **PARAMS)
+    np.testing.assert_array_equal(plab, lab)
+    np.testing.assert_array_equal(pst, st)
+    np.testing.assert_array_equal(pcnt[:, 5], cnt[:, 5])  # the same moves
+
+
+def _train(imgs, K, epochs=6):
+    import torch
+
+    import paper_1704_02083_gb300 as pkg
+
+    with pkg.Trainer(200_000, neg_rate=0.3) as tr:
+        with pkg.Context(stream=torch.cuda.current_stream(), **PARAMS) as ctx:
+            ctx.set_logging(tr)
+            ctx.set_images([torch.from_numpy(x).cuda() for x in imgs], K)
+            ctx.run()
+            ctx.sync()
+            ctx.set_logging(None)
+        n, pos = tr.count()
+        w, loss = tr.fit(epochs=epochs, batch=1024, lr=3e-3, pos_weight=4.0, seed=1)
+    return n, pos, w, loss
+
+
+def test_logging_training_and_pruned_refinement():
+    imgs = [synth.he_image(192, 192, 12, 40 + i).rgb for i in range(3)]
+    n, pos, w, loss = _train(imgs, [80, 80, 80])
+    assert n > 1000 and 0 < pos < n
+    assert np.isfinite(w).all() and np.isfinite(loss).all()
+    assert loss[-1] < loss[0]
+    rgb = synth.he_image(192, 192, 12, 50).rgb
+    plab, pst, pcnt = _run(rgb, **PARAMS)
+    lab, st, cnt = _run(rgb, w, 0.3, **PARAMS)
+    # every move is still exact: S equals recomputation, superpixels stay connected
+    M = st.shape[0]
+    np.testing.assert_array_equal(st[:, :6], stats_from_labels(rgb, lab, M)[:, :6])
+    alive = int((st[:, 0] > 0).sum())
+    assert count_components_per_label(lab) == alive
+    assert cnt[:, 4].sum() < pcnt[:, 4].sum()  # fewer blocks evaluated than the plain method
+    assert (lab != plab).mean() < 0.2
+
+
+def test_pruned_batch_equals_pruned_single_runs():
+    import torch
+
+    import paper_1704_02083_gb300 as pkg
+
+    imgs = [synth.he_image(96, 128, 6, 60 + i).rgb for i in range(3)]
+    K = [30, 20, 40]
+    W = _random_weights(9)
+    with pkg.Context(stream=torch.cuda.current_stream(), **PARAMS) as ctx:
+        ctx.set_scorer(W, 0.5)
+        ctx.set_images([torch.from_numpy(x).cuda() for x in imgs], K)
+        ctx.run()
+        got = [(ctx.image_labels(i), ctx.counters_array(i)) for i in range(3)]
+    for i, (x, k) in enumerate(zip(imgs, K)):
+        p = dict(PARAMS)
+        p["K"] = k
+        lab, _, cnt = _run(x, W, 0.5, **p)
+        np.testing.assert_array_equal(got[i][0], lab)
+        np.testing.assert_array_equal(got[i][1], cnt)
