@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="full grid for every stage")
     ap.add_argument("--no-graph", action="store_true", help="launch stage by stage instead of a CUDA graph")
+    ap.add_argument("--prune", type=float, default=None,
+                    help="the learned path: train the block scorer (untimed) and prune at this threshold")
     return ap.parse_args()
 
 
@@ -255,6 +257,11 @@ def run_rapid(args, rank, world, local):
 
     imgs, Ks, params = load_workload(args.workload)
     n = len(imgs)
+    scorer = None
+    if args.prune is not None:  # the learned path: move logs of plain runs on other seeds, then training
+        from paper_1704_02083_gb300 import scorer as sc
+        w_scorer, train_info = sc.collect_and_train(*sc.training_tiles())
+        scorer = dict(threshold=args.prune, train=train_info)
     sizes = [(int(x.shape[0]), int(x.shape[1])) for x in imgs]
     npx = sum(h * w for h, w in sizes)
     stream = torch.cuda.Stream()  # a graph needs a non-default stream
@@ -263,6 +270,8 @@ def run_rapid(args, rank, world, local):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     ctx = pkg.Context(stream=stream, **params)
     ctx.set_images(dev_imgs, Ks)
+    if scorer is not None:
+        ctx.set_scorer(w_scorer, args.prune)
     grids = ctx.autotune() if not args.no_autotune else None
     ctx.set_profiling(True)
     ctx.set_graph(not args.no_graph)
@@ -316,6 +325,8 @@ def run_rapid(args, rank, world, local):
         e2e_ctx = pkg.Context(stream=stream, **params)
         if grids is not None:
             e2e_ctx.set_stage_grids(grids)
+        if scorer is not None:
+            e2e_ctx.set_scorer(w_scorer, args.prune)
         ptrs = [p.data_ptr() for p in pins]
         times = []
         for it in range(args.warmup + args.steps):
@@ -333,6 +344,26 @@ def run_rapid(args, rank, world, local):
         e2e = {"value": whole_job_rate(npx, len(times), sum(times), dist) / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": 3 * npx,
                "d2h_bytes_per_step": 4 * npx + sum(Ms) * pkg.SP_STATS_DTYPE.itemsize}
+
+    if scorer is not None:  # judged by the plain method: its labels, and the ground truth
+        from paper_1704_02083_gb300 import quality, synth
+        gts = [synth.workload_image(args.workload).regions] if n == 1 else None
+        plain = pkg.Context(stream=stream, **params)
+        plain.set_images(dev_imgs, Ks)
+        plain.run()
+        q = dict(disagreement=0.0, br_plain=0.0, br_pruned=0.0, ue_plain=0.0, ue_pruned=0.0)
+        for i in range(n):
+            a, b = plain.image_labels(i), ctx.image_labels(i)
+            wgt = a.size / npx
+            q["disagreement"] += wgt * quality.disagreement(a, b)
+            if gts is not None:
+                q["br_plain"] += wgt * quality.boundary_recall(a, gts[i])
+                q["br_pruned"] += wgt * quality.boundary_recall(b, gts[i])
+                q["ue_plain"] += wgt * quality.undersegmentation_error(a, gts[i])
+                q["ue_pruned"] += wgt * quality.undersegmentation_error(b, gts[i])
+        plain.close()
+        scorer["quality"] = {k: round(v, 5) for k, v in q.items()}
+        scorer["evaluated_blocks"] = int(sum(ctx.counters_array(i)[:, 4].sum() for i in range(n)))
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -359,6 +390,7 @@ def run_rapid(args, rank, world, local):
                "final_grain": params["final_grain"], "size_mode": params["size_mode"],
                "predict": params["predict"], "reuse": params["reuse"],
                "stage_grids": grids[:nst] if grids is not None else None, "cuda_graph": not args.no_graph,
+               "path": "plain" if scorer is None else "learned pruning", "scorer": scorer,
                "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
                "parallelism": f"replicas x{world}"}
         if n == 1:

@@ -72,25 +72,5 @@ def total_energy(rgb: np.ndarray, lab: np.ndarray, lam_pos: float, lam_b: float)
     return E_col + Fraction(lam_pos) * E_pos + 2 * Fraction(lam_b) * unequal_pairs(lab)
 
 
-def boundary_map(lab: np.ndarray) -> np.ndarray:
-    b = np.zeros(lab.shape, bool)
-    b[:, :-1] |= lab[:, :-1] != lab[:, 1:]
-    b[:-1, :] |= lab[:-1, :] != lab[1:, :]
-    return b
-
-
-def boundary_recall(lab: np.ndarray, gt: np.ndarray, tol: int = 2) -> float:
-    gb = boundary_map(gt)
-    if not gb.any():
-        return 1.0
-    d = ndi.distance_transform_edt(~boundary_map(lab))
-    return float((d[gb] <= tol).mean())
-
-
-def undersegmentation_error(lab: np.ndarray, gt: np.ndarray) -> float:
-    g = int(gt.max()) + 1
-    pairs = lab.astype(np.int64).ravel() * g + gt.ravel()
-    u, c = np.unique(pairs, return_counts=True)
-    sp = u // g
-    spsz = np.bincount(lab.ravel().astype(np.int64))
-    return float(np.minimum(c, spsz[sp] - c).sum() / lab.size)
+# the quality measures live with the package's evaluation code
+from paper_1704_02083_gb300.quality import boundary_map, boundary_recall, undersegmentation_error  # noqa: E402,F401
