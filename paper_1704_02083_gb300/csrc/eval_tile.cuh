@@ -18,9 +18,9 @@ struct WarpTile {
   int win[kWinW * kWinH];
   int hkey[32];             // labels of the window: open-addressing table (-1 = empty)
   int hval[32];             // 1 when hkey[i] changed since the tile's previous scan
-  unsigned prevreq[3];      // blocks that requested a merge at the previous scan
-  unsigned req[3];          // blocks that request one now
-  int items[96];            // phase-class blocks (index j) that need a decision
+  unsigned prevreq[kReqWords];  // blocks that requested a merge at the previous scan
+  unsigned req[kReqWords];      // blocks that request one now
+  int items[kPhaseMax];         // phase-class blocks (index j) that need a decision
   int hcount, over;         // labels in the table; more than kTileLabels (or table full)
 };
 
@@ -347,10 +347,10 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
     const int stamp_rec = __shfl_sync(0xffffffffu, rv, 0), nlab = __shfl_sync(0xffffffffu, rv, 1);
     const int stamp = stamp_rec >= valid_from[cur] ? stamp_rec : 0;
     const unsigned char *mask = pruned[cur] ? im.mask : nullptr;
-    const unsigned pm0 = (unsigned)__shfl_sync(0xffffffffu, rv, 4 + kTileLabels);
-    const unsigned pm1 = (unsigned)__shfl_sync(0xffffffffu, rv, 5 + kTileLabels);
-    const unsigned pm2 = (unsigned)__shfl_sync(0xffffffffu, rv, 6 + kTileLabels);
-    const bool can = a.skip_tiles && stamp > 0 && nlab >= 0 && (pm0 | pm1 | pm2) == 0u;
+    // lanes 4 + kTileLabels .. hold the merge-request words of the previous scan
+    const bool req_lane = lane >= 4 + kTileLabels && lane < kRecInts;
+    const bool anyreq = __any_sync(0xffffffffu, req_lane && rv != 0);
+    const bool can = a.skip_tiles && stamp > 0 && nlab >= 0 && !anyreq;
     const int myl = __shfl_sync(0xffffffffu, rv, (4 + lane) & 31);
     const bool changed = __any_sync(0xffffffffu, can && lane < nlab && a.st.chg[myl] >= 2 * stamp);
     if (can && !changed) {
@@ -367,10 +367,10 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
     if (lane == 0) {
       W.over = 0;
       W.hcount = 0;
-      W.req[0] = W.req[1] = W.req[2] = 0u;
-      W.prevreq[0] = stamp > 0 ? pm0 : 0u;
-      W.prevreq[1] = stamp > 0 ? pm1 : 0u;
-      W.prevreq[2] = stamp > 0 ? pm2 : 0u;
+    }
+    if (req_lane) {
+      W.req[lane - 4 - kTileLabels] = 0u;
+      W.prevreq[lane - 4 - kTileLabels] = stamp > 0 ? (unsigned)rv : 0u;
     }
     __syncwarp();
     // window: lane = column (lanes 0 and 1 also take columns 32 and 33); the label of each
@@ -437,10 +437,8 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
       rec[2] = (int)de;
       rec[3] = (int)dv;
       rec[1] = W.over ? -1 : __popc(present);
-      rec[4 + kTileLabels] = (int)W.req[0];
-      rec[5 + kTileLabels] = (int)W.req[1];
-      rec[6 + kTileLabels] = (int)W.req[2];
     }
+    if (req_lane) rec[lane] = (int)W.req[lane - 4 - kTileLabels];
     __syncwarp();
   }
   flush_counts(a, cur, slot, lc, scanned, skipped);

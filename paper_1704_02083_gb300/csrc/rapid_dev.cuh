@@ -37,9 +37,13 @@ enum { DERR_TIMEOUT = 1 };
 // Evaluation tiles: TW x TH blocks, one warp each; a phase class has at most 11 x 6 blocks
 // of a tile.
 constexpr int kTileW = 32, kTileH = 16, kTileLabels = 16;
+// blocks of one phase class in a tile, and 32-bit words of one bit each
+constexpr int kPhaseMax = ((kTileW + 2) / 3) * ((kTileH + 2) / 3);
+constexpr int kReqWords = (kPhaseMax + 31) / 32;
 // tile record: stamp of the last scan, label count (-1: too many), eligible and evaluated
 // counts, the labels, and a bit per phase-class block that issued a merge request
-constexpr int kRecInts = 4 + kTileLabels + 3;
+constexpr int kRecInts = 4 + kTileLabels + kReqWords;
+static_assert(kRecInts <= 32, "a warp reads a tile record with one lane per int");
 constexpr int kCacheLabels = 16;           // neighbour labels remembered by a failed merge
 
 struct DevStats {
