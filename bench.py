@@ -272,7 +272,7 @@ def run_rapid(args, rank, world, local):
     ctx.set_images(dev_imgs, Ks)
     if scorer is not None:
         ctx.set_scorer(w_scorer, args.prune)
-    grids = ctx.autotune() if not args.no_autotune else None
+    grids, shapes = ctx.autotune() if not args.no_autotune else (None, None)
     ctx.set_profiling(True)
     ctx.set_graph(not args.no_graph)
     for _ in range(args.warmup):
@@ -325,6 +325,7 @@ def run_rapid(args, rank, world, local):
         e2e_ctx = pkg.Context(stream=stream, **params)
         if grids is not None:
             e2e_ctx.set_stage_grids(grids)
+            e2e_ctx.set_stage_shapes(shapes)
         if scorer is not None:
             e2e_ctx.set_scorer(w_scorer, args.prune)
         ptrs = [p.data_ptr() for p in pins]
@@ -389,7 +390,9 @@ def run_rapid(args, rank, world, local):
                "levels": params["num_levels"], "ratio_C": params["ratio_C"], "init_block": params["init_block"],
                "final_grain": params["final_grain"], "size_mode": params["size_mode"],
                "predict": params["predict"], "reuse": params["reuse"],
-               "stage_grids": grids[:nst] if grids is not None else None, "cuda_graph": not args.no_graph,
+               "stage_grids": grids[:nst] if grids is not None else None,
+               "stage_tiles": [f"{[32, 32, 64][k]}x{[16, 8, 16][k]}" for k in shapes[:nst]] if shapes else None,
+               "cuda_graph": not args.no_graph,
                "path": "plain" if scorer is None else "learned pruning", "scorer": scorer,
                "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
                "parallelism": f"replicas x{world}"}

@@ -205,15 +205,20 @@ rapid_status rapid_read_image_stats(rapid_ctx *ctx, int32_t i, rapid_sp_stats *d
 rapid_status rapid_read_image_counters(rapid_ctx *ctx, int32_t i, rapid_counters *dst);
 
 /* Launch geometry.  Results never depend on it (a phase's decisions are independent and
- * merges are ordered by block index), only the time does.  rapid_set_stage_grids: CTAs of
- * each stage's launch for stages 0 .. n-1 (0 = the full co-resident grid, larger values are
- * capped to it; the others reset to 0).  rapid_autotune: time the whole schedule on the
- * context's current images once per candidate grid (the full grid, then halvings down to
- * one CTA), keep per stage the fastest, and write them to grids_out (RAPID_MAX_STAGES
- * entries, may be NULL).  Synchronises; the context's results afterwards are those of a
- * normal run.  EINVAL on a negative grid, ESTATE without images. */
+ * merges are ordered by block index), only the time does.
+ * rapid_set_stage_grids: CTAs of each stage's launch for stages 0 .. n-1 (0 = the full
+ *   co-resident grid, larger values are capped to it; the others reset to 0).
+ * rapid_set_stage_shapes: evaluation-tile shape of each stage, an index into
+ *   {32 x 16, 32 x 8, 64 x 16} blocks (default 0; the others reset to 0).
+ * rapid_autotune: time the whole schedule on the context's current images once per tile
+ *   shape (full grid), then once per grid size (the full grid halved down to one CTA) with
+ *   the chosen shapes; keep per stage the fastest and write them to grids_out and
+ *   shapes_out (RAPID_MAX_STAGES entries each, either may be NULL).  Synchronises; the
+ *   context's results afterwards are those of a normal run.
+ * EINVAL on a negative grid or an unknown shape, ESTATE without images. */
 rapid_status rapid_set_stage_grids(rapid_ctx *ctx, const int32_t *grids, int32_t n);
-rapid_status rapid_autotune(rapid_ctx *ctx, int32_t *grids_out);
+rapid_status rapid_set_stage_shapes(rapid_ctx *ctx, const int32_t *shapes, int32_t n);
+rapid_status rapid_autotune(rapid_ctx *ctx, int32_t *grids_out, int32_t *shapes_out);
 
 /* ---- Learned block scorer (pruning of the boundary-block queue) ----
  * A 3-layer 3x3 convolutional net over 9 per-block features (colour gain of moving to each

@@ -112,7 +112,8 @@ def lib() -> C.CDLL:
         "rapid_trainer_count": (i32, [P, pi64, pi64]),
         "rapid_trainer_fit": (i32, [P, i32, i32, C.c_float, C.c_float, C.c_uint64, P, P, P]),
         "rapid_trainer_destroy": (None, [P]),
-        "rapid_autotune": (i32, [P, pi32]),
+        "rapid_autotune": (i32, [P, pi32, pi32]),
+        "rapid_set_stage_shapes": (i32, [P, pi32, i32]),
         "rapid_status_string": (C.c_char_p, [i32]),
         "rapid_destroy": (None, [P]),
     }
@@ -253,11 +254,18 @@ def rapid_set_stage_grids(ctx: int, grids):
     _check(lib().rapid_set_stage_grids(ctx, arr, n), "rapid_set_stage_grids")
 
 
+def rapid_set_stage_shapes(ctx: int, shapes):
+    n = len(shapes)
+    arr = (C.c_int32 * max(1, n))(*shapes)
+    _check(lib().rapid_set_stage_shapes(ctx, arr, n), "rapid_set_stage_shapes")
+
+
 def rapid_autotune(ctx: int):
-    """Per-stage grid sizes chosen by timing (RAPID_MAX_STAGES entries)."""
-    out = (C.c_int32 * RAPID_MAX_STAGES)()
-    _check(lib().rapid_autotune(ctx, out), "rapid_autotune")
-    return list(out)
+    """Per-stage grid sizes and tile shapes chosen by timing (RAPID_MAX_STAGES entries each)."""
+    grids = (C.c_int32 * RAPID_MAX_STAGES)()
+    shapes = (C.c_int32 * RAPID_MAX_STAGES)()
+    _check(lib().rapid_autotune(ctx, grids, shapes), "rapid_autotune")
+    return list(grids), list(shapes)
 
 
 RAPID_SCORER_PARAMS = 3777
@@ -526,9 +534,15 @@ class Context:
     def set_stage_grids(self, grids):
         rapid_set_stage_grids(self.h, grids)
 
+    def set_stage_shapes(self, shapes):
+        rapid_set_stage_shapes(self.h, shapes)
+
     def autotune(self):
-        """Time the schedule at several grid sizes and keep the fastest per stage."""
-        return rapid_autotune(self.h)[:max(1, self.counters().num_stages)]
+        """Time the schedule with each tile shape and grid size and keep the fastest per
+        stage; returns (grids, shapes) per stage."""
+        g, s = rapid_autotune(self.h)
+        n = max(1, self.counters().num_stages)
+        return g[:n], s[:n]
 
     def sync(self):
         rapid_sync(self.h)

@@ -1,0 +1,5 @@
+// k_stage_s2.cu — the stage kernel for 64 x 16-block evaluation tiles.
+#define RAPID_TILE_W 64
+#define RAPID_TILE_H 16
+#define RAPID_SHAPE_NS s2
+#include "stage_impl.cuh"

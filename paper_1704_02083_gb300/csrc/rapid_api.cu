@@ -77,7 +77,8 @@ struct rapid_ctx {
   ImageDesc *d_desc;
   size_t desc_cap;
   int ntiles[RAPID_MAX_STAGES];
-  int stage_grid[RAPID_MAX_STAGES];  // CTAs of each stage's launch (0 = the full co-resident grid)
+  int stage_grid[RAPID_MAX_STAGES];   // CTAs of each stage's launch (0 = the full co-resident grid)
+  int stage_shape[RAPID_MAX_STAGES];  // evaluation-tile shape of each stage (index into kShapes)
   // labels
   int M_total, M_cap;
   void *d_label_block;
@@ -204,12 +205,14 @@ extern "C" rapid_status rapid_create(const rapid_params *p, void *cuda_stream, r
   int coop = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
   ctx->coop_block = stage_block_threads();
-  int per_sm = 0, per_sm_batch = 0;
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_ptr(false), ctx->coop_block, 0);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_batch, stage_kernel_ptr(true), ctx->coop_block, 0);
-  per_sm = std::min(per_sm, per_sm_batch);
+  // one grid size that every compiled stage kernel can keep co-resident
+  int per_sm = INT_MAX;
+  for (int sh = 0; sh < kNumShapes && e == cudaSuccess; sh++)
+    for (int b = 0; b < 2 && e == cudaSuccess; b++) {
+      int k = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, stage_kernel_ptr(b == 1, sh), ctx->coop_block, 0);
+      per_sm = std::min(per_sm, k);
+    }
   if (e != cudaSuccess || !coop || per_sm < 1) {
     delete ctx;
     return RAPID_ECUDA;
@@ -395,8 +398,9 @@ static rapid_status build_descriptors(rapid_ctx *ctx) {
       d.W = h.W;
       d.nbx = ceil_div(h.W, side);
       d.nby = ceil_div(h.H, side);
-      d.ntx = (d.nbx + kTileW - 1) / kTileW;
-      d.nty = (d.nby + kTileH - 1) / kTileH;
+      const TileShape ts = kShapes[ctx->stage_shape[s]];
+      d.ntx = (d.nbx + ts.w - 1) / ts.w;
+      d.nty = (d.nby + ts.h - 1) / ts.h;
       d.Wl = ceil_div(h.W, f);
       d.Hl = ceil_div(h.H, f);
       d.tile0 = (int)tile0;
@@ -466,7 +470,11 @@ extern "C" rapid_status rapid_set_images(rapid_ctx *ctx, int32_t n, const uint8_
     const int lnbx = ceil_div(h.W, sl), lnby = ceil_div(h.H, sl);
     h.lab_off = lab_n;
     lab_n = round_up(lab_n + (size_t)lnbx * lnby, 64);
-    tiles_last += (long long)((lnbx + kTileW - 1) / kTileW) * ((lnby + kTileH - 1) / kTileH);
+    long long most = 0;  // tile records: the shape with the most tiles at the finest stage
+    for (int sh = 0; sh < kNumShapes; sh++)
+      most = std::max<long long>(most, (long long)((lnbx + kShapes[sh].w - 1) / kShapes[sh].w) *
+                                           ((lnby + kShapes[sh].h - 1) / kShapes[sh].h));
+    tiles_last += most;
     // seed grid gx x gy (same rounding as the stated formula) on the first stage's blocks
     const int nbx0 = ceil_div(h.W, s0), nby0 = ceil_div(h.H, s0);
     int gx = (int)std::floor(std::sqrt((double)h.K * (double)h.W / (double)h.H) + 0.5);
@@ -657,7 +665,7 @@ extern "C" rapid_status rapid_refine_stage(rapid_ctx *ctx, int32_t *sweeps_out, 
       ctx->launches++;
     }
   const int grid = ctx->stage_grid[i] > 0 ? std::min(ctx->stage_grid[i], ctx->coop_grid) : ctx->coop_grid;
-  CK(launch_stage(a, grid, ctx->coop_block, ctx->stream));
+  CK(launch_stage(a, grid, ctx->coop_block, ctx->stream, ctx->stage_shape[i]));
   ctx->launches++;
   if (ctx->profiling) CK(cudaEventRecordWithFlags(ctx->ev[i][1], ctx->stream, evflags));
   if (ctx->logger)  // samples: boundary blocks at the start, moved or not by the end
@@ -772,6 +780,15 @@ extern "C" rapid_status rapid_set_graph(rapid_ctx *ctx, int32_t on) {
   return RAPID_OK;
 }
 
+extern "C" rapid_status rapid_set_stage_shapes(rapid_ctx *ctx, const int32_t *shapes, int32_t n) {
+  if (!ctx || n < 0 || n > RAPID_MAX_STAGES || (n > 0 && !shapes)) return RAPID_EINVAL;
+  for (int i = 0; i < n; i++)
+    if (shapes[i] < 0 || shapes[i] >= kNumShapes) return RAPID_EINVAL;
+  for (int i = 0; i < RAPID_MAX_STAGES; i++) ctx->stage_shape[i] = i < n ? shapes[i] : 0;
+  drop_graph(ctx);
+  return ctx->image_set ? build_descriptors(ctx) : RAPID_OK;
+}
+
 extern "C" rapid_status rapid_set_stage_grids(rapid_ctx *ctx, const int32_t *grids, int32_t n) {
   if (!ctx || n < 0 || n > RAPID_MAX_STAGES || (n > 0 && !grids)) return RAPID_EINVAL;
   for (int i = 0; i < n; i++)
@@ -781,13 +798,26 @@ extern "C" rapid_status rapid_set_stage_grids(rapid_ctx *ctx, const int32_t *gri
   return RAPID_OK;
 }
 
-// Grid-size tuner.  A stage's result does not depend on how many CTAs share its work (the
-// decisions of a phase are independent, merges are ordered by block index), only its time
-// does: coarse stages with few tiles lose more to the grid barrier than they gain from
-// more SMs.  Run the whole schedule once per candidate grid (the full co-resident grid,
-// then halvings down to one CTA), time every stage with events, and keep per stage the
-// fastest candidate (ties to the larger grid).
-extern "C" rapid_status rapid_autotune(rapid_ctx *ctx, int32_t *grids_out) {
+// Launch-geometry tuner.  A stage's result does not depend on its evaluation-tile shape or
+// on how many CTAs share its work (the decisions of a phase are independent, merges are
+// ordered by block index), only its time does: coarse stages with few tiles lose more to
+// the grid barrier than they gain from more SMs, and the best tile shape depends on the
+// stage.  First the whole schedule runs once per tile shape on the full grid, then once per
+// grid size (the full co-resident grid, then halvings down to one CTA) with the chosen
+// shapes; every stage is timed with events and keeps its fastest setting (ties to the
+// earlier candidate).  Each candidate runs twice, the first run warming up.
+static rapid_status time_stages(rapid_ctx *ctx, float *ms) {
+  for (int rep = 0; rep < 2; rep++) {
+    rapid_status rs = run_sequence(ctx);
+    if (rs == RAPID_OK) rs = rapid_sync(ctx);
+    if (rs != RAPID_OK) return rs;
+  }
+  for (int s = 0; s < ctx->nstages; s++)
+    if (cudaEventElapsedTime(&ms[s], ctx->ev[s][0], ctx->ev[s][1]) != cudaSuccess) return cuda_fail(ctx);
+  return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_autotune(rapid_ctx *ctx, int32_t *grids_out, int32_t *shapes_out) {
   if (!ctx) return RAPID_EINVAL;
   if (ctx->sticky != RAPID_OK) return ctx->sticky;
   if (!ctx->image_set) return RAPID_ESTATE;
@@ -795,38 +825,41 @@ extern "C" rapid_status rapid_autotune(rapid_ctx *ctx, int32_t *grids_out) {
   ctx->profiling = 1;
   ctx->graph_on = 0;
   drop_graph(ctx);
-  int cand[16], nc = 0;
-  for (int g = ctx->coop_grid; g >= 1 && nc < 16; g /= 2) cand[nc++] = g;
-  float best_ms[RAPID_MAX_STAGES];
-  int best_g[RAPID_MAX_STAGES];
+  float best[RAPID_MAX_STAGES], ms[RAPID_MAX_STAGES];
+  int best_shape[RAPID_MAX_STAGES], best_grid[RAPID_MAX_STAGES];
   for (int s = 0; s < RAPID_MAX_STAGES; s++) {
-    best_ms[s] = 3.4e38f;
-    best_g[s] = ctx->coop_grid;
+    best[s] = 3.4e38f;
+    best_shape[s] = 0;
+    best_grid[s] = ctx->coop_grid;
+    ctx->stage_grid[s] = 0;
   }
   rapid_status rs = RAPID_OK;
-  for (int c = 0; c < nc && rs == RAPID_OK; c++) {
-    for (int s = 0; s < RAPID_MAX_STAGES; s++) ctx->stage_grid[s] = cand[c];
-    for (int rep = 0; rep < 2 && rs == RAPID_OK; rep++) {  // the first pass warms up
-      rs = run_sequence(ctx);
-      if (rs != RAPID_OK) break;
-      rs = rapid_sync(ctx);
-      if (rs != RAPID_OK || rep == 0) continue;
-      for (int s = 0; s < ctx->nstages; s++) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ctx->ev[s][0], ctx->ev[s][1]) != cudaSuccess) {
-          rs = cuda_fail(ctx);
-          break;
-        }
-        if (ms < best_ms[s]) {
-          best_ms[s] = ms;
-          best_g[s] = cand[c];
-        }
+  for (int sh = 0; sh < kNumShapes && rs == RAPID_OK; sh++) {
+    for (int s = 0; s < RAPID_MAX_STAGES; s++) ctx->stage_shape[s] = sh;
+    rs = build_descriptors(ctx);
+    if (rs == RAPID_OK) rs = time_stages(ctx, ms);
+    for (int s = 0; s < ctx->nstages && rs == RAPID_OK; s++)
+      if (ms[s] < best[s]) {
+        best[s] = ms[s];
+        best_shape[s] = sh;
       }
-    }
   }
-  for (int s = 0; s < RAPID_MAX_STAGES; s++) ctx->stage_grid[s] = s < ctx->nstages ? best_g[s] : 0;
-  if (grids_out)
-    for (int s = 0; s < ctx->nstages; s++) grids_out[s] = best_g[s];
+  for (int s = 0; s < RAPID_MAX_STAGES; s++) ctx->stage_shape[s] = best_shape[s];
+  if (rs == RAPID_OK) rs = build_descriptors(ctx);
+  for (int g = ctx->coop_grid / 2; g >= 1 && rs == RAPID_OK; g /= 2) {
+    for (int s = 0; s < RAPID_MAX_STAGES; s++) ctx->stage_grid[s] = g;
+    rs = time_stages(ctx, ms);
+    for (int s = 0; s < ctx->nstages && rs == RAPID_OK; s++)
+      if (ms[s] < best[s]) {
+        best[s] = ms[s];
+        best_grid[s] = g;
+      }
+  }
+  for (int s = 0; s < RAPID_MAX_STAGES; s++) ctx->stage_grid[s] = s < ctx->nstages ? best_grid[s] : 0;
+  for (int s = 0; s < ctx->nstages; s++) {
+    if (grids_out) grids_out[s] = best_grid[s];
+    if (shapes_out) shapes_out[s] = best_shape[s];
+  }
   ctx->profiling = saved_prof;
   ctx->graph_on = saved_graph;
   return rs;

@@ -34,15 +34,18 @@ enum { PROF_EVAL = 0, PROF_SYNC1, PROF_COMMIT, PROF_SYNC2, PROF_MERGE, PROF_N };
 // Device error word values (0 = fine).
 enum { DERR_TIMEOUT = 1 };
 
-// Evaluation tiles: TW x TH blocks, one warp each; a phase class has at most 11 x 6 blocks
-// of a tile.
-constexpr int kTileW = 32, kTileH = 16, kTileLabels = 16;
-// blocks of one phase class in a tile, and 32-bit words of one bit each
-constexpr int kPhaseMax = ((kTileW + 2) / 3) * ((kTileH + 2) / 3);
-constexpr int kReqWords = (kPhaseMax + 31) / 32;
+// Evaluation tiles: one warp takes a tile of w x h blocks.  The stage kernel is compiled
+// for each shape below (a launch uses one; the result never depends on it).
+struct TileShape {
+  int w, h;
+};
+constexpr int kNumShapes = 3;
+constexpr TileShape kShapes[kNumShapes] = {{32, 16}, {32, 8}, {64, 16}};
+constexpr int kTileLabels = 16;
 // tile record: stamp of the last scan, label count (-1: too many), eligible and evaluated
-// counts, the labels, and a bit per phase-class block that issued a merge request
-constexpr int kRecInts = 4 + kTileLabels + kReqWords;
+// counts, the labels, and a bit per phase-class block that issued a merge request (up to
+// 22 x 6 blocks for the widest shape: 5 words)
+constexpr int kRecInts = 4 + kTileLabels + 5;
 static_assert(kRecInts <= 32, "a warp reads a tile record with one lane per int");
 constexpr int kCacheLabels = 16;           // neighbour labels remembered by a failed merge
 
@@ -427,9 +430,9 @@ cudaError_t launch_adam(float *w, float *m, float *v, float *grad, float lr, flo
                         cudaStream_t s);
 
 // Host-side launchers (defined in the .cu files).
-cudaError_t launch_stage(const StageArgs &a, int grid, int block, cudaStream_t s);
+cudaError_t launch_stage(const StageArgs &a, int grid, int block, cudaStream_t s, int shape);
 int stage_block_threads();
-const void *stage_kernel_ptr(bool batch);
+const void *stage_kernel_ptr(bool batch, int shape);
 
 // Carve the per-label arrays of M labels from `base` (256-byte aligned pieces); returns the
 // bytes used, or 0 when they do not fit in `cap` bytes.  label_arrays_bytes(M) is the size.

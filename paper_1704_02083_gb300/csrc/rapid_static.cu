@@ -156,8 +156,9 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   for (int l = 0; l < nsf; l++) pyr[l] = (int4 *)cv.take((size_t)cdiv(W, sf[l]) * cdiv(H, sf[l]) * sizeof(int4));
   const long long cap = (long long)cdiv(W, side[nst - 1]) * cdiv(H, side[nst - 1]);
   int *lab[2] = {(int *)cv.take(cap * sizeof(int)), (int *)cv.take(cap * sizeof(int))};
-  const int ntx_max = (cdiv(W, side[nst - 1]) + kTileW - 1) / kTileW;
-  const int nty_max = (cdiv(H, side[nst - 1]) + kTileH - 1) / kTileH;
+  const TileShape ts = kShapes[0];  // one tile shape for every stage here
+  const int ntx_max = (cdiv(W, side[nst - 1]) + ts.w - 1) / ts.w;
+  const int nty_max = (cdiv(H, side[nst - 1]) + ts.h - 1) / ts.h;
   int *trec = (int *)cv.take((size_t)ntx_max * nty_max * 9 * kRecInts * sizeof(int));
   ImageDesc *d_desc = (ImageDesc *)cv.take((size_t)nst * sizeof(ImageDesc));
   DevStats st;
@@ -200,8 +201,8 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
     d.W = W;
     d.nbx = cdiv(W, side[i]);
     d.nby = cdiv(H, side[i]);
-    d.ntx = (d.nbx + kTileW - 1) / kTileW;
-    d.nty = (d.nby + kTileH - 1) / kTileH;
+    d.ntx = (d.nbx + ts.w - 1) / ts.w;
+    d.nty = (d.nby + ts.h - 1) / ts.h;
     d.Wl = cdiv(W, fi);
     d.Hl = cdiv(H, fi);
     d.M = M;
@@ -218,7 +219,7 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   int dev = 0, nsm = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_ptr(false), stage_block_threads(), 0) !=
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_ptr(false, 0), stage_block_threads(), 0) !=
           cudaSuccess ||
       per_sm < 1)
     return RAPID_ECUDA;
@@ -286,7 +287,7 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
     }
     CKS(cudaMemsetAsync(c.bar, 0, 8, stream));
     CKS(cudaMemsetAsync(ctl + 16, 0, cl.reset_end - 16, stream));  // merge stamps, counts, sweep changes
-    CKS(launch_stage(a, nsm * per_sm, stage_block_threads(), stream));
+    CKS(launch_stage(a, nsm * per_sm, stage_block_threads(), stream, 0));
   }
   // Outputs into the caller's buffers.
   const ImageDesc &dl = desc[nst - 1];

@@ -70,6 +70,7 @@ def _run_with_grids(rgb, grids, autotune=False, **params):
         chosen = ctx.autotune() if autotune else None
         if grids is not None:
             ctx.set_stage_grids(grids)
+            ctx.set_stage_shapes([i % 3 for i in range(len(grids))][::-1])
         ctx.run()
         st = ctx.stats()
         return ctx.labels(), np.stack([st[f] for f in ("n", "sum_r", "sum_x")], 1), ctx.counters_array(), chosen
@@ -77,7 +78,8 @@ def _run_with_grids(rgb, grids, autotune=False, **params):
 
 @pytest.mark.parametrize("name,rgb,params", CASES[:3], ids=[c[0] for c in CASES[:3]])
 def test_launch_grid_changes_nothing(name, rgb, params):
-    """Any number of CTAs per stage (one, odd counts, the full grid) gives the same run."""
+    """Any number of CTAs per stage (one, odd counts, the full grid) and any tile shape give
+    the same run."""
     ref = _run_with_grids(rgb, None, **params)
     for grids in ([1] * 8, [3, 1, 7, 2, 5, 152, 9, 4], [2 ** i for i in range(8)]):
         got = _run_with_grids(rgb, grids, **params)
@@ -90,10 +92,10 @@ def test_autotune_picks_valid_grids_and_keeps_results():
 
     rgb, params = CASES[1][1], CASES[1][2]
     ref = _run_with_grids(rgb, None, **params)
-    lab, st, cnt, chosen = _run_with_grids(rgb, None, autotune=True, **params)
+    lab, st, cnt, (grids, shapes) = _run_with_grids(rgb, None, autotune=True, **params)
     full = torch.cuda.get_device_properties(0).multi_processor_count
-    assert len(chosen) == cnt.shape[0]
-    assert all(1 <= g <= full for g in chosen)
+    assert len(grids) == len(shapes) == cnt.shape[0]
+    assert all(1 <= g <= full for g in grids) and all(0 <= k < 3 for k in shapes)
     np.testing.assert_array_equal(lab, ref[0])
     np.testing.assert_array_equal(st, ref[1])
     np.testing.assert_array_equal(cnt, ref[2])
