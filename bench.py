@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="full grid for every stage")
     ap.add_argument("--no-graph", action="store_true", help="launch stage by stage instead of a CUDA graph")
+    ap.add_argument("--geometry", default=None,
+                    help="pinned launch geometry instead of autotuning: 'grid,grid,...:shape,shape,...' per stage")
     ap.add_argument("--prune", type=float, default=None,
                     help="the learned path: train the block scorer (untimed) and prune at this threshold")
     return ap.parse_args()
@@ -190,7 +192,8 @@ def kernel_source_sha256():
     """Hash of the sources the stage kernel is compiled from."""
     csrc = os.path.join(ROOT, "paper_1704_02083_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("k_stage.cu", "eval_tile.cuh", "rapid_dev.cuh"):
+    for name in ("stage_impl.cuh", "eval_tile.cuh", "rapid_dev.cuh", "k_stage_s0.cu", "k_stage_s1.cu",
+                 "k_stage_s2.cu"):
         h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()
 
@@ -272,14 +275,20 @@ def run_rapid(args, rank, world, local):
     ctx.set_images(dev_imgs, Ks)
     if scorer is not None:
         ctx.set_scorer(w_scorer, args.prune)
-    grids, shapes = ctx.autotune() if not args.no_autotune else (None, None)
+    if args.geometry:
+        g_str, s_str = args.geometry.split(":")
+        grids, shapes = [int(x) for x in g_str.split(",")], [int(x) for x in s_str.split(",")]
+        ctx.set_stage_grids(grids)
+        ctx.set_stage_shapes(shapes)
+    else:
+        grids, shapes = ctx.autotune() if not args.no_autotune else (None, None)
     ctx.set_profiling(True)
     ctx.set_graph(not args.no_graph)
     for _ in range(args.warmup):
         ctx.run()
     ctx.sync()
     c0 = ctx.counters(0)
-    nst = c0.num_stages
+    nst = None  # stages of the schedule, known after the first run
     L, C = params["num_levels"], params["ratio_C"]
     lf = {l: C ** (L - l) for l in range(1, L + 1)}
 
@@ -288,7 +297,7 @@ def run_rapid(args, rank, world, local):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    step_ms, stage_ms, stage_bytes = [], [0.0] * nst, [0] * nst
+    step_ms, stage_ms, stage_bytes = [], [], []
     for _ in range(args.steps):
         flush.zero_()  # L2 flush between steps (outside the timed events)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -298,6 +307,9 @@ def run_rapid(args, rank, world, local):
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
+        if nst is None:
+            nst = ctx.counters(0).num_stages
+            stage_ms, stage_bytes = [0.0] * nst, [0] * nst
         for i in range(n):
             c = ctx.counters(i)
             for s in range(nst):
