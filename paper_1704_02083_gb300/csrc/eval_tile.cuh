@@ -212,7 +212,7 @@ __device__ __forceinline__ void decide_block(const StageArgs &a, const ImageDesc
   const int k = decide(a, im, in, lc);
   if (k < 0) return;
   const long long idx = (long long)by * im.nbx + bx;
-  if (a.size_mode != 0 && (long long)a.lo_den * (s.N[lbl] - in.bs.w) < (long long)a.lo_num * s.init[lbl]) {
+  if (a.size_mode != 0 && (long long)a.lo_den * (s.mN[lbl] - in.bs.w) < (long long)a.lo_num * s.init[lbl]) {
     if (a.size_mode == 2) {
       lc.req++;
       atomicOr(&W.req[j >> 5], 1u << (j & 31));
@@ -224,21 +224,22 @@ __device__ __forceinline__ void decide_block(const StageArgs &a, const ImageDesc
     }
     return;
   }
-  // Move: relabel in place, accumulate the exact deltas of both labels.
+  // Move: relabel in place, add the exact sums to S (decisions of this phase read only the
+  // snapshot means and counts, never S).
   const BlockSums &bs = in.bs;
   im.lab[idx] = k;
-  atomic_add_i64(&s.dN[lbl], -bs.w);
-  atomic_add_i64(&s.dR[lbl], -bs.r);
-  atomic_add_i64(&s.dG[lbl], -bs.g);
-  atomic_add_i64(&s.dB[lbl], -bs.b);
-  atomic_add_i64(&s.dX[lbl], -bs.x);
-  atomic_add_i64(&s.dY[lbl], -bs.y);
-  atomic_add_i64(&s.dN[k], bs.w);
-  atomic_add_i64(&s.dR[k], bs.r);
-  atomic_add_i64(&s.dG[k], bs.g);
-  atomic_add_i64(&s.dB[k], bs.b);
-  atomic_add_i64(&s.dX[k], bs.x);
-  atomic_add_i64(&s.dY[k], bs.y);
+  atomic_add_i64(&s.N[lbl], -bs.w);
+  atomic_add_i64(&s.R[lbl], -bs.r);
+  atomic_add_i64(&s.G[lbl], -bs.g);
+  atomic_add_i64(&s.B[lbl], -bs.b);
+  atomic_add_i64(&s.X[lbl], -bs.x);
+  atomic_add_i64(&s.Y[lbl], -bs.y);
+  atomic_add_i64(&s.N[k], bs.w);
+  atomic_add_i64(&s.R[k], bs.r);
+  atomic_add_i64(&s.G[k], bs.g);
+  atomic_add_i64(&s.B[k], bs.b);
+  atomic_add_i64(&s.X[k], bs.x);
+  atomic_add_i64(&s.Y[k], bs.y);
   s.dirty[lbl] = 1;
   s.dirty[k] = 1;
   // the adjacency of the block's old and new labels and of its 4-neighbours' labels may

@@ -63,7 +63,7 @@ __global__ void reset_labels_kernel(DevStats st, DevMerge mg) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= st.M) return;
   st.N[k] = st.R[k] = st.G[k] = st.B[k] = st.X[k] = st.Y[k] = st.init[k] = 0;
-  st.dN[k] = st.dR[k] = st.dG[k] = st.dB[k] = st.dX[k] = st.dY[k] = 0;
+  st.mN[k] = 0;
   st.dirty[k] = 0;
   st.y[k] = 0;
   st.imp[k] = 0;
@@ -264,7 +264,7 @@ static size_t carve_impl(char *base, size_t cap, int M, DevStats *st, DevMerge *
     return r;
   };
   long long **i64[] = {&st->N, &st->R, &st->G, &st->B, &st->X, &st->Y, &st->init,
-                       &st->dN, &st->dR, &st->dG, &st->dB, &st->dX, &st->dY};
+                       &st->mN};
   for (long long **q : i64) *q = (long long *)take(m * 8);
   double **f64[] = {&st->mR, &st->mG, &st->mB, &st->mX, &st->mY};
   for (double **q : f64) *q = (double *)take(m * 8);

@@ -226,6 +226,7 @@ extern "C" rapid_status rapid_create(const rapid_params *p, void *cuda_stream, r
   char *b = (char *)ctx->d_ctl_block;
   ctx->ctl.bar = (unsigned *)(b + 0);
   ctx->ctl.err = (int *)(b + 8);
+  ctx->ctl.gen = (unsigned *)(b + ctx->cl.gen);
   ctx->mg.req_count = (int *)(b + 16);    // [2], by phase parity
   ctx->mg.found_count = (int *)(b + 24);  // [2], by phase parity
   ctx->mg.acc_count = (int *)(b + 32);

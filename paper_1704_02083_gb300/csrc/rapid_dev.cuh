@@ -7,7 +7,7 @@
 //           (R, G, B, 0) sums of the f x f full-res footprint (Sec. 2.2, box "resize")
 //   labels  two int32 maps sized for the finest stage; the current stage uses nby x nbx
 //   S       structure of arrays over label ids: count, R, G, B, x, y, InitSize (int64),
-//           phase deltas of the first six (int64), snapshot means (5 doubles) and their
+//           the phase-start snapshot of the count, snapshot means (5 doubles) and their
 //           single-precision hi/lo splits, last-change stamps, class y (int8),
 //           boundary-superpixel flag (uint8), conservative bounding box (int4)
 //   tiles   per (tile, phase class) scan record: stamp, label set, counts
@@ -50,8 +50,8 @@ static_assert(kRecInts <= 32, "a warp reads a tile record with one lane per int"
 constexpr int kCacheLabels = 16;           // neighbour labels remembered by a failed merge
 
 struct DevStats {
-  long long *N, *R, *G, *B, *X, *Y, *init;
-  long long *dN, *dR, *dG, *dB, *dX, *dY;
+  long long *N, *R, *G, *B, *X, *Y, *init;  // S; moves add into it during a phase
+  long long *mN;                            // count N at the start of the phase (snapshot)
   double *mR, *mG, *mB, *mX, *mY;
   float4 *fhi, *flo;  // single-precision (hi, lo) of cR, cG, cB, mX
   float2 *fy;         // (hi, lo) of mY
@@ -88,6 +88,7 @@ constexpr int kMaxBatch = 64;
 
 struct DevCtl {
   unsigned int *bar;             // [0] arrivals (monotone within a launch)
+  unsigned int *gen;             // barrier generation opened by the last arrival (own line)
   int *err;                      // first device error (0 = none)
   long long spin_ns;             // give-up time of one barrier wait
   unsigned long long *changes;   // [nimg][3] moves + merges of the sweep per image, rotating slots
@@ -96,15 +97,17 @@ struct DevCtl {
   long long *prof;               // this stage's section times [PROF_N] in ns, or null
 };
 
-// Control block of a context: barrier, error word, merge counts, per-image merge stamps and
-// sweep changes, per-(image, stage) counters, per-stage section times.  Every launch
-// clears [0, 8) and [16, reset_end); the error word persists.
+// Control block of a context: barrier counter (0), error word (8), merge counts (16..36),
+// barrier generation (128, a line of its own), per-image merge stamps and sweep changes,
+// per-(image, stage) counters, per-stage section times.  Every launch clears [0, 8) and
+// [16, reset_end); the error word persists.
 struct CtlLayout {
-  size_t last_merge, changes, cnt, prof, reset_end, total;
+  size_t gen, last_merge, changes, cnt, prof, reset_end, total;
 };
 inline CtlLayout ctl_layout(int nimg) {
   CtlLayout c;
-  c.last_merge = 64;
+  c.gen = 128;
+  c.last_merge = 256;
   c.changes = (c.last_merge + 4 * (size_t)nimg + 7) / 8 * 8;
   c.reset_end = c.changes + 24 * (size_t)nimg;
   c.cnt = (c.reset_end + 255) / 256 * 256;
@@ -226,8 +229,13 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ unsigned atom_acq_rel_add_u32(unsigned *p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(const volatile int *)p; }
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
@@ -235,22 +243,26 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
 }
 
 // All CTAs of a co-resident (cooperative) grid meet here.  The arrival counter only grows
-// during a launch: barrier number `epoch` (counted by every CTA) completes when it reaches
-// (epoch + 1) * gridDim.x.  Thread 0 arrives with a release add (after the CTA barrier, so
-// it publishes the whole CTA's writes) and polls with acquire loads.  Every wait is bounded
-// by ctl.spin_ns (and an iteration cap); on give-up the CTA records DERR_TIMEOUT and the
-// whole grid returns false, so no kernel can hang.
+// during a launch: barrier number `epoch` (counted by every CTA) is complete when it reaches
+// (epoch + 1) * gridDim.x.  Thread 0 arrives (after the CTA barrier) with an acquire-release
+// add; the CTA whose add completes the count opens the barrier by a release store of the
+// generation epoch + 1 to a flag on a line of its own, which the others poll with acquire
+// loads (the chain of adds carries every CTA's release to the last arrival, whose store
+// carries them on to the pollers).  Every wait is bounded by ctl.spin_ns (and an iteration
+// cap); on give-up the CTA records DERR_TIMEOUT and the whole grid returns false, so no
+// kernel can hang.
 __device__ inline bool grid_sync(const DevCtl &c, unsigned &epoch) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int good = 1;
-    const unsigned target = (epoch + 1) * gridDim.x;
-    red_release_add_u32(&c.bar[0], 1u);
-    if (ld_acquire_u32(&c.bar[0]) < target) {
+    const unsigned gen = epoch + 1;
+    if (atom_acq_rel_add_u32(&c.bar[0], 1u) + 1u == gen * gridDim.x) {
+      st_release_u32(c.gen, gen);
+    } else if (ld_acquire_u32(c.gen) < gen) {
       const unsigned long long t0 = global_ns();
       long long iters = 0;
-      while (ld_acquire_u32(&c.bar[0]) < target) {
+      while (ld_acquire_u32(c.gen) < gen) {
         if (ld_volatile_i32(c.err) != 0) {
           good = 0;
           break;
@@ -260,7 +272,7 @@ __device__ inline bool grid_sync(const DevCtl &c, unsigned &epoch) {
           good = 0;
           break;
         }
-        __nanosleep(20);  // keep the pollers from crowding the arrivals on the counter's line
+        __nanosleep(20);
       }
     }
     ok = good;
@@ -356,6 +368,7 @@ __device__ __forceinline__ void split_f(double v, float &hi, float &lo) {
 
 __device__ __forceinline__ void set_means(const DevStats &s, int k) {
   long long n = s.N[k];
+  s.mN[k] = n;
   double cr = 0.0, cg = 0.0, cb = 0.0, mx = 0.0, my = 0.0;
   if (n > 0) {
     double dn = __ll2double_rn(n);
@@ -384,15 +397,20 @@ __device__ __forceinline__ void set_means(const DevStats &s, int k) {
 
 // Merge cost of labels a and n (Sec. 3.1): the Ward increase of the colour and position
 // energy, Na Nn / (Na + Nn) * (|ca - cn|^2 + lambda_pos |mua - mun|^2).
+// The means are taken from S itself (the state after the phase's moves), with the same
+// operations as set_means, so they equal the snapshot means the next phase will use.
+__device__ __forceinline__ double mean_of(const long long *sum, const long long *cnt, int k) {
+  return __ddiv_rn(__ll2double_rn(sum[k]), __ll2double_rn(cnt[k]));
+}
 __device__ __forceinline__ double ward_cost(const DevStats &s, int a, int n, double lam_pos) {
   double t = __ddiv_rn(__dmul_rn(__ll2double_rn(s.N[a]), __ll2double_rn(s.N[n])),
                        __ll2double_rn(s.N[a] + s.N[n]));
-  double d0 = __dsub_rn(s.mR[a], s.mR[n]);
-  double d1 = __dsub_rn(s.mG[a], s.mG[n]);
-  double d2 = __dsub_rn(s.mB[a], s.mB[n]);
+  double d0 = __dsub_rn(mean_of(s.R, s.N, a), mean_of(s.R, s.N, n));
+  double d1 = __dsub_rn(mean_of(s.G, s.N, a), mean_of(s.G, s.N, n));
+  double d2 = __dsub_rn(mean_of(s.B, s.N, a), mean_of(s.B, s.N, n));
   double dc = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
-  double e0 = __dsub_rn(s.mX[a], s.mX[n]);
-  double e1 = __dsub_rn(s.mY[a], s.mY[n]);
+  double e0 = __dsub_rn(mean_of(s.X, s.N, a), mean_of(s.X, s.N, n));
+  double e1 = __dsub_rn(mean_of(s.Y, s.N, a), mean_of(s.Y, s.N, n));
   double dm = __dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1));
   return __dmul_rn(t, __dadd_rn(dc, __dmul_rn(lam_pos, dm)));
 }

@@ -174,6 +174,7 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   DevCtl c;
   c.bar = (unsigned *)(ctl + 0);
   c.err = (int *)(ctl + 8);
+  c.gen = (unsigned *)(ctl + cl.gen);
   mg.req_count = (int *)(ctl + 16);
   mg.found_count = (int *)(ctl + 24);
   mg.acc_count = (int *)(ctl + 32);

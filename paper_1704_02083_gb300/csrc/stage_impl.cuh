@@ -172,21 +172,14 @@ __device__ __forceinline__ float eps64(const float4 &h, const float2 &hy, float 
 
 #include "eval_tile.cuh"
 
-// Fold the phase's deltas into S, refresh the snapshot means of changed labels and stamp
-// them (2g).
+// Refresh the snapshot means and counts of the labels the phase's moves changed (S itself
+// already holds the moves) and stamp them (2g).
 __device__ void commit_phase(const StageArgs &a, int g) {
   const DevStats &s = a.st;
   // label k goes to CTA k % grid: the divisions of set_means spread over every SM
   for (int k = blockIdx.x + gridDim.x * threadIdx.x; k < s.M; k += gridDim.x * blockDim.x) {
     if (!s.dirty[k]) continue;
     s.dirty[k] = 0;
-    s.N[k] += s.dN[k];
-    s.R[k] += s.dR[k];
-    s.G[k] += s.dG[k];
-    s.B[k] += s.dB[k];
-    s.X[k] += s.dX[k];
-    s.Y[k] += s.dY[k];
-    s.dN[k] = s.dR[k] = s.dG[k] = s.dB[k] = s.dX[k] = s.dY[k] = 0;
     set_means(s, k);
     s.chg[k] = 2 * g;
   }
@@ -553,13 +546,14 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
         a.mg.req_count[gp ^ 1] = 0;
         a.mg.found_count[gp ^ 1] = 0;
       }
+      // the snapshot refresh and the merge-target search (which reads only S, the label
+      // map and the merge state) share the barrier that ends them
       commit_phase(a, g);
+      if (rq > 0) merge_targets<kBatch>(a, s_img, s_label0, rq, g);
       tm.lap(PROF_COMMIT);
       if (!grid_sync(a.ctl, epoch)) return;
       tm.lap(PROF_SYNC2);
       if (rq > 0) {
-        merge_targets<kBatch>(a, s_img, s_label0, rq, g);
-        if (!grid_sync(a.ctl, epoch)) return;
         const int nf = ld_volatile_i32(a.mg.found_count + gp);
         if (nf > 0) {
           if (nf <= kAcceptSmem) {
