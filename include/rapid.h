@@ -265,6 +265,26 @@ rapid_status rapid_trainer_fit(rapid_trainer *t, int32_t epochs, int32_t batch, 
                                uint64_t seed, const float *init, float *weights_out, float *epoch_loss);
 void rapid_trainer_destroy(rapid_trainer *t);
 
+/* Whole slide.  The slide (device, H x W interleaved RGB, rows rgb_pitch_bytes apart; any
+ * size) is cut into tiles by even row and column bands of at most max_tile pixels
+ * (startRow = H i / n, Eq. parallel_spit, on both axes); the tiles, as views into the
+ * slide, are refined on ctx in batches of up to RAPID_MAX_BATCH (each with
+ * K = max(1, area / px_per_superpixel) and ctx's parameters), and every tile's labels are
+ * written into labels_dev (device, H x W int32, rows labels_pitch_bytes apart) as
+ * slide-wide ids: the tiles' superpixels numbered one after another, tile by tile in
+ * row-major order.  Superpixels never cross a tile edge.  stats_dev (device, may be NULL)
+ * receives the statistics of every slide-wide id (capacity entries; EINVAL when too few).
+ * With autotune, the launch geometry is tuned on the first batch and kept; otherwise ctx's
+ * geometry is used.  *M_out and *tiles_out (may be NULL) receive the superpixel and tile
+ * counts.  ctx's images are replaced; it can serve further calls.  Synchronises.  EINVAL on
+ * bad arguments (max_tile in [16, 46340]), ERANGE beyond 2^24 tiles or 2^31 - 1
+ * superpixels. */
+rapid_status rapid_refine_slide(rapid_ctx *ctx, const uint8_t *rgb_dev, int64_t H, int64_t W,
+                                int64_t rgb_pitch_bytes, int32_t max_tile, int32_t px_per_superpixel,
+                                int32_t autotune, int32_t *labels_dev, int64_t labels_pitch_bytes,
+                                rapid_sp_stats *stats_dev, int64_t stats_capacity, int64_t *M_out,
+                                int32_t *tiles_out);
+
 /* Graph mode (0 = off, the default): rapid_run captures the schedule into a CUDA graph on
  * its first call after rapid_set_images and replays it afterwards (profiling events are
  * captured as event-record nodes, so kernel_ms keeps working).  Needs a non-default stream

@@ -105,6 +105,7 @@ def lib() -> C.CDLL:
         "rapid_set_graph": (i32, [P, i32]),
         "rapid_set_stage_grids": (i32, [P, pi32, i32]),
         "rapid_set_scorer": (i32, [P, P, C.c_float]),
+        "rapid_refine_slide": (i32, [P, P, i64, i64, i64, i32, i32, i32, P, i64, P, i64, pi64, pi32]),
         "rapid_scorer_features": (i32, [P, i32, P]),
         "rapid_scorer_scores": (i32, [P, i32, P, P]),
         "rapid_trainer_create": (i32, [i64, C.c_float, C.POINTER(P)]),
@@ -208,6 +209,17 @@ def rapid_read_counters(ctx: int) -> rapid_counters:
 
 
 RAPID_MAX_BATCH = 64
+
+
+def rapid_refine_slide(ctx: int, rgb_dev_ptr: int, H: int, W: int, rgb_pitch_bytes: int, max_tile: int,
+                       px_per_superpixel: int, autotune: bool, labels_dev_ptr: int, labels_pitch_bytes: int,
+                       stats_dev_ptr: int = 0, stats_capacity: int = 0):
+    """Whole slide in tiles of at most max_tile px (device buffers); returns (M, tiles)."""
+    M, T = C.c_int64(), C.c_int32()
+    _check(lib().rapid_refine_slide(ctx, rgb_dev_ptr, H, W, rgb_pitch_bytes, max_tile, px_per_superpixel,
+                                    1 if autotune else 0, labels_dev_ptr, labels_pitch_bytes, stats_dev_ptr or None,
+                                    stats_capacity, C.byref(M), C.byref(T)), "rapid_refine_slide")
+    return M.value, T.value
 
 
 def rapid_set_images(ctx: int, rgb_ptrs, H, W, row_pitch_bytes, K, rgb_is_device: int):
@@ -533,6 +545,22 @@ class Context:
 
     def set_stage_grids(self, grids):
         rapid_set_stage_grids(self.h, grids)
+
+    def refine_slide(self, rgb, max_tile: int = 8192, px_per_superpixel: int = 4096, autotune: bool = False,
+                     labels=None, stats=None):
+        """Whole slide: rgb is a CUDA uint8 tensor H x W x 3 with interleaved rows; labels (a
+        CUDA int32 H x W tensor, allocated when None) receives slide-wide ids; stats (a CUDA
+        uint8 tensor of capacity x 64 bytes, optional) their statistics.  Returns
+        (labels, M, tiles)."""
+        import torch
+        H, W = int(rgb.shape[0]), int(rgb.shape[1])
+        if labels is None:
+            labels = torch.empty((H, W), dtype=torch.int32, device=rgb.device)
+        cap = 0 if stats is None else stats.numel() // SP_STATS_DTYPE.itemsize
+        M, T = rapid_refine_slide(self.h, rgb.data_ptr(), H, W, rgb.stride(0), max_tile, px_per_superpixel, autotune,
+                                  labels.data_ptr(), labels.stride(0) * 4, 0 if stats is None else stats.data_ptr(),
+                                  cap)
+        return labels, M, T
 
     def set_stage_shapes(self, shapes):
         rapid_set_stage_shapes(self.h, shapes)

@@ -1064,6 +1064,74 @@ extern "C" rapid_status rapid_trainer_fit(rapid_trainer *t, int32_t epochs, int3
   return rs;
 }
 
+// ---------------------------------------------------------------- whole slides
+extern "C" rapid_status rapid_refine_slide(rapid_ctx *ctx, const uint8_t *rgb_dev, int64_t H, int64_t W,
+                                           int64_t rgb_pitch_bytes, int32_t max_tile, int32_t px_per_superpixel,
+                                           int32_t autotune, int32_t *labels_dev, int64_t labels_pitch_bytes,
+                                           rapid_sp_stats *stats_dev, int64_t stats_capacity, int64_t *M_out,
+                                           int32_t *tiles_out) {
+  if (!ctx || !rgb_dev || !labels_dev) return RAPID_EINVAL;
+  if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  if (H < 1 || W < 1 || rgb_pitch_bytes < 3 * W || labels_pitch_bytes < 4 * W || labels_pitch_bytes % 4) return RAPID_EINVAL;
+  if (max_tile < 16 || max_tile > 46340 || px_per_superpixel < 1 || (stats_dev && stats_capacity < 0)) return RAPID_EINVAL;
+  // even row and column bands (Eq. parallel_spit) no longer than max_tile
+  const long long nr = (H + max_tile - 1) / max_tile, nc = (W + max_tile - 1) / max_tile;
+  if (nr * nc > (1ll << 24)) return RAPID_ERANGE;
+  rapid_status rs = RAPID_OK;
+  const uint8_t *ptrs[kMaxBatch];
+  int32_t hs[kMaxBatch], ws[kMaxBatch], ks[kMaxBatch];
+  int64_t pitches[kMaxBatch];
+  long long r0s[kMaxBatch], c0s[kMaxBatch];
+  long long id_base = 0, t = 0;
+  bool tuned = false;
+  while (rs == RAPID_OK && t < nr * nc) {
+    int n = 0;
+    for (; n < kMaxBatch && t < nr * nc; n++, t++) {
+      const long long i = t / nc, j = t % nc;
+      const long long r0 = H * i / nr, r1 = H * (i + 1) / nr, c0 = W * j / nc, c1 = W * (j + 1) / nc;
+      ptrs[n] = rgb_dev + r0 * rgb_pitch_bytes + 3 * c0;
+      hs[n] = (int32_t)(r1 - r0);
+      ws[n] = (int32_t)(c1 - c0);
+      ks[n] = (int32_t)std::max<long long>(1, (r1 - r0) * (c1 - c0) / px_per_superpixel);
+      pitches[n] = rgb_pitch_bytes;
+      r0s[n] = r0;
+      c0s[n] = c0;
+    }
+    rs = rapid_set_images(ctx, n, ptrs, hs, ws, pitches, ks, 1);
+    if (rs == RAPID_OK && autotune && !tuned) {  // the first batch's geometry serves them all
+      // (a context keeps the geometry it was given or tuned before: pass autotune = 0 then)
+      rs = rapid_autotune(ctx, nullptr, nullptr);
+      tuned = true;
+    }
+    if (rs == RAPID_OK) rs = rapid_run(ctx);
+    if (rs != RAPID_OK) break;
+    if (id_base + ctx->M_total >= INT_MAX) {
+      rs = RAPID_ERANGE;
+      break;
+    }
+    // each tile's labels go into the slide's map as slide-wide ids (id_base + its ids)
+    const int side = ctx->st_side[ctx->cur];
+    for (int k = 0; k < n && rs == RAPID_OK; k++) {
+      const ImgHost &h = ctx->im[k];
+      const ImageDesc &d = host_desc(ctx, ctx->cur)[k];
+      int32_t *dst = (int32_t *)((char *)labels_dev + r0s[k] * labels_pitch_bytes) + c0s[k];
+      // the context's ids are already numbered across the batch: subtract -id_base
+      if (launch_upsample(d.lab, d.nbx, side, h.H, h.W, -(int)id_base, dst, labels_pitch_bytes / 4, ctx->stream) !=
+          cudaSuccess)
+        rs = cuda_fail(ctx);
+      if (rs == RAPID_OK && stats_dev && id_base + h.label0 + h.M <= stats_capacity &&
+          launch_pack_stats(ctx->st, h.label0, h.M, stats_dev + id_base + h.label0, ctx->stream) != cudaSuccess)
+        rs = cuda_fail(ctx);
+    }
+    id_base += ctx->M_total;
+    if (rs == RAPID_OK) rs = rapid_sync(ctx);  // the next batch reuses the context's buffers
+  }
+  if (rs == RAPID_OK && stats_dev && id_base > stats_capacity) rs = RAPID_EINVAL;
+  if (M_out) *M_out = id_base;
+  if (tiles_out) *tiles_out = (int32_t)(nr * nc);
+  return rs;
+}
+
 extern "C" rapid_status rapid_get_state(rapid_ctx *ctx, int32_t *stage, int32_t *level, int32_t *block,
                                         int32_t *M) {
   if (!ctx) return RAPID_EINVAL;

@@ -129,6 +129,65 @@ def he_image(H: int, W: int, n_cells: int, seed: int, nucleus_density: float = 1
     return SynthImage(rgb=out, regions=regions, roi=roi, n_regions=int(n + n_nuc))
 
 
+FOLD = (80, 40, 110)
+
+
+def slide_image(H: int, W: int, seed: int, px_per_cell: int = 8192, white_frac: float = 0.40,
+                fold_frac: float = 0.05) -> SynthImage:
+    """A whole-slide stand-in: the tile generator over the whole slide with ``white_frac``
+    white background, then tissue folds painted over it until they cover about
+    ``fold_frac`` of the area: straight dark-purple bands (colour FOLD + U{-10..10}, the
+    same noise) of width U{20..80} px, uniform angle and centre, length U[0.3, 1.0] x the
+    shorter side.  Each band is one more ground-truth region (not ROI)."""
+    img = he_image(H, W, max(1, (H * W) // px_per_cell), seed, white_frac=white_frac)
+    rgb, regions, roi = img.rgb, img.regions, img.roi
+    rng = np.random.default_rng(seed + 7919)
+    covered, target, band = 0, fold_frac * H * W, 0
+    while covered < target and band < 10000:
+        width = int(rng.integers(20, 81))
+        length = (0.3 + 0.7 * float(rng.integers(0, 1 << 20)) / float(1 << 20)) * min(H, W)
+        theta = np.pi * float(rng.integers(0, 1 << 20)) / float(1 << 20)
+        cy, cx = float(rng.integers(0, H)), float(rng.integers(0, W))
+        dy, dx = np.sin(theta), np.cos(theta)
+        # pixels p with |n.(p - c)| <= width / 2 and |d.(p - c)| <= length / 2, row by row
+        ext = 0.5 * (abs(dy) * length + abs(dx) * width) + 1
+        ys = np.arange(max(0, int(cy - ext)), min(H, int(cy + ext) + 1))
+        if ys.size == 0:
+            band += 1
+            continue
+        # for a row y the constraints are two intervals in x; intersect them
+        lo = np.full(ys.size, -np.inf)
+        hi = np.full(ys.size, np.inf)
+        # d.(p - c) = dx (x - cx) + dy (y - cy);  n.(p - c) = -dy (x - cx) + dx (y - cy)
+        for a, by, half in ((dx, dy, 0.5 * length), (-dy, dx, 0.5 * width)):
+            b = by * (ys - cy)  # the y part of the projection
+            if abs(a) < 1e-12:
+                bad = np.abs(b) > half
+                lo[bad], hi[bad] = np.inf, -np.inf
+                continue
+            x1 = (-half - b) / a + cx
+            x2 = (half - b) / a + cx
+            lo = np.maximum(lo, np.minimum(x1, x2))
+            hi = np.minimum(hi, np.maximum(x1, x2))
+        xl = np.clip(np.ceil(lo), 0, W).astype(np.int64)
+        xr = np.clip(np.floor(hi) + 1, 0, W).astype(np.int64)
+        n = np.maximum(xr - xl, 0)
+        if n.sum() == 0:
+            band += 1
+            continue
+        yy = np.repeat(ys, n)
+        xx = np.repeat(xl, n) + (np.arange(n.sum()) - np.repeat(np.cumsum(n) - n, n))
+        col = np.array(FOLD, np.int32) + rng.integers(-10, 11, size=3)
+        u = rng.integers(0, 1 << 32, size=(yy.size, 3), dtype=np.uint64).astype(np.uint32)
+        noise = np.searchsorted(_NOISE_CDF, u, side="right").astype(np.int32) + _NOISE_LO
+        rgb[yy, xx] = np.clip(col[None, :] + noise, 0, 255).astype(np.uint8)
+        regions[yy, xx] = img.n_regions + band
+        roi[yy, xx] = False
+        covered += int(n.sum())
+        band += 1
+    return SynthImage(rgb=rgb, regions=regions, roi=roi, n_regions=img.n_regions + band)
+
+
 def flat_image(H: int, W: int, colour=(128, 128, 128)) -> np.ndarray:
     """A constant-colour image (closed-form test cases)."""
     out = np.empty((H, W, 3), np.uint8)
@@ -176,6 +235,15 @@ BATCHES = {
     "batch64_l3": dict(n=64, seed=3, px_per_cell=8192, px_per_superpixel=4096,
                        params=dict(num_levels=3, ratio_C=4, init_block=32, final_grain=1,
                                    size_mode=2, predict=1, reuse=1)),
+}
+
+
+# Whole slides (scaled-down stand-ins for 100000 x 80000 NLST slides): size, seed, the
+# tile limit of the partition, superpixel density and the 3-level schedule.
+SLIDES = {
+    "slide16k_l3": dict(H=16384, W=12288, seed=5, max_tile=8192, px_per_superpixel=4096,
+                        params=dict(num_levels=3, ratio_C=4, init_block=32, final_grain=1, size_mode=2,
+                                    predict=1, reuse=1)),
 }
 
 
