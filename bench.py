@@ -64,6 +64,12 @@ def cpu_sample(workload: str):
     """A bounded sample of the workload for the CPU oracle: a 1024 x 1024 tile of the same
     generator with the same superpixel size and parameters."""
     from paper_1704_02083_gb300 import synth
+    if workload in synth.SLIDES:
+        sd = synth.SLIDES[workload]
+        params = dict(sd["params"], K=max(1, SAMPLE_SIDE * SAMPLE_SIDE // sd["px_per_superpixel"]))
+        img = synth.slide_image(SAMPLE_SIDE, SAMPLE_SIDE, sd["seed"])
+        return img.rgb, params, (f"{SAMPLE_SIDE}x{SAMPLE_SIDE} slide of the same generator (seed {sd['seed']}) and "
+                                 f"parameters (K={params['K']}), full schedule")
     if workload in synth.BATCHES:
         b = synth.BATCHES[workload]
         params = dict(b["params"])
@@ -436,11 +442,144 @@ def run_rapid(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_slide(args, rank, world, local):
+    """A whole slide through rapid_refine_slide: tiles of at most max_tile px as views into the
+    slide in HBM, refined in batches; one step = the whole slide."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import paper_1704_02083_gb300 as pkg
+    from paper_1704_02083_gb300 import synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sd = synth.SLIDES[args.workload]
+    H, W, params = sd["H"], sd["W"], dict(sd["params"])
+    img = synth.slide_image(H, W, sd["seed"])
+    npx = H * W
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    rgb = torch.from_numpy(img.rgb).cuda()
+    labels = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    ctx = pkg.Context(stream=stream, **params)
+    ctx.set_profiling(True)
+    kw = dict(max_tile=sd["max_tile"], px_per_superpixel=sd["px_per_superpixel"], labels=labels)
+    _, M, T = ctx.refine_slide(rgb, autotune=not args.no_autotune, **kw)  # first warm-up run tunes
+    for _ in range(max(0, args.warmup - 1)):
+        ctx.refine_slide(rgb, **kw)
+    ctx.sync()
+    c0 = ctx.counters(0)
+    L, C = params["num_levels"], params["ratio_C"]
+    lf = {l: C ** (L - l) for l in range(1, L + 1)}
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms, stage_ms, stage_bytes, nst, nimg = [], [], [], None, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.refine_slide(rgb, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        if nst is None:
+            nst = ctx.counters(0).num_stages
+            stage_ms, stage_bytes = [0.0] * nst, [0] * nst
+        nimg = 0
+        while True:  # the images of the slide's last batch (every tile when it fits in one)
+            try:
+                info = ctx.image_info(nimg)
+            except pkg.RapidError:
+                break
+            c = ctx.counters(nimg)
+            for st_i in range(nst):
+                if nimg == 0:
+                    stage_ms[st_i] += c.stage[st_i].kernel_ms
+                stage_bytes[st_i] += stage_alg_bytes(info["H"], info["W"], c.stage[st_i], lf)
+            nimg += 1
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    c1 = ctx.counters(0)
+    total_ms = max_over_ranks(sum(step_ms), dist)
+    value = whole_job_rate(npx, args.steps, total_ms / 1e3, dist) / 1e6
+
+    e2e = None
+    if not args.no_e2e:  # pinned host slide -> HBM, refine, labels -> pinned host
+        pin = torch.from_numpy(img.rgb).pin_memory()
+        lab_host = torch.empty((H, W), dtype=torch.int32).pin_memory()
+        times = []
+        for it in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            rgb.copy_(pin, non_blocking=True)
+            ctx.refine_slide(rgb, **kw)
+            lab_host.copy_(labels, non_blocking=True)
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                times.append(time.perf_counter() - t)
+        e2e = {"value": whole_job_rate(npx, len(times), sum(times), dist) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * npx, "d2h_bytes_per_step": 4 * npx}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rgb_s, params_s, desc = cpu_sample(args.workload)
+        ts = time_oracle(rgb_s, params_s, reps=1)
+        cpu = {"value": rgb_s.shape[0] * rgb_s.shape[1] / ts[0] / 1e6, "unit": UNIT, "cores": 1,
+               "kind": "oracle", "sample": desc}
+
+    peak, peak_kind = measured_peak()
+    dom = max(range(nst), key=lambda i: stage_ms[i])
+    launch_ms, launch_bytes = stage_ms[dom] / args.steps, stage_bytes[dom] / args.steps
+    achieved = launch_bytes / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else None
+    st_dom = c1.stage[dom]
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "H": H, "W": W, "tiles": T, "max_tile": sd["max_tile"],
+                       "M_total": M, "px_per_superpixel": sd["px_per_superpixel"],
+                       "batches": -(-T // pkg.RAPID_MAX_BATCH), "levels": L, "ratio_C": C,
+                       "init_block": params["init_block"], "predict": params["predict"],
+                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"kernel": f"stage_kernel, stage {dom} (level {st_dom.level}, block side {st_dom.block}), "
+                                   f"last batch ({nimg} tiles)",
+                         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind, "traffic": None,
+                         "alg_bytes_per_launch": launch_bytes, "launch_ms": launch_ms},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(round((c1.launches - c0.launches))),
+            "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    from paper_1704_02083_gb300 import synth
+    if args.workload in synth.SLIDES:
+        run_slide(args, rank, world, local)
         return
     run_rapid(args, rank, world, local)
 
