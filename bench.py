@@ -364,6 +364,20 @@ def run_rapid(args, rank, world, local):
                "h2d_bytes_per_step": 3 * npx,
                "d2h_bytes_per_step": 4 * npx + sum(Ms) * pkg.SP_STATS_DTYPE.itemsize}
 
+    # parity in the same run: the plain path's labels and statistics against the oracle's
+    # golden hashes (written by tests/golden/make_golden.py from the oracle alone)
+    parity = None
+    gpath = os.path.join(ROOT, "tests", "golden", f"{args.workload}.json")
+    if n == 1 and scorer is None and os.path.exists(gpath):
+        g = json.load(open(gpath))
+        st_np = ctx.image_stats(0)
+        fields = ("n", "sum_r", "sum_g", "sum_b", "sum_x", "sum_y", "init_size")
+        stats7 = np.stack([st_np[f] for f in fields], 1).astype("<i8")
+        sha = lambda a: hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+        ok = (sha(imgs[0]) == g["image_sha256"] and sha(ctx.image_labels(0).astype("<i4")) == g["labels_sha256"]
+              and sha(stats7) == g["stats_sha256"])
+        parity = "bit-exact vs the oracle's golden hashes (labels, S)" if ok else "MISMATCH vs the oracle's golden hashes"
+
     if scorer is not None:  # judged by the plain method: its labels, and the ground truth
         from paper_1704_02083_gb300 import quality, synth
         gts = [synth.workload_image(args.workload).regions] if n == 1 else None
@@ -411,7 +425,7 @@ def run_rapid(args, rank, world, local):
                "stage_grids": grids[:nst] if grids is not None else None,
                "stage_tiles": [f"{[32, 32, 64][k]}x{[16, 8, 16][k]}" for k in shapes[:nst]] if shapes else None,
                "cuda_graph": not args.no_graph,
-               "path": "plain" if scorer is None else "learned pruning", "scorer": scorer,
+               "path": "plain" if scorer is None else "learned pruning", "scorer": scorer, "parity": parity,
                "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
                "parallelism": f"replicas x{world}"}
         if n == 1:
