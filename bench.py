@@ -194,13 +194,17 @@ def kernel_traffic(workload: str):
     return d.get("dram_bytes_per_launch"), d
 
 
-def kernel_source_sha256():
-    """Hash of the sources the stage kernel is compiled from."""
-    csrc = os.path.join(ROOT, "paper_1704_02083_gb300", "csrc")
+def kernel_source_sha256(csrc=None):
+    """Hash of the code the stage kernel is compiled from: its sources with // comments,
+    trailing blanks and empty lines removed, so that editing a comment keeps the counters."""
+    csrc = csrc or os.path.join(ROOT, "paper_1704_02083_gb300", "csrc")
     h = hashlib.sha256()
     for name in ("stage_impl.cuh", "eval_tile.cuh", "rapid_dev.cuh", "k_stage_s0.cu", "k_stage_s1.cu",
                  "k_stage_s2.cu"):
-        h.update(open(os.path.join(csrc, name), "rb").read())
+        for line in open(os.path.join(csrc, name), encoding="utf-8"):
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()
 
 

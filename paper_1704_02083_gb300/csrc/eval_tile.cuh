@@ -1,8 +1,9 @@
-// eval_tile.cuh — block decisions of one phase, one warp per tile (included by k_stage.cu).
+// eval_tile.cuh — block decisions of one phase, one warp per tile (included by
+// stage_impl.cuh, once per evaluation-tile shape).
 //
-// A warp takes a 32 x 16-block tile, stages its labels with a 1-block halo in its own
-// shared window (34 x 18 int32) and gives each lane the tile's blocks of the phase class
-// (at most 11 x 6).  Warps never wait for each other inside a phase, so the SM hides the
+// A warp takes a kTileW x kTileH-block tile, stages its labels with a 1-block halo in its
+// own shared window ((kTileW + 2) x (kTileH + 2) int32) and gives each lane the tile's
+// blocks of the phase class (at most kPhaseMax; 11 x 6 for 32 x 16 tiles).  Warps never wait for each other inside a phase, so the SM hides the
 // global-memory latency of one warp's tile behind the work of the others.
 //
 // A tile is skipped when its record says that no label present in its window (halo

@@ -1,6 +1,7 @@
 // rapid_api.cu — the C ABI (include/rapid.h): context, device buffers, stage schedule and
 // launch orchestration for a batch of images (a single image is a batch of one).  Host
-// code only; every step of the method runs in the kernels of k_prep.cu and k_stage.cu.
+// code only; every step of the method runs in the kernels of k_prep.cu, k_stage_s*.cu
+// (through the dispatcher k_stage.cu) and, for the learned scorer, k_scorer.cu.
 #include <algorithm>
 #include <climits>
 #include <cmath>

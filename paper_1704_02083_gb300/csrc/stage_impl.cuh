@@ -10,14 +10,14 @@
 // blocks are at least 3 apart, so their 3x3 windows are disjoint: every block of a phase
 // decides from labels no other block of the phase writes, their boundary pairs are
 // disjoint, and each topology test stays valid when the others move.  Decisions use a
-// snapshot of the statistics S taken when the phase starts; moves update the label map
-// in place and accumulate exact int64 deltas that are folded into S after the phase.
-// Merge requests of the phase (size bound hit, Sec. 3.1) are then resolved against the
-// post-move state.
+// snapshot of the superpixel means (and sizes, for the size rule) taken when the phase
+// starts; moves update the label map in place and add their exact int64 sums into S
+// atomically.  Merge requests of the phase (size bound hit, Sec. 3.1) are then resolved
+// against the post-move S while the snapshot is refreshed.
 //
 // Work layout: one persistent CTA of 1024 threads per SM.  In the evaluation each warp takes
-// tiles of 32 x 16 blocks (CTA b takes tiles b, b + grid, ...; its warps draw them from a
-// shared counter), stages the tile's labels with a 1-block halo in shared memory and
+// tiles of kTileW x kTileH blocks (32 x 16, 32 x 8 or 64 x 16 by unit; CTA b takes tiles
+// b, b + grid, ...; its warps draw them from a shared counter), stages the tile's labels with a 1-block halo in shared memory and
 // decides the tile's blocks of the phase class (eval_tile.cuh).  A tile is skipped when no
 // label present in it has changed since its last scan in this phase class and that scan
 // issued no merge request: its blocks would decide exactly as before (no move), so the
