@@ -170,14 +170,18 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- algorithmic bytes
-def stage_alg_bytes(H, W, stage_counters, level_factor):
+def stage_alg_bytes(H, W, stage_counters, level_factor, frontier=False):
     """Algorithmic bytes of one stage's refinement launch: one read of the block-resolution
     label map per sweep, one 4-byte write per move, and one read of the stage's colour
-    source (3 bytes per pixel at full resolution, 3 int32 sums per coarse cell above it)."""
+    source (3 bytes per pixel at full resolution, 3 int32 sums per coarse cell above it).
+    The frontier schedule reads instead one queue bit per block per sweep and the label of
+    each eligible block it pops."""
     s = stage_counters.block
     nb = -(-W // s) * -(-H // s)
     f = level_factor[stage_counters.level]
     src = 3 * H * W if f == 1 else 12 * (-(-W // f)) * (-(-H // f))
+    if frontier:
+        return nb * stage_counters.sweeps / 8 + 4 * stage_counters.eligible + 4 * stage_counters.moves + src
     return 4 * nb * stage_counters.sweeps + 4 * stage_counters.moves + src
 
 
@@ -326,7 +330,7 @@ def run_rapid(args, rank, world, local):
                 st = c.stage[s]
                 if i == 0:
                     stage_ms[s] += st.kernel_ms  # the launch covers every image
-                stage_bytes[s] += stage_alg_bytes(sizes[i][0], sizes[i][1], st, lf)
+                stage_bytes[s] += stage_alg_bytes(sizes[i][0], sizes[i][1], st, lf, params.get("schedule", 0) == 1)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -430,6 +434,7 @@ def run_rapid(args, rank, world, local):
                "stage_tiles": [f"{[32, 32, 64][k]}x{[16, 8, 16][k]}" for k in shapes[:nst]] if shapes else None,
                "cuda_graph": not args.no_graph,
                "path": "plain" if scorer is None else "learned pruning", "scorer": scorer, "parity": parity,
+               "schedule": "frontier queue" if params.get("schedule", 0) == 1 else "sweeps",
                "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
                "parallelism": f"replicas x{world}"}
         if n == 1:
@@ -446,6 +451,7 @@ def run_rapid(args, rank, world, local):
                          "share_of_step": launch_ms / (total_ms / args.steps),
                          "all_stage_launches": {"launches_per_step": nst,
                                                 "ms_per_step": all_ms / args.steps,
+                                                "stage_ms": [round(x / args.steps, 3) for x in stage_ms],
                                                 "alg_bytes_per_step": all_bytes / args.steps,
                                                 "achieved": all_achieved,
                                                 "frac": (all_achieved / peak) if all_achieved else None}},

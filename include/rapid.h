@@ -81,7 +81,14 @@ typedef struct rapid_params {
                               (same results and counters as 0, faster).  Default 1. */
   int32_t verify_filter;   /* 1: also decide every block in binary64 and count disagreements
                               with the single-precision decisions (testing).  Default 0. */
-  int32_t pad;
+  int32_t schedule;        /* which blocks a phase visits (Sec. 2.1, the boundary queue):
+                              0 = every block of the phase class, every sweep (default);
+                              1 = frontier queue: every block is queued when a stage starts, a
+                              phase pops the queued blocks of its class, and a move (or an
+                              accepted merge, at its first requesting block) pushes the
+                              block's 4-neighbours.  Results differ from 0; the stage still
+                              ends after a sweep without changes (the queue is then empty).
+                              Not combinable with the learned scorer (RAPID_EINVAL). */
 } rapid_params;
 
 #define RAPID_MAX_STAGES 32

@@ -25,7 +25,7 @@ class OrcParams(C.Structure):
         ("lambda_pos0", C.c_double), ("lambda_b", C.c_double),
         ("lo_num", C.c_int32), ("lo_den", C.c_int32), ("hi_num", C.c_int32), ("hi_den", C.c_int32),
         ("predict", C.c_int32), ("reuse", C.c_int32), ("importance_rule", C.c_int32),
-        ("max_sweeps", C.c_int32), ("h_T", C.c_int64),
+        ("max_sweeps", C.c_int32), ("h_T", C.c_int64), ("schedule", C.c_int32), ("pad", C.c_int32),
     ]
 
 
@@ -33,7 +33,7 @@ class OrcParams(C.Structure):
 # (Sec. 3.1), u = 3/2, T = 150, 64 sweeps per stage.
 DEFAULTS = dict(num_levels=1, ratio_C=4, init_block=16, final_grain=1, K=200, size_mode=2,
                 lambda_pos0=400.0, lambda_b=50.0, lo_num=1, lo_den=4, hi_num=3, hi_den=2,
-                predict=0, reuse=1, importance_rule=0, max_sweeps=64, h_T=150)
+                predict=0, reuse=1, importance_rule=0, max_sweeps=64, h_T=150, schedule=0)
 
 _lib = None
 

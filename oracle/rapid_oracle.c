@@ -23,6 +23,11 @@
  *    taken at the start of the phase, then the moves are applied together.  (The paper's
  *    queue updates after every move; the sequential FIFO variant orc_run_fifo keeps that
  *    order for quality comparison.)
+ *  - With schedule 1 the phases work through a queue instead (the boundary queue of
+ *    Sec. 2.1 kept as a set of flags, one per block): every block is queued when the
+ *    refinement of a stage starts, a phase takes the queued blocks of its class off the
+ *    queue and evaluates those, and each block that moves -- and each accepted merge, at
+ *    the block whose request was accepted -- puts its 4-neighbours on the queue.
  */
 #include "rapid_oracle.h"
 
@@ -61,6 +66,7 @@ struct orc_state {
   uint32_t *visit; /* flood-fill marks: visit[i] == visit_id means visited in this fill */
   uint32_t visit_id;
   int64_t *queue;
+  uint8_t *queued; /* schedule 1: 1 when the block is on the queue */
 };
 
 enum { C_LEVEL, C_SIDE, C_SWEEPS, C_ELIG, C_EVAL, C_MOVES, C_REQ, C_MERGES };
@@ -211,9 +217,10 @@ orc_state *orc_create(const uint8_t *rgb, int32_t H, int32_t W, const orc_params
   st->lab = (int32_t *)malloc(cap * sizeof(int32_t));
   st->visit = (uint32_t *)calloc(cap, sizeof(uint32_t));
   st->queue = (int64_t *)malloc(cap * sizeof(int64_t));
+  st->queued = (uint8_t *)malloc(cap);
   orc_simple_lut(st->lut);
   st->cur = -1;
-  if (!st->lab || !st->visit || !st->queue) { orc_destroy(st); *status = 2; return NULL; }
+  if (!st->lab || !st->visit || !st->queue || !st->queued) { orc_destroy(st); *status = 2; return NULL; }
   *status = 0;
   return st;
 }
@@ -225,6 +232,7 @@ void orc_destroy(orc_state *st) {
   free(st->lab);
   free(st->visit);
   free(st->queue);
+  free(st->queued);
   free(st->req_blk);
   free(st->req_lab);
   free(st->N); free(st->R); free(st->G); free(st->B); free(st->X); free(st->Y); free(st->init);
@@ -249,6 +257,16 @@ static void set_stage_grid(orc_state *st, int32_t i) {
   st->nby = ceil_div(st->H, st->side);
   st->cnt[i][C_LEVEL] = st->level;
   st->cnt[i][C_SIDE] = st->side;
+  memset(st->queued, 1, (size_t)st->nbx * st->nby);
+}
+
+/* Schedule 1: the 4-neighbours of block blk that lie on the grid go on the queue. */
+static void queue_neighbours(orc_state *st, int64_t blk) {
+  int32_t bx = (int32_t)(blk % st->nbx), by = (int32_t)(blk / st->nbx);
+  if (by > 0) st->queued[blk - st->nbx] = 1;
+  if (bx > 0) st->queued[blk - 1] = 1;
+  if (bx + 1 < st->nbx) st->queued[blk + 1] = 1;
+  if (by + 1 < st->nby) st->queued[blk + st->nbx] = 1;
 }
 
 /* Statistics S of every label recomputed from the label map and the current level
@@ -509,12 +527,19 @@ int32_t orc_phase_moves(orc_state *st, int32_t phase, int64_t *moves_out, int64_
   for (int32_t by = py; by < st->nby; by += 3)
     for (int32_t bx = px; bx < st->nbx; bx += 3) {
       int32_t k = -1;
-      int r = decide(st, bx, by, cR, cG, cB, mX, mY, N0, &k, &c[C_ELIG], &c[C_EVAL]);
       int64_t blk = (int64_t)by * st->nbx + bx;
+      if (st->p.schedule == 1) { /* only queued blocks, which leave the queue */
+        if (!st->queued[blk]) continue;
+        st->queued[blk] = 0;
+      }
+      int r = decide(st, bx, by, cR, cG, cB, mX, mY, N0, &k, &c[C_ELIG], &c[C_EVAL]);
       if (r == 1) { mv[nmv].blk = blk; mv[nmv].a = st->lab[blk]; mv[nmv].k = k; nmv++; }
       if (r == 2) { st->req_blk[st->nreq] = blk; st->req_lab[st->nreq] = st->lab[blk]; st->nreq++; }
     }
-  for (int64_t i = 0; i < nmv; i++) apply_move(st, mv[i].blk, mv[i].a, mv[i].k);
+  for (int64_t i = 0; i < nmv; i++) {
+    apply_move(st, mv[i].blk, mv[i].a, mv[i].k);
+    if (st->p.schedule == 1) queue_neighbours(st, mv[i].blk);
+  }
   c[C_MOVES] += nmv;
   c[C_REQ] += st->nreq;
   st->phase_moves = nmv;
@@ -544,6 +569,7 @@ int32_t orc_phase_merges(orc_state *st, int64_t *merges_out) {
       inv[a] = inv[n] = 1;
       to[a] = n;
       nmerge++;
+      if (st->p.schedule == 1) queue_neighbours(st, st->req_blk[i]);
     }
     if (nmerge > 0) {
       for (int64_t i = 0; i < (int64_t)st->nbx * st->nby; i++)
@@ -580,6 +606,7 @@ int32_t orc_phase(orc_state *st, int32_t phase, int64_t *moves_out, int64_t *mer
  * empty"), or max_sweeps. */
 int32_t orc_refine_stage(orc_state *st) {
   if (st->cur < 0) return 4;
+  memset(st->queued, 1, (size_t)st->nbx * st->nby); /* schedule 1: every block queued */
   for (int32_t s = 0; s < st->p.max_sweeps; s++) {
     int64_t changes = 0;
     for (int32_t ph = 0; ph < 9; ph++) {

@@ -36,6 +36,12 @@ typedef struct orc_params {
   int32_t importance_rule; /* 0: block's superpixel must be a boundary superpixel; 1: pair rule */
   int32_t max_sweeps;      /* per stage */
   int64_t h_T;             /* brightness threshold of the stand-in classifier */
+  int32_t schedule;        /* 0: a phase visits every block of its class; 1: frontier queue
+                              (every block queued at the start of a stage refinement; a phase
+                              pops the queued blocks of its class; a move, or an accepted
+                              merge at its first requesting block, queues the block's
+                              4-neighbours) */
+  int32_t pad;
 } orc_params;
 
 typedef struct orc_state orc_state;

@@ -35,7 +35,7 @@ class rapid_params(C.Structure):
         ("lo_num", C.c_int32), ("lo_den", C.c_int32), ("hi_num", C.c_int32), ("hi_den", C.c_int32),
         ("predict", C.c_int32), ("reuse", C.c_int32), ("importance_rule", C.c_int32),
         ("max_sweeps", C.c_int32), ("h_T", C.c_int64), ("spin_limit_ns", C.c_int64),
-        ("use_filter", C.c_int32), ("skip_tiles", C.c_int32), ("verify_filter", C.c_int32), ("pad", C.c_int32),
+        ("use_filter", C.c_int32), ("skip_tiles", C.c_int32), ("verify_filter", C.c_int32), ("schedule", C.c_int32),
     ]
 
 

@@ -22,6 +22,7 @@ struct WarpTile {
   unsigned prevreq[kReqWords];  // blocks that requested a merge at the previous scan
   unsigned req[kReqWords];      // blocks that request one now
   int items[kPhaseMax];         // phase-class blocks (index j) that need a decision
+  unsigned queue[kReqWords];    // frontier schedule: the blocks popped from the queue now
   int hcount, over;         // labels in the table; more than kTileLabels (or table full)
 };
 
@@ -194,6 +195,27 @@ __device__ __forceinline__ bool block_needs_decision(const StageArgs &a, const W
   return true;
 }
 
+// Frontier schedule: queue block (gx, gy) of image im (no-op outside the block grid).  Its
+// tile, phase class and index j in the class lattice of the tile are those eval_phase
+// enumerates: the class lattice of a tile starts at (lx % 3, ly % 3).
+__device__ __forceinline__ void queue_push(const StageArgs &a, const ImageDesc &im, int gx, int gy) {
+  if (gx < 0 || gy < 0 || gx >= im.nbx || gy >= im.nby) return;
+  const int tx = gx / kTileW, ty = gy / kTileH;
+  const int lx = gx - tx * kTileW, ly = gy - ty * kTileH;
+  const int tw = min(kTileW, im.nbx - tx * kTileW);
+  const int nx = (tw - lx % 3 + 2) / 3;
+  const int j = (ly / 3) * nx + lx / 3;
+  const long long t = (long long)im.tile0 + (long long)ty * im.ntx + tx;
+  atomicOr(&a.qbits[(t * 9 + (gy % 3) * 3 + gx % 3) * kQueueWords + (j >> 5)], 1u << (j & 31));
+}
+
+__device__ __forceinline__ void queue_push_neighbours(const StageArgs &a, const ImageDesc &im, int bx, int by) {
+  queue_push(a, im, bx, by - 1);
+  queue_push(a, im, bx - 1, by);
+  queue_push(a, im, bx + 1, by);
+  queue_push(a, im, bx, by + 1);
+}
+
 // Pass 2 (one compacted block per lane): block sums, the decision (Eq. operation), the size
 // term (Sec. 3.1) and the move.
 __device__ __forceinline__ void decide_block(const StageArgs &a, const ImageDesc &im, WarpTile &W, int c, int j, int bx,
@@ -217,8 +239,8 @@ __device__ __forceinline__ void decide_block(const StageArgs &a, const ImageDesc
     if (a.size_mode == 2) {
       lc.req++;
       atomicOr(&W.req[j >> 5], 1u << (j & 31));
-      atomicMin(&a.mg.req_min[lbl], im.blk0 + (int)idx);  // global block order
-      if (atomicExch(&a.mg.req_flag[lbl], 1) == 0) {
+      atomicMin(&a.mg.req_min[lbl], req_key(g, im.blk0 + idx));  // global block order
+      if (atomicExch(&a.mg.req_flag[lbl], g) != g) {
         const int slot = atomicAdd(a.mg.req_count + (g & 1), 1);
         a.mg.req_list[slot] = lbl;
       }
@@ -253,6 +275,7 @@ __device__ __forceinline__ void decide_block(const StageArgs &a, const ImageDesc
   atomicMin(&s.bbox[k].y, in.y0);
   atomicMax(&s.bbox[k].z, in.x0 + bs.bw - 1);
   atomicMax(&s.bbox[k].w, in.y0 + bs.bh - 1);
+  if (a.frontier) queue_push_neighbours(a, im, bx, by);  // (other phase classes only)
   lc.moves++;
 }
 
@@ -344,7 +367,19 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
     const int tx = lt % im.ntx, ty = lt / im.ntx;
     const int bx0 = tx * kTileW, by0 = ty * kTileH;
     int *rec = a.trec + ((long long)t * 9 + phase) * kRecInts;
-    const int rv = lane < kRecInts ? rec[lane] : 0;
+    const bool fq = a.frontier;
+    unsigned qv = 0u;
+    if (fq) {  // frontier schedule: pop the tile's queued blocks of this class (if any)
+      unsigned *qw = a.qbits + ((long long)t * 9 + phase) * kQueueWords;
+      qv = lane < kReqWords ? qw[lane] : 0u;
+      if (!__any_sync(0xffffffffu, qv != 0u)) {
+        if (lane == 0) skipped++;
+        continue;
+      }
+      if (lane < kReqWords) qw[lane] = 0u;
+    }
+    // the tile's record (not used by the frontier schedule)
+    const int rv = (!fq && lane < kRecInts) ? rec[lane] : 0;
     // a record from before the image's switch from pruned to full sweeps counts as none
     const int stamp_rec = __shfl_sync(0xffffffffu, rv, 0), nlab = __shfl_sync(0xffffffffu, rv, 1);
     const int stamp = stamp_rec >= valid_from[cur] ? stamp_rec : 0;
@@ -374,6 +409,7 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
       W.req[lane - 4 - kTileLabels] = 0u;
       W.prevreq[lane - 4 - kTileLabels] = stamp > 0 ? (unsigned)rv : 0u;
     }
+    if (lane < kReqWords) W.queue[lane] = qv;
     __syncwarp();
     // window: lane = column (lanes 0 and 1 also take columns 32 and 33); the label of each
     // run of equal labels down a column goes into the table
@@ -392,7 +428,7 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
         const int v = vals[wy];
         W.win[wy * kWinW + col] = v;
         // once the window has more labels than a record holds the table is not used
-        if (v != prev && v >= 0 && !*(volatile int *)&W.over) tab_insert(W, v);
+        if (!fq && v != prev && v >= 0 && !*(volatile int *)&W.over) tab_insert(W, v);
         prev = v;
       }
     }
@@ -412,7 +448,7 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
     for (int j0 = 0; j0 < nx * ny; j0 += 32) {
       const int j = j0 + lane;
       bool need = false;
-      if (j < nx * ny) {
+      if (j < nx * ny && (!fq || ((W.queue[j >> 5] >> (j & 31)) & 1u))) {
         const int lx = lx0 + 3 * (j % nx), ly = ly0 + 3 * (j / nx);
         need = block_needs_decision(a, W, (ly + 1) * kWinW + (lx + 1), j, block_skip, mask,
                                     (long long)(by0 + ly) * im.nbx + (bx0 + lx), lc);
@@ -431,16 +467,18 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
     const int de = warp_sum(lc.elig - e0), dv = warp_sum(lc.eval - v0);
     __syncwarp();
     // record: the table's labels (when at most kTileLabels), counts, request mask
-    const unsigned present = __ballot_sync(0xffffffffu, key >= 0);
-    const int pos = __popc(present & ((1u << lane) - 1u));
-    if (key >= 0 && pos < kTileLabels) rec[4 + pos] = key;
-    if (lane == 0) {
-      rec[0] = g;
-      rec[2] = (int)de;
-      rec[3] = (int)dv;
-      rec[1] = W.over ? -1 : __popc(present);
+    if (!fq) {
+      const unsigned present = __ballot_sync(0xffffffffu, key >= 0);
+      const int pos = __popc(present & ((1u << lane) - 1u));
+      if (key >= 0 && pos < kTileLabels) rec[4 + pos] = key;
+      if (lane == 0) {
+        rec[0] = g;
+        rec[2] = (int)de;
+        rec[3] = (int)dv;
+        rec[1] = W.over ? -1 : __popc(present);
+      }
+      if (req_lane) rec[lane] = (int)W.req[lane - 4 - kTileLabels];
     }
-    if (req_lane) rec[lane] = (int)W.req[lane - 4 - kTileLabels];
     __syncwarp();
   }
   flush_counts(a, cur, slot, lc, scanned, skipped);

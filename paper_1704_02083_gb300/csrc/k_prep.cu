@@ -68,7 +68,7 @@ __global__ void reset_labels_kernel(DevStats st, DevMerge mg) {
   st.y[k] = 0;
   st.imp[k] = 0;
   st.bbox[k] = make_int4(INT_MAX, INT_MAX, INT_MIN, INT_MIN);
-  mg.req_min[k] = INT_MAX;
+  mg.req_min[k] = ~0ull;
   mg.req_flag[k] = 0;
   mg.target[k] = -1;
   mg.involved[k] = 0;
@@ -275,7 +275,8 @@ static size_t carve_impl(char *base, size_t cap, int M, DevStats *st, DevMerge *
   st->chg = (int *)take(m * 4);
   st->adj = (int *)take(m * 4);
   mg->acc = (int2 *)take(m * 8);
-  int **i32[] = {&mg->req_list, &mg->req_min, &mg->req_flag, &mg->target, &mg->order, &mg->cache_stamp, &mg->cache_n};
+  mg->req_min = (unsigned long long *)take(m * 8);
+  int **i32[] = {&mg->req_list, &mg->req_flag, &mg->target, &mg->order, &mg->cache_stamp, &mg->cache_n};
   for (int **q : i32) *q = (int *)take(m * 4);
   mg->cache_nb = (int *)take(m * 4 * kCacheLabels);
   mg->found = (int *)take(m * 4);

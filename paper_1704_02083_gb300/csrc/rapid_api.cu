@@ -73,6 +73,8 @@ struct rapid_ctx {
   size_t full_cap;
   int *d_trec;  // tile scan records, sized for the finest stage
   size_t trec_cap;
+  unsigned *d_qbits;  // frontier queue (schedule 1), sized like the tile records
+  size_t qbits_cap;
   // per (stage, image) descriptors
   ImageDesc *h_desc;  // [nstages * nimg]
   ImageDesc *d_desc;
@@ -169,6 +171,7 @@ extern "C" void rapid_default_params(rapid_params *p) {
   p->use_filter = 1;
   p->skip_tiles = 1;
   p->verify_filter = 0;
+  p->schedule = 0;
 }
 
 static bool params_ok(const rapid_params *p) {
@@ -179,7 +182,8 @@ static bool params_ok(const rapid_params *p) {
   if (p->K < 1 || p->size_mode < 0 || p->size_mode > 2 || p->max_sweeps < 1) return false;
   if (p->lo_den <= 0 || p->hi_den <= 0 || p->lo_num < 0 || p->hi_num < 0) return false;
   if (!std::isfinite(p->lambda_pos0) || !std::isfinite(p->lambda_b)) return false;
-  if ((p->predict | p->reuse | p->importance_rule | p->use_filter | p->skip_tiles | p->verify_filter) & ~1)
+  if ((p->predict | p->reuse | p->importance_rule | p->use_filter | p->skip_tiles | p->verify_filter |
+       p->schedule) & ~1)
     return false;
   if (p->spin_limit_ns < 0 || p->h_T < 0 || p->h_T > (1ll << 40)) return false;
   long long f1 = 1;
@@ -273,6 +277,9 @@ static void free_image_buffers(rapid_ctx *ctx) {
   cudaFree(ctx->d_trec);
   ctx->d_trec = nullptr;
   ctx->trec_cap = 0;
+  cudaFree(ctx->d_qbits);
+  ctx->d_qbits = nullptr;
+  ctx->qbits_cap = 0;
   cudaFree(ctx->d_desc);
   ctx->d_desc = nullptr;
   ctx->desc_cap = 0;
@@ -505,6 +512,9 @@ extern "C" rapid_status rapid_set_images(rapid_ctx *ctx, int32_t n, const uint8_
   for (int b = 0; b < 2; b++)
     if (!grow(&ctx->d_lab[b], &ctx->lab_cap[b], lab_n * sizeof(int))) return RAPID_ENOMEM;
   if (!grow(&ctx->d_trec, &ctx->trec_cap, (size_t)tiles_last * 9 * kRecInts * sizeof(int))) return RAPID_ENOMEM;
+  if (ctx->p.schedule == 1 &&
+      !grow(&ctx->d_qbits, &ctx->qbits_cap, (size_t)tiles_last * 9 * kQueueWords * sizeof(unsigned)))
+    return RAPID_ENOMEM;
   if (!grow(&ctx->d_full, &ctx->full_cap, (size_t)npx_max * sizeof(int))) return RAPID_ENOMEM;
   if (!grow(&ctx->d_pack, &ctx->pack_cap, (size_t)max_M * sizeof(rapid_sp_stats))) return RAPID_ENOMEM;
   rs = ensure_label_arrays(ctx, ctx->M_total);
@@ -566,6 +576,8 @@ static StageArgs stage_args(rapid_ctx *ctx, int s) {
   a.verify_filter = ctx->p.verify_filter;
   a.skip_tiles = ctx->p.skip_tiles;
   a.prune = ctx->scorer_on;
+  a.frontier = ctx->p.schedule == 1;
+  a.qbits = ctx->d_qbits;
   return a;
 }
 
@@ -877,6 +889,7 @@ extern "C" rapid_status rapid_set_scorer(rapid_ctx *ctx, const float *weights, f
     return RAPID_OK;
   }
   if (!(threshold >= 0.f && threshold <= 1.f)) return RAPID_EINVAL;
+  if (ctx->p.schedule != 0) return RAPID_EINVAL;  // pruned sweeps are defined for schedule 0 only
   for (int i = 0; i < RAPID_SCORER_PARAMS; i++)
     if (!std::isfinite(weights[i])) return RAPID_EINVAL;
   if (!ctx->d_scorer && cudaMalloc(&ctx->d_scorer, scorer_dev_bytes()) != cudaSuccess) return RAPID_ENOMEM;

@@ -71,8 +71,10 @@ struct DevMerge {
   int *found;       // [M] those requested labels
 
   int *req_list;    // [M] requested label ids
-  int *req_min;     // [M] smallest requesting block index per label (INT_MAX = none)
-  int *req_flag;    // [M] 1 when the label is in req_list
+  // [M] smallest request key per label: (0xFFFFFFFF - phase) << 32 | global block index, so
+  // that a later phase's key always wins the atomicMin and nothing has to be cleared
+  unsigned long long *req_min;
+  int *req_flag;    // [M] phase number in which the label was last put in req_list (0 = never)
   int *target;      // [M] chosen merge target (or -1)
   int *order;       // [M] scratch: requests sorted by req_min
   int2 *acc;        // [M] accepted (source, target) pairs of the phase
@@ -83,8 +85,17 @@ struct DevMerge {
   int *cache_nb;    // [M * kCacheLabels] those neighbour labels
 };
 
+__device__ __forceinline__ unsigned long long req_key(int g, long long blk) {
+  return ((unsigned long long)(0xFFFFFFFFu - (unsigned)g) << 32) | (unsigned long long)(unsigned)blk;
+}
+// the requesting block of a key of the current phase
+__device__ __forceinline__ int req_block(unsigned long long key) { return (int)(unsigned)(key & 0xFFFFFFFFull); }
+
 // Images one context refines together (one launch per stage covers all of them).
 constexpr int kMaxBatch = 64;
+// 32-bit words of the frontier queue per (tile, phase class): enough for the largest tile
+// shape's class lattice (22 x 6 blocks of a 64 x 16 tile)
+constexpr int kQueueWords = 5;
 
 struct DevCtl {
   unsigned int *bar;             // [0] arrivals (monotone within a launch)
@@ -157,6 +168,9 @@ struct StageArgs {
   int size_mode, lo_num, lo_den, hi_num, hi_den;
   int max_sweeps;
   int prune;          // 1: sweep with the scorer's masks until a sweep changes nothing, then in full
+  int frontier;       // 1: a phase visits only the queued blocks of its class (schedule 1)
+  unsigned *qbits;    // frontier queue [ntiles * 9 * kQueueWords]: bit j of (tile, class) =
+                      // the class's j-th block of the tile (row-major over the class lattice)
 };
 
 // Box-sum levels kept for block sums: the method's level factors (> 1) plus 4, 16 and 64

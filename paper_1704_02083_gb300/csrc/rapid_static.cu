@@ -97,7 +97,7 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   if (p->K < 1 || p->size_mode < 0 || p->size_mode > 2 || p->max_sweeps < 1) return RAPID_EINVAL;
   if (p->lo_den <= 0 || p->hi_den <= 0 || p->lo_num < 0 || p->hi_num < 0) return RAPID_EINVAL;
   if (!std::isfinite(p->lambda_pos0) || !std::isfinite(p->lambda_b)) return RAPID_EINVAL;
-  if ((p->predict | p->reuse | p->importance_rule) & ~1) return RAPID_EINVAL;
+  if ((p->predict | p->reuse | p->importance_rule | p->schedule) & ~1) return RAPID_EINVAL;
   if (p->spin_limit_ns < 0 || p->h_T < 0 || p->h_T > (1ll << 40)) return RAPID_EINVAL;
   if ((long long)H * W > RAPID_STATIC_MAX_PIXELS) return RAPID_ERANGE;
   cudaStream_t stream = (cudaStream_t)cuda_stream;
@@ -160,6 +160,9 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   const int ntx_max = (cdiv(W, side[nst - 1]) + ts.w - 1) / ts.w;
   const int nty_max = (cdiv(H, side[nst - 1]) + ts.h - 1) / ts.h;
   int *trec = (int *)cv.take((size_t)ntx_max * nty_max * 9 * kRecInts * sizeof(int));
+  unsigned *qbits = p->schedule == 1
+                        ? (unsigned *)cv.take((size_t)ntx_max * nty_max * 9 * kQueueWords * sizeof(unsigned))
+                        : nullptr;
   ImageDesc *d_desc = (ImageDesc *)cv.take((size_t)nst * sizeof(ImageDesc));
   DevStats st;
   DevMerge mg;
@@ -167,7 +170,7 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   std::memset(&mg, 0, sizeof mg);
   const size_t lbytes = label_arrays_bytes(M);
   void *lblock = cv.take(lbytes);
-  bool ok = ctl && lab[0] && lab[1] && trec && d_desc && lblock;
+  bool ok = ctl && lab[0] && lab[1] && trec && d_desc && lblock && (qbits || p->schedule != 1);
   for (int l = 0; l < nsf; l++) ok = ok && pyr[l];
   if (!ok) return RAPID_ERANGE;  // this image and parameter set need more than the fixed array
   carve_label_arrays(lblock, lbytes, M, &st, &mg);
@@ -259,6 +262,8 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   a.hi_den = p->hi_den;
   a.max_sweeps = p->max_sweeps;
   a.trec = trec;
+  a.frontier = p->schedule == 1;
+  a.qbits = qbits;
   a.verify_filter = p->verify_filter;
   a.skip_tiles = p->skip_tiles;
   int launches = 0;

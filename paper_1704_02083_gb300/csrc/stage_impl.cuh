@@ -53,6 +53,7 @@ constexpr int kTileW = RAPID_TILE_W, kTileH = RAPID_TILE_H;
 constexpr int kPhaseMax = ((kTileW + 2) / 3) * ((kTileH + 2) / 3);
 constexpr int kReqWords = (kPhaseMax + 31) / 32;
 static_assert(4 + kTileLabels + kReqWords <= kRecInts, "the tile record holds the request words");
+static_assert(kReqWords <= kQueueWords, "the frontier queue holds a tile's class lattice");
 
 static constexpr int kThreads = 1024;
 static_assert(kThreads == 1024, "stage_block_threads() in k_stage.cu returns 1024");
@@ -240,11 +241,7 @@ __device__ __forceinline__ void merge_targets(const StageArgs &a, const ImageDes
     if (threadIdx.x < kMergeSet) nset[threadIdx.x] = -1;
     __syncthreads();
     if (s_hit) {
-      if (threadIdx.x == 0) {  // no target: the request is finished here
-        mg.target[al] = -1;
-        mg.req_flag[al] = 0;
-        mg.req_min[al] = INT_MAX;
-      }
+      if (threadIdx.x == 0) mg.target[al] = -1;  // no target: the request is finished here
       __syncthreads();
       continue;
     }
@@ -331,12 +328,7 @@ __device__ __forceinline__ void merge_targets(const StageArgs &a, const ImageDes
     if (threadIdx.x == 0) {
       const int tgt = sn[0] == INT_MAX ? -1 : sn[0];
       mg.target[al] = tgt;
-      if (tgt >= 0) {  // goes on to the acceptance walk
-        mg.found[atomicAdd(mg.found_count + (g & 1), 1)] = al;
-      } else {  // no target: the request is finished here
-        mg.req_flag[al] = 0;
-        mg.req_min[al] = INT_MAX;
-      }
+      if (tgt >= 0) mg.found[atomicAdd(mg.found_count + (g & 1), 1)] = al;  // to the acceptance walk
       if (tgt < 0) {  // remember the failure with its neighbour set
         int n = 0;
         while (!s_over && n < kMergeSet && nset[n] >= 0) n++;
@@ -370,7 +362,7 @@ __device__ int merge_walk_small(const StageArgs &a, int nf, int2 *s_acc) {
   for (int j = threadIdx.x; j < nf; j += blockDim.x) {
     const int al = mg.found[j];
     s_lab[j] = al;
-    s_key[j] = mg.req_min[al];
+    s_key[j] = req_block(mg.req_min[al]);
     s_tgt[j] = mg.target[al];
   }
   __syncthreads();
@@ -404,7 +396,7 @@ __device__ int merge_walk_small(const StageArgs &a, int nf, int2 *s_acc) {
 __device__ void merge_walk_big(const StageArgs &a, int nf) {
   const DevMerge &mg = a.mg;
   for (int j = threadIdx.x; j < nf; j += blockDim.x) {
-    const int key = mg.req_min[mg.found[j]];
+    const unsigned long long key = mg.req_min[mg.found[j]];
     int rank = 0;
     for (int i = 0; i < nf; i++) rank += mg.req_min[mg.found[i]] < key;
     mg.order[rank] = mg.found[j];
@@ -429,10 +421,12 @@ __device__ void merge_walk_big(const StageArgs &a, int nf) {
   }
 }
 
-// Apply accepted merges (list in shared or global memory) and finish every found request.
+// Apply accepted merges (list in shared or global memory).  The request state needs no
+// clearing: its keys and flags carry the phase number, so another CTA may still read them
+// for its own walk while this one applies.
 template <bool kBatch>
 __device__ __forceinline__ void merge_apply(const StageArgs &a, const ImageDesc *imgs, const int *label0,
-                                            const int2 *acc, int nacc, int nf, int g, int slot) {
+                                            const int2 *acc, int nacc, int g, int slot) {
   const DevStats &s = a.st;
   const DevMerge &mg = a.mg;
   for (int j = blockIdx.x; j < nacc; j += gridDim.x) {
@@ -461,6 +455,10 @@ __device__ __forceinline__ void merge_apply(const StageArgs &a, const ImageDesc 
       s.bbox[n] = bn;
       atomic_add_i64(&a.ctl.cnt[(long long)ii * kCntStride + CNT_MERGES], 1);
       atomicAdd(&a.ctl.changes[3 * ii + slot], 1ull);
+      if (a.frontier) {  // the 4-neighbours of the request's first block join the queue
+        const long long blk = (long long)req_block(mg.req_min[al]) - im.blk0;
+        queue_push_neighbours(a, im, (int)(blk % im.nbx), (int)(blk / im.nbx));
+      }
     }
     const int bx0 = ba.x / a.side, bx1 = ba.z / a.side, by0 = ba.y / a.side, by1 = ba.w / a.side;
     const int bw = bx1 - bx0 + 1;
@@ -469,12 +467,6 @@ __device__ __forceinline__ void merge_apply(const StageArgs &a, const ImageDesc 
       const long long idx = (long long)(by0 + (int)(t / bw)) * im.nbx + bx0 + (int)(t % bw);
       if (im.lab[idx] == al) im.lab[idx] = n;
     }
-  }
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += gridDim.x * blockDim.x) {
-    const int al = mg.found[j];
-    mg.req_flag[al] = 0;
-    mg.req_min[al] = INT_MAX;
-    mg.target[al] = -1;
   }
 }
 
@@ -522,10 +514,14 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
     set_means(a.st, k);
     a.st.chg[k] = 0;
     a.mg.cache_stamp[k] = 0;
+    a.mg.req_flag[k] = 0;  // phase numbers restart at 1 in every launch
+    a.mg.req_min[k] = ~0ull;
     a.st.adj[k] = 0;
   }
   const long long nrec = (long long)a.ntiles * 9;
   for (long long i = gtid; i < nrec; i += gstride) a.trec[i * kRecInts] = 0;
+  if (a.frontier)  // frontier schedule: every block is queued when the stage starts
+    for (long long i = gtid; i < nrec * kQueueWords; i += gstride) a.qbits[i] = ~0u;
   if (!grid_sync(a.ctl, epoch)) return;
   Timer tm(a.ctl.prof);
   int g = 0;
@@ -558,11 +554,11 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
         if (nf > 0) {
           if (nf <= kAcceptSmem) {
             const int nacc = merge_walk_small(a, nf, s_acc);
-            merge_apply<kBatch>(a, s_img, s_label0, s_acc, nacc, nf, g, slot);
+            merge_apply<kBatch>(a, s_img, s_label0, s_acc, nacc, g, slot);
           } else {
             if (blockIdx.x == 0) merge_walk_big(a, nf);
             if (!grid_sync(a.ctl, epoch)) return;
-            merge_apply<kBatch>(a, s_img, s_label0, a.mg.acc, ld_volatile_i32(a.mg.acc_count), nf, g, slot);
+            merge_apply<kBatch>(a, s_img, s_label0, a.mg.acc, ld_volatile_i32(a.mg.acc_count), g, slot);
           }
           if (!grid_sync(a.ctl, epoch)) return;
         }

@@ -223,6 +223,10 @@ WORKLOADS = {
                             params=dict(num_levels=3, ratio_C=4, init_block=32, final_grain=1,
                                         K=4096, size_mode=2, predict=1, reuse=1)),
 }
+# The same images refined with the frontier schedule (schedule 1: the boundary queue of
+# Sec. 2.1 as one flag per block, popped by the phases and refilled around every move).
+for _name in list(WORKLOADS):
+    WORKLOADS[_name + "_frontier"] = dict(WORKLOADS[_name], params=dict(WORKLOADS[_name]["params"], schedule=1))
 
 
 # Batches of uneven tiles (the adaptive data partitioning of whole slides, Sec. 3.3): tile

@@ -152,7 +152,8 @@ def _sha(a):
     return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
 
 
-@pytest.mark.parametrize("name", ["he321x481_k200", "he4096_k4096_l3"])
+@pytest.mark.parametrize("name", ["he321x481_k200", "he4096_k4096_l3", "he321x481_k200_frontier",
+                                  "he4096_k4096_l3_frontier"])
 def test_full_size_against_golden(name):
     """Full-size workloads in the bench's launch configuration against the oracle's stored
     output (tests/golden, written by make_golden.py from the oracle alone)."""

@@ -48,12 +48,13 @@ def _static(torch, pkg, rgb, params, fill):
 CASES = [
     ("he321x481_k200", synth.WORKLOADS["he321x481_k200"]["params"]),
     ("he384x512_l3", dict(num_levels=3, ratio_C=4, init_block=32, K=192, predict=1, size_mode=2)),
+    ("he321x481_k200_frontier", synth.WORKLOADS["he321x481_k200_frontier"]["params"]),
 ]
 
 
 def test_static_entry_matches_allocating_path_twice_in_a_row(env):
     torch, pkg = env
-    for (name, params), fill in zip(CASES, (-7, 123)):
+    for (name, params), fill in zip(CASES, (-7, 123, 5)):
         if name in synth.WORKLOADS:
             rgb = synth.workload_image(name).rgb
         else:
