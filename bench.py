@@ -406,6 +406,23 @@ def run_rapid(args, rank, world, local):
         scorer["quality"] = {k: round(v, 5) for k, v in q.items()}
         scorer["evaluated_blocks"] = int(sum(ctx.counters_array(i)[:, 4].sum() for i in range(n)))
 
+    sched_quality = None
+    if params.get("schedule", 0) == 1 and n == 1 and rank == 0:  # judged by the sweep schedule (untimed)
+        from paper_1704_02083_gb300 import quality, synth
+        gt = synth.workload_image(args.workload).regions
+        sw = pkg.Context(stream=stream, **dict(params, schedule=0))
+        sw.set_images(dev_imgs, Ks)
+        sw.run()
+        a, b = sw.image_labels(0), ctx.image_labels(0)
+        sched_quality = {"br_sweeps": quality.boundary_recall(a, gt), "br_frontier": quality.boundary_recall(b, gt),
+                         "ue_sweeps": quality.undersegmentation_error(a, gt),
+                         "ue_frontier": quality.undersegmentation_error(b, gt),
+                         "disagreement": float(quality.disagreement(a, b)),
+                         "evaluated_sweeps": int(sw.counters_array(0)[:, 4].sum()),
+                         "evaluated_frontier": int(ctx.counters_array(0)[:, 4].sum())}
+        sched_quality = {k: (round(v, 5) if isinstance(v, float) else v) for k, v in sched_quality.items()}
+        sw.close()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rgb_s, params_s, desc = cpu_sample(args.workload)
@@ -435,6 +452,7 @@ def run_rapid(args, rank, world, local):
                "cuda_graph": not args.no_graph,
                "path": "plain" if scorer is None else "learned pruning", "scorer": scorer, "parity": parity,
                "schedule": "frontier queue" if params.get("schedule", 0) == 1 else "sweeps",
+               "schedule_quality": sched_quality,
                "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
                "parallelism": f"replicas x{world}"}
         if n == 1:

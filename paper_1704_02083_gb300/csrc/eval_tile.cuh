@@ -159,12 +159,11 @@ __device__ __forceinline__ int decide(const StageArgs &a, const ImageDesc &im, c
 // passed the tests and, when block_skip holds (the tile was scanned before in this phase
 // class and its label set is complete), its label or a neighbour label changed since, or
 // it requested a merge then.  Otherwise it decides as at the previous scan: no move.
-__device__ __forceinline__ bool block_needs_decision(const StageArgs &a, const WarpTile &W, int c, int j,
-                                                     bool block_skip, const unsigned char *mask, long long blk,
-                                                     Local &lc) {
-  const int *win = W.win;
-  const int lbl = win[c];
-  const int nN = win[c - kWinW], nW = win[c - 1], nE = win[c + 1], nS = win[c + kWinW];
+// The tests of one block from its label, its 4-neighbours (N, W, E, S) and its diagonal
+// neighbours (NW, NE, SE, SW); -1 outside the grid.  Counts eligible and evaluated blocks.
+__device__ __forceinline__ bool block_tests(const StageArgs &a, int lbl, int nN, int nW, int nE, int nS, int nNW,
+                                            int nNE, int nSE, int nSW, const unsigned char *mask, long long blk,
+                                            Local &lc) {
   const bool boundary = (nN >= 0 && nN != lbl) || (nW >= 0 && nW != lbl) || (nE >= 0 && nE != lbl) ||
                         (nS >= 0 && nS != lbl);
   if (!boundary) return false;
@@ -182,12 +181,23 @@ __device__ __forceinline__ bool block_needs_decision(const StageArgs &a, const W
   lc.elig++;
   // pruned sweeps: the learned scorer decides which eligible blocks get the exact tests
   if (mask && !mask[blk]) return false;
-  const int nNW = win[c - kWinW - 1], nNE = win[c - kWinW + 1], nSE = win[c + kWinW + 1], nSW = win[c + kWinW - 1];
   const unsigned m = (unsigned)(nNW == lbl) | ((unsigned)(nN == lbl) << 1) | ((unsigned)(nNE == lbl) << 2) |
                      ((unsigned)(nE == lbl) << 3) | ((unsigned)(nSE == lbl) << 4) | ((unsigned)(nS == lbl) << 5) |
                      ((unsigned)(nSW == lbl) << 6) | ((unsigned)(nW == lbl) << 7);
   if (!simple_mask(m)) return false;
   lc.eval++;
+  return true;
+}
+
+__device__ __forceinline__ bool block_needs_decision(const StageArgs &a, const WarpTile &W, int c, int j,
+                                                     bool block_skip, const unsigned char *mask, long long blk,
+                                                     Local &lc) {
+  const int *win = W.win;
+  const int lbl = win[c];
+  const int nN = win[c - kWinW], nW = win[c - 1], nE = win[c + 1], nS = win[c + kWinW];
+  if (!block_tests(a, lbl, nN, nW, nE, nS, win[c - kWinW - 1], win[c - kWinW + 1], win[c + kWinW + 1],
+                   win[c + kWinW - 1], mask, blk, lc))
+    return false;
   if (block_skip && !((W.prevreq[j >> 5] >> (j & 31)) & 1u) && !win_label_changed(W, lbl) &&
       (nN < 0 || !win_label_changed(W, nN)) && (nW < 0 || !win_label_changed(W, nW)) &&
       (nE < 0 || !win_label_changed(W, nE)) && (nS < 0 || !win_label_changed(W, nS)))
@@ -198,15 +208,29 @@ __device__ __forceinline__ bool block_needs_decision(const StageArgs &a, const W
 // Frontier schedule: queue block (gx, gy) of image im (no-op outside the block grid).  Its
 // tile, phase class and index j in the class lattice of the tile are those eval_phase
 // enumerates: the class lattice of a tile starts at (lx % 3, ly % 3).
-__device__ __forceinline__ void queue_push(const StageArgs &a, const ImageDesc &im, int gx, int gy) {
-  if (gx < 0 || gy < 0 || gx >= im.nbx || gy >= im.nby) return;
+// The queue word of block (gx, gy) (inside the grid) and its bit.
+__device__ __forceinline__ unsigned *queue_word(const StageArgs &a, const ImageDesc &im, int gx, int gy,
+                                                unsigned *bit) {
   const int tx = gx / kTileW, ty = gy / kTileH;
   const int lx = gx - tx * kTileW, ly = gy - ty * kTileH;
   const int tw = min(kTileW, im.nbx - tx * kTileW);
   const int nx = (tw - lx % 3 + 2) / 3;
   const int j = (ly / 3) * nx + lx / 3;
   const long long t = (long long)im.tile0 + (long long)ty * im.ntx + tx;
-  atomicOr(&a.qbits[(t * 9 + (gy % 3) * 3 + gx % 3) * kQueueWords + (j >> 5)], 1u << (j & 31));
+  *bit = 1u << (j & 31);
+  return a.qbits + (t * 9 + (gy % 3) * 3 + gx % 3) * kQueueWords + (j >> 5);
+}
+
+// A block that was not queued also goes on its class's worklist (global block index), from
+// which sparse phases take their blocks.  Each queued block is listed at most once.
+__device__ __forceinline__ void queue_push(const StageArgs &a, const ImageDesc &im, int gx, int gy) {
+  if (gx < 0 || gy < 0 || gx >= im.nbx || gy >= im.nby) return;
+  unsigned bit;
+  unsigned *w = queue_word(a, im, gx, gy, &bit);
+  if (atomicOr(w, bit) & bit) return;
+  const int cls = (gy % 3) * 3 + gx % 3;
+  const int slot = atomicAdd(a.wl_count + cls, 1);
+  a.wl[(long long)cls * a.wl_cap + slot] = im.blk0 + gy * im.nbx + gx;
 }
 
 __device__ __forceinline__ void queue_push_neighbours(const StageArgs &a, const ImageDesc &im, int bx, int by) {
@@ -218,34 +242,32 @@ __device__ __forceinline__ void queue_push_neighbours(const StageArgs &a, const 
 
 // Pass 2 (one compacted block per lane): block sums, the decision (Eq. operation), the size
 // term (Sec. 3.1) and the move.
-__device__ __forceinline__ void decide_block(const StageArgs &a, const ImageDesc &im, WarpTile &W, int c, int j, int bx,
-                                             int by, int g, Local &lc) {
-  const int *win = W.win;
+// Returns true when the block raised a merge request instead of moving.
+__device__ __forceinline__ bool decide_block_at(const StageArgs &a, const ImageDesc &im, int lbl0, int nN, int nW,
+                                                int nE, int nS, int bx, int by, int g, Local &lc) {
   const DevStats &s = a.st;
   BlockIn in;
-  in.lbl = win[c];
-  in.nb[0] = win[c - kWinW];
-  in.nb[1] = win[c - 1];
-  in.nb[2] = win[c + 1];
-  in.nb[3] = win[c + kWinW];
+  in.lbl = lbl0;
+  in.nb[0] = nN;
+  in.nb[1] = nW;
+  in.nb[2] = nE;
+  in.nb[3] = nS;
   in.bs = block_sums(a, im, bx, by);
   in.x0 = bx * a.side;
   in.y0 = by * a.side;
   const int lbl = in.lbl;
   const int k = decide(a, im, in, lc);
-  if (k < 0) return;
+  if (k < 0) return false;
   const long long idx = (long long)by * im.nbx + bx;
   if (a.size_mode != 0 && (long long)a.lo_den * (s.mN[lbl] - in.bs.w) < (long long)a.lo_num * s.init[lbl]) {
-    if (a.size_mode == 2) {
-      lc.req++;
-      atomicOr(&W.req[j >> 5], 1u << (j & 31));
-      atomicMin(&a.mg.req_min[lbl], req_key(g, im.blk0 + idx));  // global block order
-      if (atomicExch(&a.mg.req_flag[lbl], g) != g) {
-        const int slot = atomicAdd(a.mg.req_count + (g & 1), 1);
-        a.mg.req_list[slot] = lbl;
-      }
+    if (a.size_mode != 2) return false;
+    lc.req++;
+    atomicMin(&a.mg.req_min[lbl], req_key(g, im.blk0 + idx));  // global block order
+    if (atomicExch(&a.mg.req_flag[lbl], g) != g) {
+      const int slot = atomicAdd(a.mg.req_count + (g & 1), 1);
+      a.mg.req_list[slot] = lbl;
     }
-    return;
+    return true;
   }
   // Move: relabel in place, add the exact sums to S (decisions of this phase read only the
   // snapshot means and counts, never S).
@@ -277,6 +299,15 @@ __device__ __forceinline__ void decide_block(const StageArgs &a, const ImageDesc
   atomicMax(&s.bbox[k].w, in.y0 + bs.bh - 1);
   if (a.frontier) queue_push_neighbours(a, im, bx, by);  // (other phase classes only)
   lc.moves++;
+  return false;
+}
+
+// Pass 2 of the tile path: the block at window index c (phase-class index j).
+__device__ __forceinline__ void decide_block(const StageArgs &a, const ImageDesc &im, WarpTile &W, int c, int j, int bx,
+                                             int by, int g, Local &lc) {
+  const int *win = W.win;
+  if (decide_block_at(a, im, win[c], win[c - kWinW], win[c - 1], win[c + 1], win[c + kWinW], bx, by, g, lc))
+    atomicOr(&W.req[j >> 5], 1u << (j & 31));
 }
 
 __device__ inline int warp_sum(int v) {
@@ -482,4 +513,74 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
     __syncwarp();
   }
   flush_counts(a, cur, slot, lc, scanned, skipped);
+}
+
+// ---------------------------------------------------------------- sparse frontier phase
+// Frontier schedule, phase class `phase` with nq listed blocks: one thread per listed block
+// (32 consecutive entries per warp, warps spread over the CTAs first), no tile walk.  The
+// listed blocks are exactly the queued blocks of the class; each leaves the queue here.
+// Counts go through the CTA's per-image shared counters s_cnt[image * 6 + ...].
+template <bool kBatch>
+__device__ __forceinline__ void eval_queue(const StageArgs &a, const ImageDesc *imgs, const unsigned char *active,
+                                           int *s_cnt, int phase, int g, int slot, int nq) {
+  const int nimg = kBatch ? a.nimg : 1;
+  for (int i = threadIdx.x; i < nimg * 6; i += blockDim.x) s_cnt[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int *list = a.wl + (long long)phase * a.wl_cap;
+  for (long long base = (long long)(warp * gridDim.x + blockIdx.x) * 32; base < nq; base += (long long)nwarps * 32) {
+    const long long e = base + lane;
+    if (e >= nq) continue;
+    const int gb = list[e];
+    int ii = 0;
+    if (kBatch) {
+      int lo = 0, hi = nimg - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (imgs[mid].blk0 <= gb) lo = mid;
+        else hi = mid - 1;
+      }
+      ii = lo;
+    }
+    if (!active[ii]) continue;
+    const ImageDesc &im = kBatch ? imgs[ii] : a.img0;
+    const int idx = gb - im.blk0;
+    const int bx = idx % im.nbx, by = idx / im.nbx;
+    unsigned bit;
+    unsigned *w = queue_word(a, im, bx, by, &bit);
+    atomicAnd(w, ~bit);  // off the queue
+    const int *lab = im.lab;
+    const int W = im.nbx, H = im.nby;
+    const bool n_ok = by > 0, s_ok = by + 1 < H, w_ok = bx > 0, e_ok = bx + 1 < W;
+    const int lbl = lab[idx];
+    const int nN = n_ok ? lab[idx - W] : -1, nS = s_ok ? lab[idx + W] : -1;
+    const int nW = w_ok ? lab[idx - 1] : -1, nE = e_ok ? lab[idx + 1] : -1;
+    const int nNW = (n_ok && w_ok) ? lab[idx - W - 1] : -1, nNE = (n_ok && e_ok) ? lab[idx - W + 1] : -1;
+    const int nSW = (s_ok && w_ok) ? lab[idx + W - 1] : -1, nSE = (s_ok && e_ok) ? lab[idx + W + 1] : -1;
+    Local lc = {0, 0, 0, 0, 0, 0};
+    if (block_tests(a, lbl, nN, nW, nE, nS, nNW, nNE, nSE, nSW, nullptr, 0, lc))
+      decide_block_at(a, im, lbl, nN, nW, nE, nS, bx, by, g, lc);
+    int *c = s_cnt + ii * 6;
+    if (lc.elig) atomicAdd(c + 0, lc.elig);
+    if (lc.eval) atomicAdd(c + 1, lc.eval);
+    if (lc.moves) atomicAdd(c + 2, lc.moves);
+    if (lc.req) atomicAdd(c + 3, lc.req);
+    if (lc.fallback) atomicAdd(c + 4, lc.fallback);
+    if (lc.mismatch) atomicAdd(c + 5, lc.mismatch);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nimg; i += blockDim.x) {
+    const int *c = s_cnt + i * 6;
+    long long *cnt = a.ctl.cnt + (long long)i * kCntStride;
+    if (c[0]) atomic_add_i64(&cnt[CNT_ELIG], c[0]);
+    if (c[1]) atomic_add_i64(&cnt[CNT_EVAL], c[1]);
+    if (c[2]) {
+      atomic_add_i64(&cnt[CNT_MOVES], c[2]);
+      atomicAdd(&a.ctl.changes[3 * i + slot], (unsigned long long)c[2]);
+    }
+    if (c[3]) atomic_add_i64(&cnt[CNT_REQ], c[3]);
+    if (c[4]) atomic_add_i64(&cnt[CNT_FALLBACK], c[4]);
+    if (c[5]) atomic_add_i64(&cnt[CNT_MISMATCH], c[5]);
+  }
 }

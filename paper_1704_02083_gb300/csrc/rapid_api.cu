@@ -75,6 +75,9 @@ struct rapid_ctx {
   size_t trec_cap;
   unsigned *d_qbits;  // frontier queue (schedule 1), sized like the tile records
   size_t qbits_cap;
+  int *d_wl;          // frontier worklists (9 * wl_cap) and their 9 counts
+  size_t wl_bytes_cap;
+  int wl_cap;
   // per (stage, image) descriptors
   ImageDesc *h_desc;  // [nstages * nimg]
   ImageDesc *d_desc;
@@ -229,9 +232,8 @@ extern "C" rapid_status rapid_create(const rapid_params *p, void *cuda_stream, r
     return RAPID_ENOMEM;
   }
   char *b = (char *)ctx->d_ctl_block;
-  ctx->ctl.bar = (unsigned *)(b + 0);
+  ctx->ctl.bar = (unsigned *)(b + ctx->cl.bar);
   ctx->ctl.err = (int *)(b + 8);
-  ctx->ctl.gen = (unsigned *)(b + ctx->cl.gen);
   ctx->mg.req_count = (int *)(b + 16);    // [2], by phase parity
   ctx->mg.found_count = (int *)(b + 24);  // [2], by phase parity
   ctx->mg.acc_count = (int *)(b + 32);
@@ -280,6 +282,9 @@ static void free_image_buffers(rapid_ctx *ctx) {
   cudaFree(ctx->d_qbits);
   ctx->d_qbits = nullptr;
   ctx->qbits_cap = 0;
+  cudaFree(ctx->d_wl);
+  ctx->d_wl = nullptr;
+  ctx->wl_bytes_cap = 0;
   cudaFree(ctx->d_desc);
   ctx->d_desc = nullptr;
   ctx->desc_cap = 0;
@@ -463,7 +468,7 @@ extern "C" rapid_status rapid_set_images(rapid_ctx *ctx, int32_t n, const uint8_
   // per-image layout (image copy, sum levels, label maps), seed grid and label range
   const int s0 = ctx->st_side[0], sl = ctx->st_side[ctx->nstages - 1];
   size_t img_bytes = 0, pyr_n[kMaxSumLevels] = {0}, lab_n = 0;
-  long long tiles_last = 0, M_total = 0, max_M = 0, npx_max = 0;
+  long long tiles_last = 0, M_total = 0, max_M = 0, npx_max = 0, class_blocks = 0;
   for (int i = 0; i < n; i++) {
     ImgHost &h = ctx->im[i];
     h.H = H[i];
@@ -484,6 +489,7 @@ extern "C" rapid_status rapid_set_images(rapid_ctx *ctx, int32_t n, const uint8_
       most = std::max<long long>(most, (long long)((lnbx + kShapes[sh].w - 1) / kShapes[sh].w) *
                                            ((lnby + kShapes[sh].h - 1) / kShapes[sh].h));
     tiles_last += most;
+    class_blocks += (long long)((lnbx + 2) / 3) * ((lnby + 2) / 3);  // blocks of one phase class, at most
     // seed grid gx x gy (same rounding as the stated formula) on the first stage's blocks
     const int nbx0 = ceil_div(h.W, s0), nby0 = ceil_div(h.H, s0);
     int gx = (int)std::floor(std::sqrt((double)h.K * (double)h.W / (double)h.H) + 0.5);
@@ -512,9 +518,12 @@ extern "C" rapid_status rapid_set_images(rapid_ctx *ctx, int32_t n, const uint8_
   for (int b = 0; b < 2; b++)
     if (!grow(&ctx->d_lab[b], &ctx->lab_cap[b], lab_n * sizeof(int))) return RAPID_ENOMEM;
   if (!grow(&ctx->d_trec, &ctx->trec_cap, (size_t)tiles_last * 9 * kRecInts * sizeof(int))) return RAPID_ENOMEM;
-  if (ctx->p.schedule == 1 &&
-      !grow(&ctx->d_qbits, &ctx->qbits_cap, (size_t)tiles_last * 9 * kQueueWords * sizeof(unsigned)))
-    return RAPID_ENOMEM;
+  if (ctx->p.schedule == 1) {
+    if (!grow(&ctx->d_qbits, &ctx->qbits_cap, (size_t)tiles_last * 9 * kQueueWords * sizeof(unsigned)))
+      return RAPID_ENOMEM;
+    if (!grow(&ctx->d_wl, &ctx->wl_bytes_cap, ((size_t)class_blocks * 9 + 16) * sizeof(int))) return RAPID_ENOMEM;
+    ctx->wl_cap = (int)class_blocks;
+  }
   if (!grow(&ctx->d_full, &ctx->full_cap, (size_t)npx_max * sizeof(int))) return RAPID_ENOMEM;
   if (!grow(&ctx->d_pack, &ctx->pack_cap, (size_t)max_M * sizeof(rapid_sp_stats))) return RAPID_ENOMEM;
   rs = ensure_label_arrays(ctx, ctx->M_total);
@@ -578,6 +587,9 @@ static StageArgs stage_args(rapid_ctx *ctx, int s) {
   a.prune = ctx->scorer_on;
   a.frontier = ctx->p.schedule == 1;
   a.qbits = ctx->d_qbits;
+  a.wl = ctx->d_wl;
+  a.wl_count = ctx->d_wl ? ctx->d_wl + (size_t)ctx->wl_cap * 9 : nullptr;
+  a.wl_cap = ctx->wl_cap;
   return a;
 }
 
@@ -649,8 +661,7 @@ extern "C" rapid_status rapid_refine_stage(rapid_ctx *ctx, int32_t *sweeps_out, 
   if (ctx->sticky != RAPID_OK) return ctx->sticky;
   if (ctx->cur < 0) return RAPID_ESTATE;
   const int i = ctx->cur;
-  // fresh barrier words; merge stamps, request / found counts and sweep-change slots
-  CK(cudaMemsetAsync(ctx->ctl.bar, 0, 8, ctx->stream));
+  // fresh barrier counter, merge stamps, request / found counts and sweep-change slots
   CK(cudaMemsetAsync((char *)ctx->d_ctl_block + 16, 0, ctx->cl.reset_end - 16, ctx->stream));
   StageArgs a = stage_args(ctx, i);
   // events around the launch (inside a captured graph as event-record nodes)

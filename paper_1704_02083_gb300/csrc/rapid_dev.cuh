@@ -98,8 +98,7 @@ constexpr int kMaxBatch = 64;
 constexpr int kQueueWords = 5;
 
 struct DevCtl {
-  unsigned int *bar;             // [0] arrivals (monotone within a launch)
-  unsigned int *gen;             // barrier generation opened by the last arrival (own line)
+  unsigned int *bar;             // grid-barrier arrivals (monotone within a launch; own line)
   int *err;                      // first device error (0 = none)
   long long spin_ns;             // give-up time of one barrier wait
   unsigned long long *changes;   // [nimg][3] moves + merges of the sweep per image, rotating slots
@@ -108,16 +107,16 @@ struct DevCtl {
   long long *prof;               // this stage's section times [PROF_N] in ns, or null
 };
 
-// Control block of a context: barrier counter (0), error word (8), merge counts (16..36),
-// barrier generation (128, a line of its own), per-image merge stamps and sweep changes,
-// per-(image, stage) counters, per-stage section times.  Every launch clears [0, 8) and
-// [16, reset_end); the error word persists.
+// Control block of a context: error word (8), merge counts (16..36), barrier counter (128,
+// a line of its own: every CTA polls it), per-image merge stamps and sweep changes,
+// per-(image, stage) counters, per-stage section times.  Every launch clears [16,
+// reset_end), which holds the barrier counter; the error word persists.
 struct CtlLayout {
-  size_t gen, last_merge, changes, cnt, prof, reset_end, total;
+  size_t bar, last_merge, changes, cnt, prof, reset_end, total;
 };
 inline CtlLayout ctl_layout(int nimg) {
   CtlLayout c;
-  c.gen = 128;
+  c.bar = 128;
   c.last_merge = 256;
   c.changes = (c.last_merge + 4 * (size_t)nimg + 7) / 8 * 8;
   c.reset_end = c.changes + 24 * (size_t)nimg;
@@ -171,6 +170,10 @@ struct StageArgs {
   int frontier;       // 1: a phase visits only the queued blocks of its class (schedule 1)
   unsigned *qbits;    // frontier queue [ntiles * 9 * kQueueWords]: bit j of (tile, class) =
                       // the class's j-th block of the tile (row-major over the class lattice)
+  int *wl;            // frontier worklists [9 * wl_cap]: global block indices queued since
+                      // their class's last phase (each listed once)
+  int *wl_count;      // [9] entries of each class's worklist
+  int wl_cap;         // entries one class can hold (its blocks over all images)
 };
 
 // Box-sum levels kept for block sums: the method's level factors (> 1) plus 4, 16 and 64
@@ -243,13 +246,8 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ unsigned atom_acq_rel_add_u32(unsigned *p, unsigned v) {
-  unsigned old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
-}
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(const volatile int *)p; }
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
@@ -258,25 +256,25 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
 
 // All CTAs of a co-resident (cooperative) grid meet here.  The arrival counter only grows
 // during a launch: barrier number `epoch` (counted by every CTA) is complete when it reaches
-// (epoch + 1) * gridDim.x.  Thread 0 arrives (after the CTA barrier) with an acquire-release
-// add; the CTA whose add completes the count opens the barrier by a release store of the
-// generation epoch + 1 to a flag on a line of its own, which the others poll with acquire
-// loads (the chain of adds carries every CTA's release to the last arrival, whose store
-// carries them on to the pollers).  Every wait is bounded by ctl.spin_ns (and an iteration
-// cap); on give-up the CTA records DERR_TIMEOUT and the whole grid returns false, so no
-// kernel can hang.
+// (epoch + 1) * gridDim.x.  Thread 0 arrives (after the CTA barrier) with a release add that
+// does not wait for its result, then polls the counter with acquire loads: every arrival is
+// a read-modify-write of the counter, so the final count lies in the release sequence of
+// every CTA's arrival and the acquire that reads it synchronises with all of them.  (Polling
+// the counter itself measured 1.30 us per barrier on 152 CTAs, against 1.85 us for an
+// acquire-release add whose last arriver opens a separate flag.)  Every wait is bounded by
+// ctl.spin_ns (and an iteration cap); on give-up the CTA records DERR_TIMEOUT and the whole
+// grid returns false, so no kernel can hang.
 __device__ inline bool grid_sync(const DevCtl &c, unsigned &epoch) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int good = 1;
-    const unsigned gen = epoch + 1;
-    if (atom_acq_rel_add_u32(&c.bar[0], 1u) + 1u == gen * gridDim.x) {
-      st_release_u32(c.gen, gen);
-    } else if (ld_acquire_u32(c.gen) < gen) {
+    const unsigned target = (epoch + 1) * gridDim.x;
+    red_release_add_u32(&c.bar[0], 1u);
+    if (ld_acquire_u32(c.bar) < target) {
       const unsigned long long t0 = global_ns();
       long long iters = 0;
-      while (ld_acquire_u32(c.gen) < gen) {
+      while (ld_acquire_u32(c.bar) < target) {
         if (ld_volatile_i32(c.err) != 0) {
           good = 0;
           break;
@@ -286,7 +284,6 @@ __device__ inline bool grid_sync(const DevCtl &c, unsigned &epoch) {
           good = 0;
           break;
         }
-        __nanosleep(20);
       }
     }
     ok = good;

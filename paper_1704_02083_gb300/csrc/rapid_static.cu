@@ -163,6 +163,8 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   unsigned *qbits = p->schedule == 1
                         ? (unsigned *)cv.take((size_t)ntx_max * nty_max * 9 * kQueueWords * sizeof(unsigned))
                         : nullptr;
+  const int wl_cap = ((cdiv(W, side[nst - 1]) + 2) / 3) * ((cdiv(H, side[nst - 1]) + 2) / 3);
+  int *wl = p->schedule == 1 ? (int *)cv.take(((size_t)wl_cap * 9 + 16) * sizeof(int)) : nullptr;
   ImageDesc *d_desc = (ImageDesc *)cv.take((size_t)nst * sizeof(ImageDesc));
   DevStats st;
   DevMerge mg;
@@ -170,14 +172,13 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   std::memset(&mg, 0, sizeof mg);
   const size_t lbytes = label_arrays_bytes(M);
   void *lblock = cv.take(lbytes);
-  bool ok = ctl && lab[0] && lab[1] && trec && d_desc && lblock && (qbits || p->schedule != 1);
+  bool ok = ctl && lab[0] && lab[1] && trec && d_desc && lblock && ((qbits && wl) || p->schedule != 1);
   for (int l = 0; l < nsf; l++) ok = ok && pyr[l];
   if (!ok) return RAPID_ERANGE;  // this image and parameter set need more than the fixed array
   carve_label_arrays(lblock, lbytes, M, &st, &mg);
   DevCtl c;
-  c.bar = (unsigned *)(ctl + 0);
+  c.bar = (unsigned *)(ctl + cl.bar);
   c.err = (int *)(ctl + 8);
-  c.gen = (unsigned *)(ctl + cl.gen);
   mg.req_count = (int *)(ctl + 16);
   mg.found_count = (int *)(ctl + 24);
   mg.acc_count = (int *)(ctl + 32);
@@ -264,6 +265,9 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   a.trec = trec;
   a.frontier = p->schedule == 1;
   a.qbits = qbits;
+  a.wl = wl;
+  a.wl_count = wl ? wl + (size_t)wl_cap * 9 : nullptr;
+  a.wl_cap = wl_cap;
   a.verify_filter = p->verify_filter;
   a.skip_tiles = p->skip_tiles;
   int launches = 0;
@@ -291,8 +295,7 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
       set_stage(i);
       if (!p->reuse && lev[i] != lev[i - 1]) CKS(launch_recompute(a, &desc[i], 1, stream, &launches));
     }
-    CKS(cudaMemsetAsync(c.bar, 0, 8, stream));
-    CKS(cudaMemsetAsync(ctl + 16, 0, cl.reset_end - 16, stream));  // merge stamps, counts, sweep changes
+    CKS(cudaMemsetAsync(ctl + 16, 0, cl.reset_end - 16, stream));  // barrier, merge stamps, counts, changes
     CKS(launch_stage(a, nsm * per_sm, stage_block_threads(), stream, 0));
   }
   // Outputs into the caller's buffers.

@@ -497,6 +497,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
   __shared__ int s_tile0[kImgs], s_label0[kImgs];
   __shared__ unsigned char s_active[kImgs], s_pruned[kImgs];
   __shared__ int s_valid_from[kImgs];
+  __shared__ int s_cnt[kImgs * 6];
   __shared__ int s_draw, s_any;
   unsigned epoch = 0;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
@@ -520,8 +521,10 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
   }
   const long long nrec = (long long)a.ntiles * 9;
   for (long long i = gtid; i < nrec; i += gstride) a.trec[i * kRecInts] = 0;
-  if (a.frontier)  // frontier schedule: every block is queued when the stage starts
+  if (a.frontier) {  // frontier schedule: every block is queued when the stage starts
     for (long long i = gtid; i < nrec * kQueueWords; i += gstride) a.qbits[i] = ~0u;
+    if (gtid < 9) a.wl_count[gtid] = 0;  // blocks queued from the start are not listed
+  }
   if (!grid_sync(a.ctl, epoch)) return;
   Timer tm(a.ctl.prof);
   int g = 0;
@@ -531,7 +534,13 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
       for (int i = threadIdx.x; i < a.nimg; i += blockDim.x) a.ctl.changes[3 * i + (sweep + 1) % 3] = 0;
     for (int ph = 0; ph < 9; ph++) {
       g++;
-      eval_phase<kBatch>(a, s_img, s_tile0, s_active, s_pruned, s_valid_from, wts, &s_draw, ph, g, slot);
+      // frontier schedule: after the first sweep every queued block is on its class's list;
+      // a short list is worked off one thread per block, a long one by the tile walk
+      const int nq = (a.frontier && sweep > 0) ? ld_volatile_i32(a.wl_count + ph) : INT_MAX;
+      if (nq <= 4 * (int)(gridDim.x * blockDim.x))
+        eval_queue<kBatch>(a, s_img, s_active, s_cnt, ph, g, slot, nq);
+      else
+        eval_phase<kBatch>(a, s_img, s_tile0, s_active, s_pruned, s_valid_from, wts, &s_draw, ph, g, slot);
 
       tm.lap(PROF_EVAL);
       if (!grid_sync(a.ctl, epoch)) return;
@@ -541,6 +550,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {  // slots of the next phase; last read a phase ago
         a.mg.req_count[gp ^ 1] = 0;
         a.mg.found_count[gp ^ 1] = 0;
+        if (a.frontier) a.wl_count[ph] = 0;  // the class's queued blocks all left the queue above
       }
       // the snapshot refresh and the merge-target search (which reads only S, the label
       // map and the merge state) share the barrier that ends them
