@@ -70,9 +70,11 @@ def lib():
         L.orc_lambda_pos.argtypes = [P]
         L.orc_lambda_pos.restype = C.c_double
         L.orc_simple_lut.argtypes = [P]
+        L.orc_set_classifier.argtypes = [P, P]
+        L.orc_read_features.argtypes = [P, P]
         for name in ("orc_stage_info", "orc_phase", "orc_get_grid", "orc_read_block_labels",
                      "orc_read_labels", "orc_read_stats", "orc_read_counters", "orc_read_pyramid",
-                     "orc_level_dims", "orc_simple_lut"):
+                     "orc_level_dims", "orc_simple_lut", "orc_set_classifier", "orc_read_features"):
             getattr(L, name).restype = C.c_int32
         _lib = L
     return _lib
@@ -165,6 +167,23 @@ class Oracle:
     def run_fifo(self):
         self._ok(lib().orc_run_fifo(self.h))
         return self
+
+    def set_classifier(self, theta):
+        """Eq. predict with h = theta[0] + theta[1:] . F (None: the brightness stand-in)."""
+        if theta is None:
+            self._ok(lib().orc_set_classifier(self.h, None))
+            return self
+        self._theta = np.ascontiguousarray(theta, dtype=np.float64)
+        assert self._theta.shape == (5,)
+        self._ok(lib().orc_set_classifier(self.h, self._theta.ctypes.data))
+        return self
+
+    def features(self) -> np.ndarray:
+        """M x 4 features of the last prediction: absolute brightness, comparative
+        brightness, extra-region dissimilarity, intra-region dissimilarity."""
+        out = np.zeros((self.grid()["M"], 4), np.float64)
+        self._ok(lib().orc_read_features(self.h, out.ctypes.data))
+        return out
 
     def grid(self):
         v = [C.c_int32() for _ in range(6)]

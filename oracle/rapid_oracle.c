@@ -67,6 +67,9 @@ struct orc_state {
   uint32_t visit_id;
   int64_t *queue;
   uint8_t *queued; /* schedule 1: 1 when the block is on the queue */
+  int32_t use_theta; /* 1: Eq. predict evaluates the linear classifier theta on F */
+  double theta[5];
+  double *feat;      /* M x 4 features of the last prediction */
 };
 
 enum { C_LEVEL, C_SIDE, C_SWEEPS, C_ELIG, C_EVAL, C_MOVES, C_REQ, C_MERGES };
@@ -236,7 +239,7 @@ void orc_destroy(orc_state *st) {
   free(st->req_blk);
   free(st->req_lab);
   free(st->N); free(st->R); free(st->G); free(st->B); free(st->X); free(st->Y); free(st->init);
-  free(st->y); free(st->imp);
+  free(st->y); free(st->imp); free(st->feat);
   free(st);
 }
 
@@ -302,13 +305,15 @@ int32_t orc_seed(orc_state *st) {
           (int32_t)(((int64_t)by * gy / st->nby) * gx + ((int64_t)bx * gx / st->nbx));
   size_t M = (size_t)st->M;
   free(st->N); free(st->R); free(st->G); free(st->B); free(st->X); free(st->Y); free(st->init);
-  free(st->y); free(st->imp);
+  free(st->y); free(st->imp); free(st->feat);
+  st->feat = (double *)calloc(M * 4, 8);
   st->N = (int64_t *)calloc(M, 8); st->R = (int64_t *)calloc(M, 8); st->G = (int64_t *)calloc(M, 8);
   st->B = (int64_t *)calloc(M, 8); st->X = (int64_t *)calloc(M, 8); st->Y = (int64_t *)calloc(M, 8);
   st->init = (int64_t *)calloc(M, 8);
   st->y = (int8_t *)calloc(M, 1);
   st->imp = (uint8_t *)calloc(M, 1);
-  if (!st->N || !st->R || !st->G || !st->B || !st->X || !st->Y || !st->init || !st->y || !st->imp) return 2;
+  if (!st->N || !st->R || !st->G || !st->B || !st->X || !st->Y || !st->init || !st->y || !st->imp || !st->feat)
+    return 2;
   recompute_stats(st);
   for (int32_t k = 0; k < st->M; k++) st->init[k] = st->N[k];
   /* lambda_pos scales with the initial superpixel area H*W/M (position energy per pixel
@@ -620,14 +625,83 @@ int32_t orc_refine_stage(orc_state *st) {
   return 0;
 }
 
+/* Superpixel features at the prediction point (the F in R^4 of Sec. 4.1: absolute and
+ * comparative brightness, extra- and intra-region dissimilarity), over the current block
+ * grid.  With b_k = (R_k + G_k + B_k) / (3 N_k) and c_k = (R_k, G_k, B_k) / N_k:
+ *   f1 = b_k;
+ *   f2 = b_k - the mean of b_j over the 4-adjacent block pairs (p, q), p in k, q in j != k,
+ *        each b_j taken as floor(2^16 b_j) / 2^16 (an exact integer quotient);
+ *   f3 = the mean over the same pairs of |c_k - c_j|, each truncated to a multiple of 2^-16;
+ *   f4 = sqrt(sum over k's blocks p of w_p |c_p - c_k|^2, each term truncated to a multiple
+ *        of 2^-16, divided by N_k), c_p the block's mean colour.
+ * Pairs and blocks are summed as integers, so the summation order does not matter; a
+ * label without neighbours has f2 = f3 = 0. */
+static void features(orc_state *st) {
+  int32_t M = st->M;
+  double *cr = (double *)calloc((size_t)M, 8), *cg = (double *)calloc((size_t)M, 8);
+  double *cb = (double *)calloc((size_t)M, 8);
+  int64_t *sb = (int64_t *)calloc((size_t)M, 8), *sd = (int64_t *)calloc((size_t)M, 8);
+  int64_t *si = (int64_t *)calloc((size_t)M, 8), *np = (int64_t *)calloc((size_t)M, 8);
+  for (int32_t k = 0; k < M; k++)
+    if (st->N[k] > 0) {
+      double n = (double)st->N[k];
+      cr[k] = (double)st->R[k] / n; cg[k] = (double)st->G[k] / n; cb[k] = (double)st->B[k] / n;
+    }
+  for (int32_t by = 0; by < st->nby; by++)
+    for (int32_t bx = 0; bx < st->nbx; bx++) {
+      int32_t a = label_at(st, bx, by);
+      int64_t s6[6];
+      block_sums(st, bx, by, s6);
+      double w = (double)s6[0];
+      double dr = (double)s6[1] / w - cr[a], dg = (double)s6[2] / w - cg[a], db = (double)s6[3] / w - cb[a];
+      double v = w * (dr * dr + dg * dg + db * db);
+      si[a] += (int64_t)(v * 65536.0);
+      int32_t nb[2] = {label_at(st, bx + 1, by), label_at(st, bx, by + 1)};
+      for (int j = 0; j < 2; j++) {
+        int32_t b = nb[j];
+        if (b < 0 || b == a) continue;
+        sb[a] += ((st->R[b] + st->G[b] + st->B[b]) << 16) / (3 * st->N[b]);
+        sb[b] += ((st->R[a] + st->G[a] + st->B[a]) << 16) / (3 * st->N[a]);
+        np[a]++;
+        np[b]++;
+        double er = cr[a] - cr[b], eg = cg[a] - cg[b], eb = cb[a] - cb[b];
+        int64_t dq = (int64_t)(sqrt(er * er + eg * eg + eb * eb) * 65536.0);
+        sd[a] += dq;
+        sd[b] += dq;
+      }
+    }
+  for (int32_t k = 0; k < M; k++) {
+    double *f = st->feat + 4 * (int64_t)k;
+    f[0] = f[1] = f[2] = f[3] = 0.0;
+    if (st->N[k] == 0) continue;
+    f[0] = (double)(st->R[k] + st->G[k] + st->B[k]) / (double)(3 * st->N[k]);
+    if (np[k] > 0) {
+      f[1] = f[0] - ((double)sb[k] / (double)np[k]) / 65536.0;
+      f[2] = ((double)sd[k] / (double)np[k]) / 65536.0;
+    }
+    f[3] = sqrt(((double)si[k] / 65536.0) / (double)st->N[k]);
+  }
+  free(cr); free(cg); free(cb); free(sb); free(sd); free(si); free(np);
+}
+
 /* Prediction at the start of level 2 (Algorithm RAPID; Eq. predict): y_k = 1 when
- * h(k) >= 0, else -1, with the stand-in classifier h(k) = 3 T N_k - (R_k + G_k + B_k)
+ * h(k) >= 0, else -1.  h is the linear classifier theta_0 + theta . F(k) when one is set
+ * (orc_set_classifier), else the integer stand-in h(k) = 3 T N_k - (R_k + G_k + B_k)
  * (ROI = dark superpixels).  Boundary superpixels (Eq. new_bound; "blocks located in
  * boundary superpixel"): labels 4-adjacent to a label of the other class. */
 static void predict(orc_state *st) {
+  features(st);
   for (int32_t k = 0; k < st->M; k++) {
-    int64_t h = 3 * st->p.h_T * st->N[k] - (st->R[k] + st->G[k] + st->B[k]);
-    st->y[k] = (int8_t)(h >= 0 ? 1 : -1);
+    int32_t pos;
+    if (st->use_theta) {
+      const double *f = st->feat + 4 * (int64_t)k, *t = st->theta;
+      double h = (((t[0] + t[1] * f[0]) + t[2] * f[1]) + t[3] * f[2]) + t[4] * f[3];
+      pos = h >= 0.0;
+    } else {
+      int64_t h = 3 * st->p.h_T * st->N[k] - (st->R[k] + st->G[k] + st->B[k]);
+      pos = h >= 0;
+    }
+    st->y[k] = (int8_t)(pos ? 1 : -1);
     st->imp[k] = 0;
   }
   for (int32_t by = 0; by < st->nby; by++)
@@ -638,6 +712,18 @@ static void predict(orc_state *st) {
       if (s >= 0 && s != a && st->y[s] != st->y[a]) st->imp[a] = st->imp[s] = 1;
     }
   st->imp_on = 1;
+}
+
+int32_t orc_set_classifier(orc_state *st, const double *theta5) {
+  st->use_theta = theta5 != NULL;
+  for (int i = 0; i < 5; i++) st->theta[i] = theta5 ? theta5[i] : 0.0;
+  return 0;
+}
+
+int32_t orc_read_features(const orc_state *st, double *dst4) {
+  if (st->cur < 0) return 4;
+  memcpy(dst4, st->feat, sizeof(double) * 4 * (size_t)st->M);
+  return 0;
 }
 
 /* Next stage: prediction on entering level 2, then each block splits into 2x2 blocks

@@ -74,6 +74,12 @@ int32_t orc_level_dims(const orc_state *st, int32_t level, int32_t *Wl, int32_t 
 double orc_lambda_pos(const orc_state *st);
 int32_t orc_simple_lut(uint8_t *dst256);
 int32_t orc_run_fifo(orc_state *st);
+/* Eq. predict with the linear classifier theta[0] + theta[1..4] . F over the features F of
+ * each superpixel (NULL: the integer brightness stand-in), and the features of the last
+ * prediction (M x 4: absolute brightness, comparative brightness, extra-region and
+ * intra-region dissimilarity). */
+int32_t orc_set_classifier(orc_state *st, const double *theta5);
+int32_t orc_read_features(const orc_state *st, double *dst4);
 
 #ifdef __cplusplus
 }
