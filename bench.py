@@ -49,6 +49,8 @@ def parse():
                     help="pinned launch geometry instead of autotuning: 'grid,grid,...:shape,shape,...' per stage")
     ap.add_argument("--prune", type=float, default=None,
                     help="the learned path: train the block scorer (untimed) and prune at this threshold")
+    ap.add_argument("--classifier", action="store_true",
+                    help="fit the linear classifier of Eq. predict on the superpixel features (untimed) and use it")
     return ap.parse_args()
 
 
@@ -279,6 +281,11 @@ def run_rapid(args, rank, world, local):
         from paper_1704_02083_gb300 import scorer as sc
         w_scorer, train_info = sc.collect_and_train(*sc.training_tiles())
         scorer = dict(threshold=args.prune, train=train_info)
+    classifier = None
+    if args.classifier:  # features and ground truth at the prediction point of other seeds, then the fit
+        from paper_1704_02083_gb300 import roi
+        theta, cls_info = roi.train()
+        classifier = dict(train=cls_info)
     sizes = [(int(x.shape[0]), int(x.shape[1])) for x in imgs]
     npx = sum(h * w for h, w in sizes)
     stream = torch.cuda.Stream()  # a graph needs a non-default stream
@@ -289,6 +296,8 @@ def run_rapid(args, rank, world, local):
     ctx.set_images(dev_imgs, Ks)
     if scorer is not None:
         ctx.set_scorer(w_scorer, args.prune)
+    if classifier is not None:
+        ctx.set_classifier(theta)
     if args.geometry:
         g_str, s_str = args.geometry.split(":")
         grids, shapes = [int(x) for x in g_str.split(",")], [int(x) for x in s_str.split(",")]
@@ -376,7 +385,7 @@ def run_rapid(args, rank, world, local):
     # golden hashes (written by tests/golden/make_golden.py from the oracle alone)
     parity = None
     gpath = os.path.join(ROOT, "tests", "golden", f"{args.workload}.json")
-    if n == 1 and scorer is None and os.path.exists(gpath):
+    if n == 1 and scorer is None and classifier is None and os.path.exists(gpath):
         g = json.load(open(gpath))
         st_np = ctx.image_stats(0)
         fields = ("n", "sum_r", "sum_g", "sum_b", "sum_x", "sum_y", "init_size")
@@ -405,6 +414,12 @@ def run_rapid(args, rank, world, local):
         plain.close()
         scorer["quality"] = {k: round(v, 5) for k, v in q.items()}
         scorer["evaluated_blocks"] = int(sum(ctx.counters_array(i)[:, 4].sum() for i in range(n)))
+
+    if classifier is not None and n == 1 and rank == 0:  # judged against the brightness stand-in (untimed)
+        from paper_1704_02083_gb300 import roi, synth
+        classifier["eval"] = roi.evaluate(theta, synth.workload_image(args.workload), Ks[0], dict(params),
+                                          stream=stream)
+        classifier["parity"] = "bit-exact vs the oracle in tests/test_gpu_classifier.py (features, y, runs)"
 
     sched_quality = None
     if params.get("schedule", 0) == 1 and n == 1 and rank == 0:  # judged by the sweep schedule (untimed)
@@ -453,6 +468,7 @@ def run_rapid(args, rank, world, local):
                "path": "plain" if scorer is None else "learned pruning", "scorer": scorer, "parity": parity,
                "schedule": "frontier queue" if params.get("schedule", 0) == 1 else "sweeps",
                "schedule_quality": sched_quality,
+               "classifier": classifier,
                "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
                "parallelism": f"replicas x{world}"}
         if n == 1:

@@ -239,6 +239,27 @@ rapid_status rapid_autotune(rapid_ctx *ctx, int32_t *grids_out, int32_t *shapes_
 #define RAPID_SCORER_PARAMS 3777
 #define RAPID_SCORER_FEATURES 9
 
+/* ---- Superpixel features and a linear classifier for Eq. predict ----
+ * With theta (host, 5 doubles; NULL = off, the default) the prediction at the entry to
+ * level 2 evaluates h = theta[0] + theta[1] f1 + theta[2] f2 + theta[3] f3 + theta[4] f4
+ * (binary64, left to right) over each superpixel's features on the last level-1 block grid
+ * (the F in R^4 of Sec. 4.1), and y = 1 when h >= 0; without theta it uses the brightness
+ * stand-in 3 h_T N - (R + G + B).  With b the mean brightness (R + G + B) / (3 N) and c the
+ * mean colour:
+ *   f1 absolute brightness b;
+ *   f2 comparative brightness: b minus the mean, over the superpixel's 4-adjacent block
+ *      pairs with other superpixels, of their b (each as floor(2^16 b) / 2^16);
+ *   f3 extra-region dissimilarity: the mean over those pairs of |c - c_other| (each
+ *      truncated to a multiple of 2^-16);
+ *   f4 intra-region dissimilarity: sqrt of the pixel-weighted mean over its blocks of
+ *      |c_block - c|^2 (each block's term truncated to a multiple of 2^-16).
+ * theta = (3 h_T, -3, 0, 0, 0) reproduces the stand-in exactly.  EINVAL on a non-finite
+ * theta.  rapid_read_features copies image i's features of the last prediction made with
+ * a classifier (M_i x 4 doubles, host dst; ESTATE when no classifier was set).
+ * Synchronises. */
+rapid_status rapid_set_classifier(rapid_ctx *ctx, const double *theta5);
+rapid_status rapid_read_features(rapid_ctx *ctx, int32_t i, double *dst_host);
+
 /* Pruned refinement: with weights (host, RAPID_SCORER_PARAMS floats; NULL = off) every stage
  * first scores its blocks (score = sigmoid of the net's output) and sweeps only over the
  * eligible blocks scoring >= threshold until a sweep changes nothing; then it sweeps over

@@ -105,6 +105,8 @@ def lib() -> C.CDLL:
         "rapid_set_graph": (i32, [P, i32]),
         "rapid_set_stage_grids": (i32, [P, pi32, i32]),
         "rapid_set_scorer": (i32, [P, P, C.c_float]),
+        "rapid_set_classifier": (i32, [P, P]),
+        "rapid_read_features": (i32, [P, i32, P]),
         "rapid_refine_slide": (i32, [P, P, i64, i64, i64, i32, i32, i32, P, i64, P, i64, pi64, pi32]),
         "rapid_scorer_features": (i32, [P, i32, P]),
         "rapid_scorer_scores": (i32, [P, i32, P, P]),
@@ -298,6 +300,24 @@ def rapid_set_scorer(ctx: int, weights, threshold: float):
         return
     w = _f32(weights)
     _check(lib().rapid_set_scorer(ctx, w.ctypes.data, float(threshold)), "rapid_set_scorer")
+
+
+def rapid_set_classifier(ctx: int, theta):
+    """Eq. predict with h = theta[0] + theta[1:] . F over the superpixel features (None: the
+    brightness stand-in)."""
+    if theta is None:
+        _check(lib().rapid_set_classifier(ctx, None), "rapid_set_classifier")
+        return
+    t = np.ascontiguousarray(theta, dtype=np.float64)
+    if t.shape != (5,):
+        raise ValueError("theta has 5 entries")
+    _check(lib().rapid_set_classifier(ctx, t.ctypes.data), "rapid_set_classifier")
+
+
+def rapid_read_features(ctx: int, i: int, M: int) -> np.ndarray:
+    out = np.zeros((M, 4), np.float64)
+    _check(lib().rapid_read_features(ctx, i, out.ctypes.data), "rapid_read_features")
+    return out
 
 
 def rapid_scorer_features(ctx: int, i: int, dst_dev_ptr: int):
@@ -539,6 +559,16 @@ class Context:
 
     def set_scorer(self, weights, threshold: float = 0.3):
         rapid_set_scorer(self.h, weights, threshold)
+
+    def set_classifier(self, theta):
+        """theta (5 floats) for Eq. predict over the superpixel features, or None."""
+        rapid_set_classifier(self.h, theta)
+        return self
+
+    def features(self, i: int = 0) -> np.ndarray:
+        """Image i's superpixel features of the last prediction (M x 4: absolute brightness,
+        comparative brightness, extra-region and intra-region dissimilarity)."""
+        return rapid_read_features(self.h, i, self.image_info(i)["M"])
 
     def set_logging(self, trainer):
         rapid_set_logging(self.h, trainer.h if trainer is not None else None)

@@ -167,6 +167,116 @@ __global__ void importance_kernel(const int *lab, int nbx, int nby, DevStats st)
   }
 }
 
+// ---------------------------------------------------------------- features (Sec. 4.1's F)
+// The features of a superpixel at the prediction point, with b_k = (R_k + G_k + B_k) /
+// (3 N_k) and c_k its mean colour: f1 = b_k; f2 = b_k minus the mean over k's 4-adjacent
+// block pairs (p in k, q in j != k) of b_j taken as floor(2^16 b_j) / 2^16; f3 = the mean over
+// those pairs of |c_k - c_j| truncated to 2^-16; f4 = sqrt(sum over k's blocks of w_p
+// |c_p - c_k|^2, each truncated to 2^-16, over N_k).  Every pair and block term is an
+// integer, so the atomic sums do not depend on their order, and the binary64 operations
+// are those of the definition in the order written.
+
+// Sums cleared; the mean colours go to feat[4k .. 4k + 2] for the pass over the blocks.
+__global__ void feature_init_kernel(DevStats st) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= st.M) return;
+  st.fsb[k] = st.fsd[k] = st.fsi[k] = 0;
+  st.fnp[k] = 0;
+  const long long n = st.N[k];
+  double *f = st.feat + 4ll * k;
+  if (n > 0) {
+    const double dn = __ll2double_rn(n);
+    f[0] = __ddiv_rn(__ll2double_rn(st.R[k]), dn);
+    f[1] = __ddiv_rn(__ll2double_rn(st.G[k]), dn);
+    f[2] = __ddiv_rn(__ll2double_rn(st.B[k]), dn);
+  } else {
+    f[0] = f[1] = f[2] = 0.0;
+  }
+  f[3] = 0.0;
+}
+
+__device__ __forceinline__ long long brightness_q16(const DevStats &st, int j) {
+  return ((st.R[j] + st.G[j] + st.B[j]) << 16) / (3 * st.N[j]);
+}
+
+// One thread per block of the prediction grid: its squared deviation, and its pairs with
+// the E and S neighbours.
+__global__ void feature_pass_kernel(StageArgs a, ImageDesc im, DevStats st) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)im.nbx * im.nby) return;
+  const int bx = (int)(i % im.nbx), by = (int)(i / im.nbx);
+  const int k = im.lab[i];
+  const double *ck = st.feat + 4ll * k;
+  const BlockSums bs = block_sums(a, im, bx, by);
+  const double w = __ll2double_rn(bs.w);
+  const double dr = __dsub_rn(__ddiv_rn(__ll2double_rn(bs.r), w), ck[0]);
+  const double dg = __dsub_rn(__ddiv_rn(__ll2double_rn(bs.g), w), ck[1]);
+  const double db = __dsub_rn(__ddiv_rn(__ll2double_rn(bs.b), w), ck[2]);
+  const double v = __dmul_rn(w, __dadd_rn(__dadd_rn(__dmul_rn(dr, dr), __dmul_rn(dg, dg)), __dmul_rn(db, db)));
+  atomicAdd((unsigned long long *)&st.fsi[k], (unsigned long long)__double2ll_rz(__dmul_rn(v, 65536.0)));
+  const int q[2] = {bx + 1 < im.nbx ? im.lab[i + 1] : -1, by + 1 < im.nby ? im.lab[i + im.nbx] : -1};
+  for (int t = 0; t < 2; t++) {
+    const int j = q[t];
+    if (j < 0 || j == k) continue;
+    atomicAdd((unsigned long long *)&st.fsb[k], (unsigned long long)brightness_q16(st, j));
+    atomicAdd((unsigned long long *)&st.fsb[j], (unsigned long long)brightness_q16(st, k));
+    atomicAdd(&st.fnp[k], 1);
+    atomicAdd(&st.fnp[j], 1);
+    const double *cj = st.feat + 4ll * j;
+    const double er = __dsub_rn(ck[0], cj[0]), eg = __dsub_rn(ck[1], cj[1]), eb = __dsub_rn(ck[2], cj[2]);
+    const double d = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(er, er), __dmul_rn(eg, eg)), __dmul_rn(eb, eb)));
+    const unsigned long long dq = (unsigned long long)__double2ll_rz(__dmul_rn(d, 65536.0));
+    atomicAdd((unsigned long long *)&st.fsd[k], dq);
+    atomicAdd((unsigned long long *)&st.fsd[j], dq);
+  }
+}
+
+// The features from the sums, then Eq. predict with h = t0 + t1 f1 + t2 f2 + t3 f3 + t4 f4
+// (summed left to right): y = 1 when h >= 0.
+__global__ void classify_linear_kernel(DevStats st, double t0, double t1, double t2, double t3, double t4) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= st.M) return;
+  const long long n = st.N[k];
+  double f1 = 0.0, f2 = 0.0, f3 = 0.0, f4 = 0.0;
+  if (n > 0) {
+    f1 = __ddiv_rn(__ll2double_rn(st.R[k] + st.G[k] + st.B[k]), __ll2double_rn(3 * n));
+    const int np = st.fnp[k];
+    if (np > 0) {
+      const double dnp = (double)np;
+      f2 = __dsub_rn(f1, __ddiv_rn(__ddiv_rn(__ll2double_rn(st.fsb[k]), dnp), 65536.0));
+      f3 = __ddiv_rn(__ddiv_rn(__ll2double_rn(st.fsd[k]), dnp), 65536.0);
+    }
+    f4 = __dsqrt_rn(__ddiv_rn(__ddiv_rn(__ll2double_rn(st.fsi[k]), 65536.0), __ll2double_rn(n)));
+  }
+  double *f = st.feat + 4ll * k;
+  f[0] = f1;
+  f[1] = f2;
+  f[2] = f3;
+  f[3] = f4;
+  const double h =
+      __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(t0, __dmul_rn(t1, f1)), __dmul_rn(t2, f2)), __dmul_rn(t3, f3)),
+                __dmul_rn(t4, f4));
+  st.y[k] = h >= 0.0 ? 1 : -1;
+  st.imp[k] = 0;
+}
+
+// Prediction with the linear classifier theta over the features; a: the launch arguments
+// of the stage whose block grid the prediction reads (for the block sums).
+cudaError_t launch_predict_linear(const StageArgs &a, const ImageDesc *ims, int n, const double *theta,
+                                  cudaStream_t s, int *launches) {
+  const DevStats &st = a.st;
+  feature_init_kernel<<<blocks_for(st.M, 256), 256, 0, s>>>(st);
+  for (int i = 0; i < n; i++)
+    feature_pass_kernel<<<blocks_for((long long)ims[i].nbx * ims[i].nby, 256), 256, 0, s>>>(a, ims[i], st);
+  classify_linear_kernel<<<blocks_for(st.M, 256), 256, 0, s>>>(st, theta[0], theta[1], theta[2], theta[3],
+                                                                 theta[4]);
+  for (int i = 0; i < n; i++)
+    importance_kernel<<<blocks_for((long long)ims[i].nbx * ims[i].nby, 256), 256, 0, s>>>(ims[i].lab, ims[i].nbx,
+                                                                                           ims[i].nby, st);
+  *launches += 2 + 2 * n;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_predict(const ImageDesc *ims, int n, const DevStats &st, long long hT, cudaStream_t s,
                            int *launches) {
   classify_kernel<<<blocks_for(st.M, 256), 256, 0, s>>>(st, hT);
@@ -274,6 +384,11 @@ static size_t carve_impl(char *base, size_t cap, int M, DevStats *st, DevMerge *
   st->bbox = (int4 *)take(m * 16);
   st->chg = (int *)take(m * 4);
   st->adj = (int *)take(m * 4);
+  st->fsb = (long long *)take(m * 8);
+  st->fsd = (long long *)take(m * 8);
+  st->fsi = (long long *)take(m * 8);
+  st->fnp = (int *)take(m * 4);
+  st->feat = (double *)take(m * 32);
   mg->acc = (int2 *)take(m * 8);
   mg->req_min = (unsigned long long *)take(m * 8);
   int **i32[] = {&mg->req_list, &mg->req_flag, &mg->target, &mg->order, &mg->cache_stamp, &mg->cache_n};

@@ -21,6 +21,8 @@ cudaError_t launch_recompute(const StageArgs &a, const ImageDesc *ims, int n, cu
 cudaError_t launch_split(const int *src, int snbx, int *dst, int dnbx, int dnby, cudaStream_t s);
 cudaError_t launch_predict(const ImageDesc *ims, int n, const DevStats &st, long long hT, cudaStream_t s,
                            int *launches);
+cudaError_t launch_predict_linear(const StageArgs &a, const ImageDesc *ims, int n, const double *theta,
+                                  cudaStream_t s, int *launches);
 cudaError_t launch_upsample(const int *lab, int nbx, int side, int H, int W, int label0, int *dst,
                             long long pitch_elems, cudaStream_t s);
 cudaError_t launch_pack_stats(const DevStats &st, int label0, int M, rapid_sp_stats *out, cudaStream_t s);
@@ -111,6 +113,8 @@ struct rapid_ctx {
   // learned scorer: pruning weights, per-image masks (at the label maps' offsets)
   size_t lab_total;  // ints of one label-map buffer (all images)
   int scorer_on;
+  int theta_on;       // Eq. predict with the linear classifier over the features
+  double theta[5];
   float scorer_thr;
   void *d_scorer, *d_scorer_tmp;
   ScorerDev sdev;
@@ -723,7 +727,10 @@ extern "C" rapid_status rapid_split(rapid_ctx *ctx) {
   int nl = 0;
   if (ctx->p.predict && ctx->st_level[nxt] >= 2 && prev_level < 2) {
     StageArgs a = stage_args(ctx, ctx->cur);
-    CK(launch_predict(host_desc(ctx, ctx->cur), ctx->nimg, a.st, ctx->p.h_T, ctx->stream, &nl));
+    if (ctx->theta_on)
+      CK(launch_predict_linear(a, host_desc(ctx, ctx->cur), ctx->nimg, ctx->theta, ctx->stream, &nl));
+    else
+      CK(launch_predict(host_desc(ctx, ctx->cur), ctx->nimg, a.st, ctx->p.h_T, ctx->stream, &nl));
     ctx->imp_on = 1;
   }
   const ImageDesc *src = host_desc(ctx, ctx->cur), *dst = host_desc(ctx, nxt);
@@ -888,6 +895,31 @@ extern "C" rapid_status rapid_autotune(rapid_ctx *ctx, int32_t *grids_out, int32
   ctx->profiling = saved_prof;
   ctx->graph_on = saved_graph;
   return rs;
+}
+
+// ---------------------------------------------------------------- linear classifier
+extern "C" rapid_status rapid_set_classifier(rapid_ctx *ctx, const double *theta5) {
+  if (!ctx) return RAPID_EINVAL;
+  if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  if (theta5)
+    for (int i = 0; i < 5; i++)
+      if (!std::isfinite(theta5[i])) return RAPID_EINVAL;
+  drop_graph(ctx);
+  ctx->theta_on = theta5 != nullptr;
+  for (int i = 0; i < 5; i++) ctx->theta[i] = theta5 ? theta5[i] : 0.0;
+  return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_read_features(rapid_ctx *ctx, int32_t i, double *dst_host) {
+  if (!ctx || !dst_host) return RAPID_EINVAL;
+  if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  if (!ctx->theta_on || !ctx->image_set) return RAPID_ESTATE;
+  if (i < 0 || i >= ctx->nimg) return RAPID_EINVAL;
+  const ImgHost &h = ctx->im[i];
+  CK(cudaMemcpyAsync(dst_host, ctx->st.feat + 4ll * h.label0, sizeof(double) * 4 * (size_t)h.M,
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return RAPID_OK;
 }
 
 // ---------------------------------------------------------------- learned scorer

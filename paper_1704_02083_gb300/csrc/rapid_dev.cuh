@@ -62,6 +62,12 @@ struct DevStats {
   signed char *y;
   unsigned char *imp;
   int4 *bbox;  // inclusive full-res pixel box: x0, y0, x1, y1
+  // prediction with a linear classifier: per-label integer sums over block pairs (brightness
+  // in 2^-16 units, colour distance in 2^-16 units, pair count) and over blocks (squared
+  // colour deviation in 2^-16 units), and the 4 features of the last prediction
+  long long *fsb, *fsd, *fsi;
+  int *fnp;
+  double *feat;  // [M * 4]
   int M;
 };
 

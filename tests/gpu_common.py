@@ -9,13 +9,15 @@ import oracle
 STAT_FIELDS = ("n", "sum_r", "sum_g", "sum_b", "sum_x", "sum_y", "init_size")
 
 
-def gpu_run(rgb: np.ndarray, device_input: bool = True, **params):
+def gpu_run(rgb: np.ndarray, device_input: bool = True, theta=None, **params):
     import torch
 
     import paper_1704_02083_gb300 as pkg
 
     stream = torch.cuda.current_stream()
     with pkg.Context(stream=stream, **params) as ctx:
+        if theta is not None:
+            ctx.set_classifier(theta)
         if device_input:
             ctx.set_image(torch.from_numpy(np.ascontiguousarray(rgb)).cuda())
         else:
@@ -28,9 +30,13 @@ def gpu_run(rgb: np.ndarray, device_input: bool = True, **params):
     return lab, stats, st["y"].astype(np.int8), st["important"].astype(np.uint8), cnt
 
 
-def oracle_run(rgb: np.ndarray, **params):
+def oracle_run(rgb: np.ndarray, theta=None, **params):
     p = {k: v for k, v in params.items() if k in oracle.DEFAULTS}
-    return oracle.run(rgb, **p)
+    if theta is None:
+        return oracle.run(rgb, **p)
+    o = oracle.Oracle(rgb, **p).set_classifier(theta).run()
+    s, y, imp = o.stats()
+    return o.labels(), s, y, imp, o.counters()
 
 
 def gpu_counters(rgb: np.ndarray, **params):
@@ -46,9 +52,9 @@ def gpu_counters(rgb: np.ndarray, **params):
         return [c.stage[i] for i in range(c.num_stages)], ctx.labels()
 
 
-def assert_parity(rgb, **params):
-    lab, st, y, imp, cnt = gpu_run(rgb, **params)
-    rlab, rst, ry, rimp, rcnt = oracle_run(rgb, **params)
+def assert_parity(rgb, theta=None, **params):
+    lab, st, y, imp, cnt = gpu_run(rgb, theta=theta, **params)
+    rlab, rst, ry, rimp, rcnt = oracle_run(rgb, theta=theta, **params)
     assert lab.shape == rlab.shape
     diff = np.argwhere(lab != rlab)
     assert diff.size == 0, f"{len(diff)} labels differ, first at {diff[:3].tolist()}"
