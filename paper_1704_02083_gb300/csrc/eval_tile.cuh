@@ -221,23 +221,28 @@ __device__ __forceinline__ unsigned *queue_word(const StageArgs &a, const ImageD
   return a.qbits + (t * 9 + (gy % 3) * 3 + gx % 3) * kQueueWords + (j >> 5);
 }
 
-// A block that was not queued also goes on its class's worklist (global block index), from
-// which sparse phases take their blocks.  Each queued block is listed at most once.
-__device__ __forceinline__ void queue_push(const StageArgs &a, const ImageDesc &im, int gx, int gy) {
-  if (gx < 0 || gy < 0 || gx >= im.nbx || gy >= im.nby) return;
-  unsigned bit;
-  unsigned *w = queue_word(a, im, gx, gy, &bit);
-  if (atomicOr(w, bit) & bit) return;
-  const int cls = (gy % 3) * 3 + gx % 3;
-  const int slot = atomicAdd(a.wl_count + cls, 1);
-  a.wl[(long long)cls * a.wl_cap + slot] = im.blk0 + gy * im.nbx + gx;
-}
-
+// The 4-neighbours of block (bx, by) go on the queue; those that were not queued also go on
+// their class's worklist (global block index), from which sparse phases take their blocks,
+// so each queued block is listed at most once.  The four flag updates are issued together,
+// then the list slots together.
 __device__ __forceinline__ void queue_push_neighbours(const StageArgs &a, const ImageDesc &im, int bx, int by) {
-  queue_push(a, im, bx, by - 1);
-  queue_push(a, im, bx - 1, by);
-  queue_push(a, im, bx + 1, by);
-  queue_push(a, im, bx, by + 1);
+  const int nx[4] = {bx, bx - 1, bx + 1, bx}, ny[4] = {by - 1, by, by, by + 1};
+  unsigned old[4], bit[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    old[q] = bit[q] = 0u;
+    if (nx[q] < 0 || ny[q] < 0 || nx[q] >= im.nbx || ny[q] >= im.nby) continue;
+    unsigned *w = queue_word(a, im, nx[q], ny[q], &bit[q]);
+    old[q] = atomicOr(w, bit[q]);
+  }
+  int slot[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+    slot[q] = (bit[q] && !(old[q] & bit[q])) ? atomicAdd(a.wl_count + (ny[q] % 3) * 3 + nx[q] % 3, 1) : -1;
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+    if (slot[q] >= 0)
+      a.wl[(long long)((ny[q] % 3) * 3 + nx[q] % 3) * a.wl_cap + slot[q]] = im.blk0 + ny[q] * im.nbx + nx[q];
 }
 
 // Pass 2 (one compacted block per lane): block sums, the decision (Eq. operation), the size
@@ -547,9 +552,6 @@ __device__ __forceinline__ void eval_queue(const StageArgs &a, const ImageDesc *
     const ImageDesc &im = kBatch ? imgs[ii] : a.img0;
     const int idx = gb - im.blk0;
     const int bx = idx % im.nbx, by = idx / im.nbx;
-    unsigned bit;
-    unsigned *w = queue_word(a, im, bx, by, &bit);
-    atomicAnd(w, ~bit);  // off the queue
     const int *lab = im.lab;
     const int W = im.nbx, H = im.nby;
     const bool n_ok = by > 0, s_ok = by + 1 < H, w_ok = bx > 0, e_ok = bx + 1 < W;
@@ -558,6 +560,26 @@ __device__ __forceinline__ void eval_queue(const StageArgs &a, const ImageDesc *
     const int nW = w_ok ? lab[idx - 1] : -1, nE = e_ok ? lab[idx + 1] : -1;
     const int nNW = (n_ok && w_ok) ? lab[idx - W - 1] : -1, nNE = (n_ok && e_ok) ? lab[idx - W + 1] : -1;
     const int nSW = (s_ok && w_ok) ? lab[idx + W - 1] : -1, nSE = (s_ok && e_ok) ? lab[idx + W + 1] : -1;
+    // what the tests and the decision read next, fetched into L1 at once instead of one
+    // round trip after another
+    prefetch_l1(a.st.imp + lbl);
+    prefetch_l1(a.st.mN + lbl);
+    prefetch_l1(a.st.init + lbl);
+    prefetch_l1(a.st.fhi + lbl);
+    prefetch_l1(a.st.flo + lbl);
+    prefetch_l1(a.st.fy + lbl);
+    const int nb4[4] = {nN, nW, nE, nS};
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+      if (nb4[q] >= 0 && nb4[q] != lbl) {
+        prefetch_l1(a.st.fhi + nb4[q]);
+        prefetch_l1(a.st.flo + nb4[q]);
+        prefetch_l1(a.st.fy + nb4[q]);
+      }
+    if (a.f == 1) prefetch_l1(im.img + (long long)by * a.side * im.img_pitch + 3ll * bx * a.side);
+    unsigned bit;
+    unsigned *w = queue_word(a, im, bx, by, &bit);
+    atomicAnd(w, ~bit);  // off the queue
     Local lc = {0, 0, 0, 0, 0, 0};
     if (block_tests(a, lbl, nN, nW, nE, nS, nNW, nNE, nSE, nSW, nullptr, 0, lc))
       decide_block_at(a, im, lbl, nN, nW, nE, nS, bx, by, g, lc);

@@ -256,6 +256,7 @@ __device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(const volatile int *)p; }
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
   return *(const volatile unsigned long long *)p;
 }

@@ -546,7 +546,6 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
       if (!grid_sync(a.ctl, epoch)) return;
       tm.lap(PROF_SYNC1);
       const int gp = g & 1;
-      const int rq = ld_volatile_i32(a.mg.req_count + gp);
       if (blockIdx.x == 0 && threadIdx.x == 0) {  // slots of the next phase; last read a phase ago
         a.mg.req_count[gp ^ 1] = 0;
         a.mg.found_count[gp ^ 1] = 0;
@@ -555,6 +554,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
       // the snapshot refresh and the merge-target search (which reads only S, the label
       // map and the merge state) share the barrier that ends them
       commit_phase(a, g);
+      const int rq = ld_volatile_i32(a.mg.req_count + gp);
       if (rq > 0) merge_targets<kBatch>(a, s_img, s_label0, rq, g);
       tm.lap(PROF_COMMIT);
       if (!grid_sync(a.ctl, epoch)) return;
