@@ -34,6 +34,10 @@ L2_FLUSH_BYTES = 256 << 20
 SAMPLE_SIDE = 1024  # CPU legs: a 1024 x 1024 tile of the same generator and parameters
 
 
+# evaluation-tile shapes of the stage kernel, by index (blocks per tile, threads per CTA)
+TILE_NAMES = ["32x16", "32x8", "64x16", "32x16/512t", "32x8/512t", "64x16/512t"]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -463,7 +467,7 @@ def run_rapid(args, rank, world, local):
                "final_grain": params["final_grain"], "size_mode": params["size_mode"],
                "predict": params["predict"], "reuse": params["reuse"],
                "stage_grids": grids[:nst] if grids is not None else None,
-               "stage_tiles": [f"{[32, 32, 64][k]}x{[16, 8, 16][k]}" for k in shapes[:nst]] if shapes else None,
+               "stage_tiles": [TILE_NAMES[k] for k in shapes[:nst]] if shapes else None,
                "cuda_graph": not args.no_graph,
                "path": "plain" if scorer is None else "learned pruning", "scorer": scorer, "parity": parity,
                "schedule": "frontier queue" if params.get("schedule", 0) == 1 else "sweeps",

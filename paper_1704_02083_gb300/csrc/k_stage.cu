@@ -3,20 +3,26 @@
 #include "rapid_dev.cuh"
 
 namespace rapid {
-const void *stage_kernel_ptr_s0(bool batch);
-const void *stage_kernel_ptr_s1(bool batch);
-const void *stage_kernel_ptr_s2(bool batch);
-cudaError_t launch_stage_s0(const StageArgs &a, int grid, int block, cudaStream_t s);
-cudaError_t launch_stage_s1(const StageArgs &a, int grid, int block, cudaStream_t s);
-cudaError_t launch_stage_s2(const StageArgs &a, int grid, int block, cudaStream_t s);
-static_assert(kNumShapes == 3, "one entry per compiled shape");
+#define RAPID_SHAPE_DECL(NS)                                  \
+  const void *stage_kernel_ptr_##NS(bool batch);              \
+  cudaError_t launch_stage_##NS(const StageArgs &a, int grid, int block, cudaStream_t s);
+RAPID_SHAPE_DECL(s0)
+RAPID_SHAPE_DECL(s1)
+RAPID_SHAPE_DECL(s2)
+RAPID_SHAPE_DECL(s3)
+RAPID_SHAPE_DECL(s4)
+RAPID_SHAPE_DECL(s5)
+static_assert(kNumShapes == 6, "one entry per compiled shape");
 
-int stage_block_threads() { return 1024; }
+int stage_block_threads(int shape) { return kShapes[(shape >= 0 && shape < kNumShapes) ? shape : 0].threads; }
 
 const void *stage_kernel_ptr(bool batch, int shape) {
   switch (shape) {
     case 1: return stage_kernel_ptr_s1(batch);
     case 2: return stage_kernel_ptr_s2(batch);
+    case 3: return stage_kernel_ptr_s3(batch);
+    case 4: return stage_kernel_ptr_s4(batch);
+    case 5: return stage_kernel_ptr_s5(batch);
     default: return stage_kernel_ptr_s0(batch);
   }
 }
@@ -25,6 +31,9 @@ cudaError_t launch_stage(const StageArgs &a, int grid, int block, cudaStream_t s
   switch (shape) {
     case 1: return launch_stage_s1(a, grid, block, s);
     case 2: return launch_stage_s2(a, grid, block, s);
+    case 3: return launch_stage_s3(a, grid, block, s);
+    case 4: return launch_stage_s4(a, grid, block, s);
+    case 5: return launch_stage_s5(a, grid, block, s);
     default: return launch_stage_s0(a, grid, block, s);
   }
 }

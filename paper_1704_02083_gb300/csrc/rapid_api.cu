@@ -51,7 +51,7 @@ struct ImgHost {
 struct rapid_ctx {
   rapid_params p;
   cudaStream_t stream;
-  int device, nsm, coop_grid, coop_block;
+  int device, nsm, coop_grid;
   rapid_status sticky;
   // images and levels
   int nimg;
@@ -216,13 +216,12 @@ extern "C" rapid_status rapid_create(const rapid_params *p, void *cuda_stream, r
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
   int coop = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
-  ctx->coop_block = stage_block_threads();
   // one grid size that every compiled stage kernel can keep co-resident
   int per_sm = INT_MAX;
   for (int sh = 0; sh < kNumShapes && e == cudaSuccess; sh++)
     for (int b = 0; b < 2 && e == cudaSuccess; b++) {
       int k = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, stage_kernel_ptr(b == 1, sh), ctx->coop_block, 0);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, stage_kernel_ptr(b == 1, sh), stage_block_threads(sh), 0);
       per_sm = std::min(per_sm, k);
     }
   if (e != cudaSuccess || !coop || per_sm < 1) {
@@ -694,7 +693,7 @@ extern "C" rapid_status rapid_refine_stage(rapid_ctx *ctx, int32_t *sweeps_out, 
       ctx->launches++;
     }
   const int grid = ctx->stage_grid[i] > 0 ? std::min(ctx->stage_grid[i], ctx->coop_grid) : ctx->coop_grid;
-  CK(launch_stage(a, grid, ctx->coop_block, ctx->stream, ctx->stage_shape[i]));
+  CK(launch_stage(a, grid, stage_block_threads(ctx->stage_shape[i]), ctx->stream, ctx->stage_shape[i]));
   ctx->launches++;
   if (ctx->profiling) CK(cudaEventRecordWithFlags(ctx->ev[i][1], ctx->stream, evflags));
   if (ctx->logger)  // samples: boundary blocks at the start, moved or not by the end

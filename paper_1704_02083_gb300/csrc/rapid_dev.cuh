@@ -35,12 +35,15 @@ enum { PROF_EVAL = 0, PROF_SYNC1, PROF_COMMIT, PROF_SYNC2, PROF_MERGE, PROF_N };
 enum { DERR_TIMEOUT = 1 };
 
 // Evaluation tiles: one warp takes a tile of w x h blocks.  The stage kernel is compiled
-// for each shape below (a launch uses one; the result never depends on it).
+// for each shape below, with `threads` per CTA: 1024 threads hold 64 registers each (some
+// spill), 512 hold 128 (none spill, half the warps per SM).  A launch uses one shape; the
+// result never depends on it.
 struct TileShape {
-  int w, h;
+  int w, h, threads;
 };
-constexpr int kNumShapes = 3;
-constexpr TileShape kShapes[kNumShapes] = {{32, 16}, {32, 8}, {64, 16}};
+constexpr int kNumShapes = 6;
+constexpr TileShape kShapes[kNumShapes] = {{32, 16, 1024}, {32, 8, 1024}, {64, 16, 1024},
+                                           {32, 16, 512},  {32, 8, 512},  {64, 16, 512}};
 constexpr int kTileLabels = 16;
 // tile record: stamp of the last scan, label count (-1: too many), eligible and evaluated
 // counts, the labels, and a bit per phase-class block that issued a merge request (up to
@@ -467,7 +470,7 @@ cudaError_t launch_adam(float *w, float *m, float *v, float *grad, float lr, flo
 
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_stage(const StageArgs &a, int grid, int block, cudaStream_t s, int shape);
-int stage_block_threads();
+int stage_block_threads(int shape);
 const void *stage_kernel_ptr(bool batch, int shape);
 
 // Carve the per-label arrays of M labels from `base` (256-byte aligned pieces); returns the

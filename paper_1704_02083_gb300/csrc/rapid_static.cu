@@ -224,7 +224,7 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   int dev = 0, nsm = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_ptr(false, 0), stage_block_threads(), 0) !=
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_ptr(false, 0), stage_block_threads(0), 0) !=
           cudaSuccess ||
       per_sm < 1)
     return RAPID_ECUDA;
@@ -296,7 +296,7 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
       if (!p->reuse && lev[i] != lev[i - 1]) CKS(launch_recompute(a, &desc[i], 1, stream, &launches));
     }
     CKS(cudaMemsetAsync(ctl + 16, 0, cl.reset_end - 16, stream));  // barrier, merge stamps, counts, changes
-    CKS(launch_stage(a, nsm * per_sm, stage_block_threads(), stream, 0));
+    CKS(launch_stage(a, nsm * per_sm, stage_block_threads(0), stream, 0));
   }
   // Outputs into the caller's buffers.
   const ImageDesc &dl = desc[nst - 1];

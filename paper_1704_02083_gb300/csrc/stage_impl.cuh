@@ -15,7 +15,7 @@
 // atomically.  Merge requests of the phase (size bound hit, Sec. 3.1) are then resolved
 // against the post-move S while the snapshot is refreshed.
 //
-// Work layout: one persistent CTA of 1024 threads per SM.  In the evaluation each warp takes
+// Work layout: one persistent CTA of 1024 (or 512) threads per SM.  In the evaluation each warp takes
 // tiles of kTileW x kTileH blocks (32 x 16, 32 x 8 or 64 x 16 by unit; CTA b takes tiles
 // b, b + grid, ...; its warps draw them from a shared counter), stages the tile's labels with a 1-block halo in shared memory and
 // decides the tile's blocks of the phase class (eval_tile.cuh).  A tile is skipped when no
@@ -55,8 +55,10 @@ constexpr int kReqWords = (kPhaseMax + 31) / 32;
 static_assert(4 + kTileLabels + kReqWords <= kRecInts, "the tile record holds the request words");
 static_assert(kReqWords <= kQueueWords, "the frontier queue holds a tile's class lattice");
 
-static constexpr int kThreads = 1024;
-static_assert(kThreads == 1024, "stage_block_threads() in k_stage.cu returns 1024");
+#ifndef RAPID_THREADS
+#define RAPID_THREADS 1024
+#endif
+static constexpr int kThreads = RAPID_THREADS;
 static_assert((kThreads & (kThreads - 1)) == 0, "block reductions assume a power-of-two CTA size");
 
 static constexpr int kMergeSet = 64;

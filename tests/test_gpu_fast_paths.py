@@ -70,7 +70,7 @@ def _run_with_grids(rgb, grids, autotune=False, **params):
         chosen = ctx.autotune() if autotune else None
         if grids is not None:
             ctx.set_stage_grids(grids)
-            ctx.set_stage_shapes([i % 3 for i in range(len(grids))][::-1])
+            ctx.set_stage_shapes([i % 6 for i in range(len(grids))][::-1])
         ctx.run()
         st = ctx.stats()
         return ctx.labels(), np.stack([st[f] for f in ("n", "sum_r", "sum_x")], 1), ctx.counters_array(), chosen
@@ -95,7 +95,7 @@ def test_autotune_picks_valid_grids_and_keeps_results():
     lab, st, cnt, (grids, shapes) = _run_with_grids(rgb, None, autotune=True, **params)
     full = torch.cuda.get_device_properties(0).multi_processor_count
     assert len(grids) == len(shapes) == cnt.shape[0]
-    assert all(1 <= g <= full for g in grids) and all(0 <= k < 3 for k in shapes)
+    assert all(1 <= g <= full for g in grids) and all(0 <= k < 6 for k in shapes)
     np.testing.assert_array_equal(lab, ref[0])
     np.testing.assert_array_equal(st, ref[1])
     np.testing.assert_array_equal(cnt, ref[2])

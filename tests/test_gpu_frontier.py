@@ -74,7 +74,7 @@ def test_every_tile_shape_and_grid_gives_the_oracle_run(name, rgb, params):
     """The queue flags live per (tile, phase class): pushes across tile edges and ragged
     tiles must land on the block the oracle queues, whatever the shape and grid."""
     rlab, rst, _, _, rcnt = oracle_run(rgb, schedule=1, **params)
-    for shape in (0, 1, 2):
+    for shape in range(6):
         for grids in (None, [1], [7, 3, 152]):
             lab, st, cnt = _run_shapes(rgb, shape, grids, **params)
             tag = f"shape {shape} grids {grids}"
