@@ -423,15 +423,16 @@ __device__ __forceinline__ void set_means(const DevStats &s, int k) {
 __device__ __forceinline__ double mean_of(const long long *sum, const long long *cnt, int k) {
   return __ddiv_rn(__ll2double_rn(sum[k]), __ll2double_rn(cnt[k]));
 }
-__device__ __forceinline__ double ward_cost(const DevStats &s, int a, int n, double lam_pos) {
+// am: a's means (R, G, B, X, Y) as mean_of gives them.
+__device__ __forceinline__ double ward_cost(const DevStats &s, int a, const double *am, int n, double lam_pos) {
   double t = __ddiv_rn(__dmul_rn(__ll2double_rn(s.N[a]), __ll2double_rn(s.N[n])),
                        __ll2double_rn(s.N[a] + s.N[n]));
-  double d0 = __dsub_rn(mean_of(s.R, s.N, a), mean_of(s.R, s.N, n));
-  double d1 = __dsub_rn(mean_of(s.G, s.N, a), mean_of(s.G, s.N, n));
-  double d2 = __dsub_rn(mean_of(s.B, s.N, a), mean_of(s.B, s.N, n));
+  double d0 = __dsub_rn(am[0], mean_of(s.R, s.N, n));
+  double d1 = __dsub_rn(am[1], mean_of(s.G, s.N, n));
+  double d2 = __dsub_rn(am[2], mean_of(s.B, s.N, n));
   double dc = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
-  double e0 = __dsub_rn(mean_of(s.X, s.N, a), mean_of(s.X, s.N, n));
-  double e1 = __dsub_rn(mean_of(s.Y, s.N, a), mean_of(s.Y, s.N, n));
+  double e0 = __dsub_rn(am[3], mean_of(s.X, s.N, n));
+  double e1 = __dsub_rn(am[4], mean_of(s.Y, s.N, n));
   double dm = __dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1));
   return __dmul_rn(t, __dadd_rn(dc, __dmul_rn(lam_pos, dm)));
 }

@@ -212,6 +212,7 @@ __device__ __forceinline__ void merge_targets(const StageArgs &a, const ImageDes
   __shared__ int nset[kMergeSet];
   __shared__ int s_over, s_hit;
   __shared__ int s_ext[4];
+  __shared__ double s_am[5];
   const DevStats &s = a.st;
   const DevMerge &mg = a.mg;
   for (int j = blockIdx.x; j < rq; j += gridDim.x) {
@@ -241,6 +242,13 @@ __device__ __forceinline__ void merge_targets(const StageArgs &a, const ImageDes
       }
     }
     if (threadIdx.x < kMergeSet) nset[threadIdx.x] = -1;
+    if (threadIdx.x == 32) {  // the requesting label's means, shared by every candidate's cost
+      s_am[0] = mean_of(s.R, s.N, al);
+      s_am[1] = mean_of(s.G, s.N, al);
+      s_am[2] = mean_of(s.B, s.N, al);
+      s_am[3] = mean_of(s.X, s.N, al);
+      s_am[4] = mean_of(s.Y, s.N, al);
+    }
     __syncthreads();
     if (s_hit) {
       if (threadIdx.x == 0) mg.target[al] = -1;  // no target: the request is finished here
@@ -256,18 +264,42 @@ __device__ __forceinline__ void merge_targets(const StageArgs &a, const ImageDes
     const int *lab = im.lab;
     const int nbx = im.nbx, nby = im.nby;
     int mnx = INT_MAX, mny = INT_MAX, mxx = -1, mxy = -1;
-    for (long long t = threadIdx.x; t < total; t += blockDim.x) {
-      const int cx = bx0 + (int)(t % bw), cy = by0 + (int)(t / bw);
-      const long long idx = (long long)cy * nbx + cx;
-      if (lab[idx] != al) continue;
-      mnx = min(mnx, cx);
-      mxx = max(mxx, cx);
-      mny = min(mny, cy);
-      mxy = max(mxy, cy);
-      const int q[4] = {cy > 0 ? lab[idx - nbx] : -1, cx > 0 ? lab[idx - 1] : -1,
-                        cx + 1 < nbx ? lab[idx + 1] : -1, cy + 1 < nby ? lab[idx + nbx] : -1};
-      for (int i = 0; i < 4; i++)
-        if (q[i] >= 0 && q[i] != al) set_insert(nset, kMergeSet, q[i], &s_over);
+    // kScan boxes per thread at a time: their labels in one round trip, then the
+    // neighbours of those labelled al in another
+    constexpr int kScan = 4;
+    for (long long t0 = threadIdx.x; t0 < total; t0 += (long long)kScan * blockDim.x) {
+      int cx[kScan], cy[kScan];
+      bool hit[kScan];
+#pragma unroll
+      for (int u = 0; u < kScan; u++) {
+        const long long t = t0 + (long long)u * blockDim.x;
+        hit[u] = false;
+        cx[u] = cy[u] = 0;
+        if (t < total) {
+          cx[u] = bx0 + (int)(t % bw);
+          cy[u] = by0 + (int)(t / bw);
+          hit[u] = lab[(long long)cy[u] * nbx + cx[u]] == al;
+        }
+      }
+      int q[kScan][4];
+#pragma unroll
+      for (int u = 0; u < kScan; u++) {
+        q[u][0] = q[u][1] = q[u][2] = q[u][3] = -1;
+        if (!hit[u]) continue;
+        const long long idx = (long long)cy[u] * nbx + cx[u];
+        mnx = min(mnx, cx[u]);
+        mxx = max(mxx, cx[u]);
+        mny = min(mny, cy[u]);
+        mxy = max(mxy, cy[u]);
+        q[u][0] = cy[u] > 0 ? lab[idx - nbx] : -1;
+        q[u][1] = cx[u] > 0 ? lab[idx - 1] : -1;
+        q[u][2] = cx[u] + 1 < nbx ? lab[idx + 1] : -1;
+        q[u][3] = cy[u] + 1 < nby ? lab[idx + nbx] : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < kScan; u++)
+        for (int i = 0; i < 4; i++)
+          if (q[u][i] >= 0 && q[u][i] != al) set_insert(nset, kMergeSet, q[u][i], &s_over);
     }
     if (mxx >= 0) {
       atomicMin(&s_ext[0], mnx);
@@ -287,7 +319,7 @@ __device__ __forceinline__ void merge_targets(const StageArgs &a, const ImageDes
         const int n = nset[i];
         if (n < 0) continue;
         if ((long long)a.hi_den * (s.N[n] + s.N[al]) > (long long)a.hi_num * s.init[n]) continue;
-        const double wv = ward_cost(s, al, n, im.lam_pos);
+        const double wv = ward_cost(s, al, s_am, n, im.lam_pos);
         if (bestn == INT_MAX || wv < best || (wv == best && n < bestn)) {
           best = wv;
           bestn = n;
@@ -304,7 +336,7 @@ __device__ __forceinline__ void merge_targets(const StageArgs &a, const ImageDes
           const int n = q[i];
           if (n < 0 || n == al) continue;
           if ((long long)a.hi_den * (s.N[n] + s.N[al]) > (long long)a.hi_num * s.init[n]) continue;
-          const double wv = ward_cost(s, al, n, im.lam_pos);
+          const double wv = ward_cost(s, al, s_am, n, im.lam_pos);
           if (bestn == INT_MAX || wv < best || (wv == best && n < bestn)) {
             best = wv;
             bestn = n;
