@@ -366,7 +366,9 @@ rapid_status rapid_simple_table(uint8_t *out256);
  * every byte of working memory comes from one fixed 16 MiB __device__ array inside the
  * library; every GPU that loads the library holds that array until the process exits.
  *
- * p: parameters as for rapid_create.  rgb_dev: H x W interleaved RGB in device memory, rows
+ * p: parameters as for rapid_create (schedule 0 or 1; the prediction uses the brightness
+ * stand-in: a context's classifier, scorer and tile shapes do not apply here, and every
+ * stage uses the 32 x 16-block tiles).  rgb_dev: H x W interleaved RGB in device memory, rows
  * rgb_pitch_bytes apart (>= 3*W), read only.  labels_dev: device H x W int32 output, rows
  * labels_pitch_bytes apart (>= 4*W, multiple of 4).  stats_dev: device output of
  * stats_capacity entries (>= M), index = label id.  *M_out (host, may be NULL) receives M.

@@ -44,16 +44,18 @@ def _single(rgb, K, **params):
         return ctx.labels(), ctx.state()["M"], ctx.stats()
 
 
+@pytest.mark.parametrize("schedule", [0, 1], ids=["sweeps", "queue"])
 @pytest.mark.parametrize("H,W,max_tile,ppsp,check", [(600, 900, 256, 1024, "all"), (300, 310, 32, 256, "some")],
                          ids=["12_tiles", "100_tiles_two_batches"])
-def test_slide_tiles_equal_single_runs(H, W, max_tile, ppsp, check):
+def test_slide_tiles_equal_single_runs(H, W, max_tile, ppsp, check, schedule):
     import torch
 
     import paper_1704_02083_gb300 as pkg
 
     img = synth.slide_image(H, W, 7)
     rgb = torch.from_numpy(img.rgb).cuda()
-    with pkg.Context(stream=torch.cuda.current_stream(), **PARAMS) as ctx:
+    params = dict(PARAMS, schedule=schedule)
+    with pkg.Context(stream=torch.cuda.current_stream(), **params) as ctx:
         stats = torch.zeros((200000 * pkg.SP_STATS_DTYPE.itemsize,), dtype=torch.uint8, device="cuda")
         labels, M, T = ctx.refine_slide(rgb, max_tile=max_tile, px_per_superpixel=ppsp, stats=stats)
         torch.cuda.synchronize()
@@ -69,7 +71,7 @@ def test_slide_tiles_equal_single_runs(H, W, max_tile, ppsp, check):
             tile = np.ascontiguousarray(img.rgb[r0:r1, c0:c1])
             sub = lab[r0:r1, c0:c1]
             if check == "all" or t % 17 == 0 or t == T - 1:
-                slab, m, sst = _single(tile, K, **PARAMS)
+                slab, m, sst = _single(tile, K, **params)
                 np.testing.assert_array_equal(sub - offset, slab, err_msg=f"tile {t}")
                 np.testing.assert_array_equal(st[offset:offset + m]["n"], sst["n"])
                 np.testing.assert_array_equal(st[offset:offset + m]["sum_x"], sst["sum_x"])
