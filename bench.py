@@ -567,7 +567,8 @@ def run_slide(args, rank, world, local):
             for st_i in range(nst):
                 if nimg == 0:
                     stage_ms[st_i] += c.stage[st_i].kernel_ms
-                stage_bytes[st_i] += stage_alg_bytes(info["H"], info["W"], c.stage[st_i], lf)
+                stage_bytes[st_i] += stage_alg_bytes(info["H"], info["W"], c.stage[st_i], lf,
+                                                     params.get("schedule", 0) == 1)
             nimg += 1
     torch.cuda.synchronize()
     if world > 1:
@@ -615,6 +616,7 @@ def run_slide(args, rank, world, local):
                        "M_total": M, "px_per_superpixel": sd["px_per_superpixel"],
                        "batches": -(-T // pkg.RAPID_MAX_BATCH), "levels": L, "ratio_C": C,
                        "init_block": params["init_block"], "predict": params["predict"],
+                       "schedule": "frontier queue" if params.get("schedule", 0) == 1 else "sweeps",
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"kernel": f"stage_kernel, stage {dom} (level {st_dom.level}, block side {st_dom.block}), "

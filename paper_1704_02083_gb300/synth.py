@@ -249,6 +249,10 @@ SLIDES = {
                         params=dict(num_levels=3, ratio_C=4, init_block=32, final_grain=1, size_mode=2,
                                     predict=1, reuse=1)),
 }
+# The same batch and slide refined with the queue schedule.
+for _d in (BATCHES, SLIDES):
+    for _name in list(_d):
+        _d[_name + "_frontier"] = dict(_d[_name], params=dict(_d[_name]["params"], schedule=1))
 
 
 def batch_sizes(n: int, seed: int):
