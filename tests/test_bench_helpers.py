@@ -1,0 +1,40 @@
+"""Host helpers of bench.py: the stage kernel's code hash that keys the committed DRAM
+counters (comments and blank lines do not change it, code does), and the algorithmic
+bytes of a stage launch under both schedules."""
+import os
+import shutil
+import types
+
+import bench
+
+CSRC = os.path.join(bench.ROOT, "paper_1704_02083_gb300", "csrc")
+
+
+def _copy(tmp_path):
+    d = tmp_path / "csrc"
+    shutil.copytree(CSRC, d)
+    return str(d)
+
+
+def test_code_hash_ignores_comments_but_not_code(tmp_path):
+    d = _copy(tmp_path)
+    h0 = bench.kernel_source_sha256(d)
+    assert h0 == bench.kernel_source_sha256()
+    p = os.path.join(d, "stage_impl.cuh")
+    src = open(p).read()
+    open(p, "w").write("// a new comment line\n\n" + src.replace("\n", "  // trailing note\n", 1))
+    assert bench.kernel_source_sha256(d) == h0
+    open(p, "w").write(src.replace("kMergeSet = 64", "kMergeSet = 32"))
+    assert bench.kernel_source_sha256(d) != h0
+
+
+def test_stage_alg_bytes_both_schedules():
+    st = types.SimpleNamespace(block=1, level=3, sweeps=64, moves=1000, eligible=50000)
+    lf = {1: 16, 2: 4, 3: 1}
+    H = W = 4096
+    nb = H * W
+    assert bench.stage_alg_bytes(H, W, st, lf) == 4 * nb * 64 + 4 * 1000 + 3 * H * W
+    assert bench.stage_alg_bytes(H, W, st, lf, True) == nb * 64 / 8 + 4 * 50000 + 4 * 1000 + 3 * H * W
+    coarse = types.SimpleNamespace(block=32, level=1, sweeps=6, moves=10, eligible=100)
+    nbc = (H // 32) * (W // 32)
+    assert bench.stage_alg_bytes(H, W, coarse, lf) == 4 * nbc * 6 + 40 + 12 * (H // 16) * (W // 16)
