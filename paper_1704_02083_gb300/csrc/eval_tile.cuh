@@ -247,7 +247,9 @@ __device__ __forceinline__ void queue_push_neighbours(const StageArgs &a, const 
 
 // Pass 2 (one compacted block per lane): block sums, the decision (Eq. operation), the size
 // term (Sec. 3.1) and the move.
-// Returns true when the block raised a merge request instead of moving.
+// Returns true when the block raised a merge request instead of moving.  kFrontier: the queue
+// schedule (moves queue their 4-neighbours).
+template <bool kFrontier>
 __device__ __forceinline__ bool decide_block_at(const StageArgs &a, const ImageDesc &im, int lbl0, int nN, int nW,
                                                 int nE, int nS, int bx, int by, int g, Local &lc) {
   const DevStats &s = a.st;
@@ -302,16 +304,17 @@ __device__ __forceinline__ bool decide_block_at(const StageArgs &a, const ImageD
   atomicMin(&s.bbox[k].y, in.y0);
   atomicMax(&s.bbox[k].z, in.x0 + bs.bw - 1);
   atomicMax(&s.bbox[k].w, in.y0 + bs.bh - 1);
-  if (a.frontier) queue_push_neighbours(a, im, bx, by);  // (other phase classes only)
+  if (kFrontier) queue_push_neighbours(a, im, bx, by);  // (other phase classes only)
   lc.moves++;
   return false;
 }
 
 // Pass 2 of the tile path: the block at window index c (phase-class index j).
+template <bool kFrontier>
 __device__ __forceinline__ void decide_block(const StageArgs &a, const ImageDesc &im, WarpTile &W, int c, int j, int bx,
                                              int by, int g, Local &lc) {
   const int *win = W.win;
-  if (decide_block_at(a, im, win[c], win[c - kWinW], win[c - 1], win[c + 1], win[c + kWinW], bx, by, g, lc))
+  if (decide_block_at<kFrontier>(a, im, win[c], win[c - kWinW], win[c - 1], win[c + 1], win[c + kWinW], bx, by, g, lc))
     atomicOr(&W.req[j >> 5], 1u << (j & 31));
 }
 
@@ -363,8 +366,8 @@ __device__ __forceinline__ void flush_counts(const StageArgs &a, int ii, int slo
 
 // g: 1-based phase number within the launch; slot: the sweep's change-count slot.  imgs,
 // tile0 and active are the CTA's shared copies of the images, their first tiles and
-// whether each still refines in this stage.
-template <bool kBatch>
+// whether each still refines in this stage.  kFrontier: the queue schedule's tile walk.
+template <bool kBatch, bool kFrontier>
 __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *imgs, const int *tile0,
                                            const unsigned char *active, const unsigned char *pruned,
                                            const int *valid_from, WarpTile *wts, int *s_draw, int phase, int g,
@@ -403,7 +406,7 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
     const int tx = lt % im.ntx, ty = lt / im.ntx;
     const int bx0 = tx * kTileW, by0 = ty * kTileH;
     int *rec = a.trec + ((long long)t * 9 + phase) * kRecInts;
-    const bool fq = a.frontier;
+    constexpr bool fq = kFrontier;
     unsigned qv = 0u;
     if (fq) {  // frontier schedule: pop the tile's queued blocks of this class (if any)
       unsigned *qw = a.qbits + ((long long)t * 9 + phase) * kQueueWords;
@@ -498,7 +501,7 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
     for (int it = lane; it < nitems; it += 32) {
       const int j = W.items[it];
       const int lx = lx0 + 3 * (j % nx), ly = ly0 + 3 * (j / nx);
-      decide_block(a, im, W, (ly + 1) * kWinW + (lx + 1), j, bx0 + lx, by0 + ly, g, lc);
+      decide_block<kFrontier>(a, im, W, (ly + 1) * kWinW + (lx + 1), j, bx0 + lx, by0 + ly, g, lc);
     }
     const int de = warp_sum(lc.elig - e0), dv = warp_sum(lc.eval - v0);
     __syncwarp();
@@ -582,7 +585,7 @@ __device__ __forceinline__ void eval_queue(const StageArgs &a, const ImageDesc *
     atomicAnd(w, ~bit);  // off the queue
     Local lc = {0, 0, 0, 0, 0, 0};
     if (block_tests(a, lbl, nN, nW, nE, nS, nNW, nNE, nSE, nSW, nullptr, 0, lc))
-      decide_block_at(a, im, lbl, nN, nW, nE, nS, bx, by, g, lc);
+      decide_block_at<true>(a, im, lbl, nN, nW, nE, nS, bx, by, g, lc);
     int *c = s_cnt + ii * 6;
     if (lc.elig) atomicAdd(c + 0, lc.elig);
     if (lc.eval) atomicAdd(c + 1, lc.eval);

@@ -4,7 +4,7 @@
 
 namespace rapid {
 #define RAPID_SHAPE_DECL(NS)                                  \
-  const void *stage_kernel_ptr_##NS(bool batch);              \
+  const void *stage_kernel_ptr_##NS(bool batch, bool frontier); \
   cudaError_t launch_stage_##NS(const StageArgs &a, int grid, int block, cudaStream_t s);
 RAPID_SHAPE_DECL(s0)
 RAPID_SHAPE_DECL(s1)
@@ -16,14 +16,14 @@ static_assert(kNumShapes == 6, "one entry per compiled shape");
 
 int stage_block_threads(int shape) { return kShapes[(shape >= 0 && shape < kNumShapes) ? shape : 0].threads; }
 
-const void *stage_kernel_ptr(bool batch, int shape) {
+const void *stage_kernel_ptr(bool batch, bool frontier, int shape) {
   switch (shape) {
-    case 1: return stage_kernel_ptr_s1(batch);
-    case 2: return stage_kernel_ptr_s2(batch);
-    case 3: return stage_kernel_ptr_s3(batch);
-    case 4: return stage_kernel_ptr_s4(batch);
-    case 5: return stage_kernel_ptr_s5(batch);
-    default: return stage_kernel_ptr_s0(batch);
+    case 1: return stage_kernel_ptr_s1(batch, frontier);
+    case 2: return stage_kernel_ptr_s2(batch, frontier);
+    case 3: return stage_kernel_ptr_s3(batch, frontier);
+    case 4: return stage_kernel_ptr_s4(batch, frontier);
+    case 5: return stage_kernel_ptr_s5(batch, frontier);
+    default: return stage_kernel_ptr_s0(batch, frontier);
   }
 }
 

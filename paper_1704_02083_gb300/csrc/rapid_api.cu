@@ -219,9 +219,10 @@ extern "C" rapid_status rapid_create(const rapid_params *p, void *cuda_stream, r
   // one grid size that every compiled stage kernel can keep co-resident
   int per_sm = INT_MAX;
   for (int sh = 0; sh < kNumShapes && e == cudaSuccess; sh++)
-    for (int b = 0; b < 2 && e == cudaSuccess; b++) {
+    for (int b = 0; b < 4 && e == cudaSuccess; b++) {
       int k = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, stage_kernel_ptr(b == 1, sh), stage_block_threads(sh), 0);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, stage_kernel_ptr(b & 1, b >> 1, sh), stage_block_threads(sh),
+                                                        0);
       per_sm = std::min(per_sm, k);
     }
   if (e != cudaSuccess || !coop || per_sm < 1) {

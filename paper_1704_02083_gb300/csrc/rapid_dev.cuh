@@ -472,7 +472,7 @@ cudaError_t launch_adam(float *w, float *m, float *v, float *grad, float lr, flo
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_stage(const StageArgs &a, int grid, int block, cudaStream_t s, int shape);
 int stage_block_threads(int shape);
-const void *stage_kernel_ptr(bool batch, int shape);
+const void *stage_kernel_ptr(bool batch, bool frontier, int shape);
 
 // Carve the per-label arrays of M labels from `base` (256-byte aligned pieces); returns the
 // bytes used, or 0 when they do not fit in `cap` bytes.  label_arrays_bytes(M) is the size.

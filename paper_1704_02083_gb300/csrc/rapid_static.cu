@@ -224,7 +224,7 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   int dev = 0, nsm = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_ptr(false, 0), stage_block_threads(0), 0) !=
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_ptr(false, p->schedule == 1, 0), stage_block_threads(0), 0) !=
           cudaSuccess ||
       per_sm < 1)
     return RAPID_ECUDA;

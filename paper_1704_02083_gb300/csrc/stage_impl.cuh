@@ -458,7 +458,7 @@ __device__ void merge_walk_big(const StageArgs &a, int nf) {
 // Apply accepted merges (list in shared or global memory).  The request state needs no
 // clearing: its keys and flags carry the phase number, so another CTA may still read them
 // for its own walk while this one applies.
-template <bool kBatch>
+template <bool kBatch, bool kFrontier>
 __device__ __forceinline__ void merge_apply(const StageArgs &a, const ImageDesc *imgs, const int *label0,
                                             const int2 *acc, int nacc, int g, int slot) {
   const DevStats &s = a.st;
@@ -489,7 +489,7 @@ __device__ __forceinline__ void merge_apply(const StageArgs &a, const ImageDesc 
       s.bbox[n] = bn;
       atomic_add_i64(&a.ctl.cnt[(long long)ii * kCntStride + CNT_MERGES], 1);
       atomicAdd(&a.ctl.changes[3 * ii + slot], 1ull);
-      if (a.frontier) {  // the 4-neighbours of the request's first block join the queue
+      if (kFrontier) {  // the 4-neighbours of the request's first block join the queue
         const long long blk = (long long)req_block(mg.req_min[al]) - im.blk0;
         queue_push_neighbours(a, im, (int)(blk % im.nbx), (int)(blk / im.nbx));
       }
@@ -521,8 +521,9 @@ struct Timer {
 };
 
 // kBatch: a launch over several images (descriptors copied to shared memory); otherwise
-// one image, whose descriptor the kernel reads from its parameters.
-template <bool kBatch>
+// one image, whose descriptor the kernel reads from its parameters.  kFrontier: the queue
+// schedule (compiled separately, so the sweep schedule's kernel carries none of its code).
+template <bool kBatch, bool kFrontier>
 __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
   constexpr int kImgs = kBatch ? kMaxBatch : 1;
   __shared__ WarpTile wts[kThreads / 32];
@@ -555,7 +556,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
   }
   const long long nrec = (long long)a.ntiles * 9;
   for (long long i = gtid; i < nrec; i += gstride) a.trec[i * kRecInts] = 0;
-  if (a.frontier) {  // frontier schedule: every block is queued when the stage starts
+  if (kFrontier) {  // frontier schedule: every block is queued when the stage starts
     for (long long i = gtid; i < nrec * kQueueWords; i += gstride) a.qbits[i] = ~0u;
     if (gtid < 9) a.wl_count[gtid] = 0;  // blocks queued from the start are not listed
   }
@@ -570,11 +571,15 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
       g++;
       // frontier schedule: after the first sweep every queued block is on its class's list;
       // a short list is worked off one thread per block, a long one by the tile walk
-      const int nq = (a.frontier && sweep > 0) ? ld_volatile_i32(a.wl_count + ph) : INT_MAX;
-      if (nq <= 4 * (int)(gridDim.x * blockDim.x))
-        eval_queue<kBatch>(a, s_img, s_active, s_cnt, ph, g, slot, nq);
-      else
-        eval_phase<kBatch>(a, s_img, s_tile0, s_active, s_pruned, s_valid_from, wts, &s_draw, ph, g, slot);
+      if constexpr (kFrontier) {
+        const int nq = sweep > 0 ? ld_volatile_i32(a.wl_count + ph) : INT_MAX;
+        if (nq <= 4 * (int)(gridDim.x * blockDim.x))
+          eval_queue<kBatch>(a, s_img, s_active, s_cnt, ph, g, slot, nq);
+        else
+          eval_phase<kBatch, true>(a, s_img, s_tile0, s_active, s_pruned, s_valid_from, wts, &s_draw, ph, g, slot);
+      } else {
+        eval_phase<kBatch, false>(a, s_img, s_tile0, s_active, s_pruned, s_valid_from, wts, &s_draw, ph, g, slot);
+      }
 
       tm.lap(PROF_EVAL);
       if (!grid_sync(a.ctl, epoch)) return;
@@ -583,7 +588,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {  // slots of the next phase; last read a phase ago
         a.mg.req_count[gp ^ 1] = 0;
         a.mg.found_count[gp ^ 1] = 0;
-        if (a.frontier) a.wl_count[ph] = 0;  // the class's queued blocks all left the queue above
+        if (kFrontier) a.wl_count[ph] = 0;  // the class's queued blocks all left the queue above
       }
       // the snapshot refresh and the merge-target search (which reads only S, the label
       // map and the merge state) share the barrier that ends them
@@ -598,11 +603,11 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
         if (nf > 0) {
           if (nf <= kAcceptSmem) {
             const int nacc = merge_walk_small(a, nf, s_acc);
-            merge_apply<kBatch>(a, s_img, s_label0, s_acc, nacc, g, slot);
+            merge_apply<kBatch, kFrontier>(a, s_img, s_label0, s_acc, nacc, g, slot);
           } else {
             if (blockIdx.x == 0) merge_walk_big(a, nf);
             if (!grid_sync(a.ctl, epoch)) return;
-            merge_apply<kBatch>(a, s_img, s_label0, a.mg.acc, ld_volatile_i32(a.mg.acc_count), g, slot);
+            merge_apply<kBatch, kFrontier>(a, s_img, s_label0, a.mg.acc, ld_volatile_i32(a.mg.acc_count), g, slot);
           }
           if (!grid_sync(a.ctl, epoch)) return;
         }
@@ -635,15 +640,17 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
 
 }  // namespace RAPID_SHAPE_NS
 
-const void *RAPID_CAT(stage_kernel_ptr_, RAPID_SHAPE_NS)(bool batch) {
-  return batch ? (const void *)RAPID_SHAPE_NS::stage_kernel<true> : (const void *)RAPID_SHAPE_NS::stage_kernel<false>;
+const void *RAPID_CAT(stage_kernel_ptr_, RAPID_SHAPE_NS)(bool batch, bool frontier) {
+  using namespace RAPID_SHAPE_NS;
+  if (frontier) return batch ? (const void *)stage_kernel<true, true> : (const void *)stage_kernel<false, true>;
+  return batch ? (const void *)stage_kernel<true, false> : (const void *)stage_kernel<false, false>;
 }
 
 cudaError_t RAPID_CAT(launch_stage_, RAPID_SHAPE_NS)(const StageArgs &a, int grid, int block, cudaStream_t s) {
   StageArgs copy = a;
   void *args[] = {&copy};
-  return cudaLaunchCooperativeKernel(RAPID_CAT(stage_kernel_ptr_, RAPID_SHAPE_NS)(a.nimg > 1), dim3(grid),
-                                     dim3(block), args, 0, s);
+  return cudaLaunchCooperativeKernel(RAPID_CAT(stage_kernel_ptr_, RAPID_SHAPE_NS)(a.nimg > 1, a.frontier != 0),
+                                     dim3(grid), dim3(block), args, 0, s);
 }
 
 }  // namespace rapid
