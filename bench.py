@@ -109,6 +109,23 @@ def load_workload(name: str):
     return [synth.workload_image(name).rgb], [params.pop("K")], params
 
 
+def host_cpu():
+    """The host's CPU model and the cores this process may run on."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware") and ":" in line:
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"cpu_model": model, "host_cores": len(os.sched_getaffinity(0)), "threads_used": 1}
+
+
 def time_oracle(rgb, params, reps=1):
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle
@@ -259,7 +276,7 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ts),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": args.workload, "sample": desc},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, **host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -447,7 +464,7 @@ def run_rapid(args, rank, world, local):
         rgb_s, params_s, desc = cpu_sample(args.workload)
         ts = time_oracle(rgb_s, params_s, reps=1)
         cpu = {"value": rgb_s.shape[0] * rgb_s.shape[1] / ts[0] / 1e6, "unit": UNIT, "cores": 1,
-               "kind": "oracle", "sample": desc}
+               "kind": "oracle", "sample": desc, **host_cpu()}
 
     # roofline of the dominant launch: the stage launch with the largest device time (the
     # finest stage); its duration from CUDA events around each stage launch on ``stream``
@@ -600,7 +617,7 @@ def run_slide(args, rank, world, local):
         rgb_s, params_s, desc = cpu_sample(args.workload)
         ts = time_oracle(rgb_s, params_s, reps=1)
         cpu = {"value": rgb_s.shape[0] * rgb_s.shape[1] / ts[0] / 1e6, "unit": UNIT, "cores": 1,
-               "kind": "oracle", "sample": desc}
+               "kind": "oracle", "sample": desc, **host_cpu()}
 
     peak, peak_kind = measured_peak()
     dom = max(range(nst), key=lambda i: stage_ms[i])
