@@ -117,7 +117,10 @@ typedef struct rapid_stage_counters {
   int64_t filter_mismatches; /* with verify_filter: single-precision decisions that differ
                               from binary64 (must be 0) */
   int64_t tiles_scanned;   /* tile-phase scans performed ... */
-  int64_t tiles_skipped;   /* ... and skipped because nothing they depend on changed */
+  int64_t tiles_skipped;   /* ... and skipped because nothing they depend on changed (queue
+                              schedule: because none of their blocks of the phase class was
+                              queued; its sparse phases take listed blocks, not tiles, and
+                              count neither) */
   int64_t merge_searches;  /* merge-target searches that scanned the label map ... */
   int64_t merge_cache_hits; /* ... and requests answered by a still-valid earlier failure */
   float kernel_ms;         /* device time of the stage's refinement launch when profiling is
