@@ -496,7 +496,8 @@ def run_rapid(args, rank, world, local):
             cfg.update({"H": sizes[0][0], "W": sizes[0][1]})
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "ms_per_step_median": statistics.median(step_ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": cfg,
             "roofline": {"kernel": f"stage_kernel, stage {dom} (level {st_dom.level}, block side {st_dom.block})",
@@ -627,7 +628,8 @@ def run_slide(args, rank, world, local):
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "ms_per_step_median": statistics.median(step_ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "H": H, "W": W, "tiles": T, "max_tile": sd["max_tile"],
                        "M_total": M, "px_per_superpixel": sd["px_per_superpixel"],
