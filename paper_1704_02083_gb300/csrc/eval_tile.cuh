@@ -247,9 +247,9 @@ __device__ __forceinline__ void queue_push_neighbours(const StageArgs &a, const 
 
 // Pass 2 (one compacted block per lane): block sums, the decision (Eq. operation), the size
 // term (Sec. 3.1) and the move.
-// Returns true when the block raised a merge request instead of moving.  kFrontier: the queue
-// schedule (moves queue their 4-neighbours).
-template <bool kFrontier>
+// Returns true when the block raised a merge request instead of moving.  Under the queue
+// schedule a move queues its 4-neighbours.
+template <int kSched>
 __device__ __forceinline__ bool decide_block_at(const StageArgs &a, const ImageDesc &im, int lbl0, int nN, int nW,
                                                 int nE, int nS, int bx, int by, int g, Local &lc) {
   const DevStats &s = a.st;
@@ -304,17 +304,17 @@ __device__ __forceinline__ bool decide_block_at(const StageArgs &a, const ImageD
   atomicMin(&s.bbox[k].y, in.y0);
   atomicMax(&s.bbox[k].z, in.x0 + bs.bw - 1);
   atomicMax(&s.bbox[k].w, in.y0 + bs.bh - 1);
-  if (kFrontier) queue_push_neighbours(a, im, bx, by);  // (other phase classes only)
+  if (queue_schedule<kSched>(a)) queue_push_neighbours(a, im, bx, by);  // (other phase classes only)
   lc.moves++;
   return false;
 }
 
 // Pass 2 of the tile path: the block at window index c (phase-class index j).
-template <bool kFrontier>
+template <int kSched>
 __device__ __forceinline__ void decide_block(const StageArgs &a, const ImageDesc &im, WarpTile &W, int c, int j, int bx,
                                              int by, int g, Local &lc) {
   const int *win = W.win;
-  if (decide_block_at<kFrontier>(a, im, win[c], win[c - kWinW], win[c - 1], win[c + 1], win[c + kWinW], bx, by, g, lc))
+  if (decide_block_at<kSched>(a, im, win[c], win[c - kWinW], win[c - 1], win[c + 1], win[c + kWinW], bx, by, g, lc))
     atomicOr(&W.req[j >> 5], 1u << (j & 31));
 }
 
@@ -366,8 +366,8 @@ __device__ __forceinline__ void flush_counts(const StageArgs &a, int ii, int slo
 
 // g: 1-based phase number within the launch; slot: the sweep's change-count slot.  imgs,
 // tile0 and active are the CTA's shared copies of the images, their first tiles and
-// whether each still refines in this stage.  kFrontier: the queue schedule's tile walk.
-template <bool kBatch, bool kFrontier>
+// whether each still refines in this stage.  kSched: the schedule (kSchedSweeps, ...).
+template <bool kBatch, int kSched>
 __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *imgs, const int *tile0,
                                            const unsigned char *active, const unsigned char *pruned,
                                            const int *valid_from, WarpTile *wts, int *s_draw, int phase, int g,
@@ -406,7 +406,7 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
     const int tx = lt % im.ntx, ty = lt / im.ntx;
     const int bx0 = tx * kTileW, by0 = ty * kTileH;
     int *rec = a.trec + ((long long)t * 9 + phase) * kRecInts;
-    constexpr bool fq = kFrontier;
+    const bool fq = queue_schedule<kSched>(a);
     unsigned qv = 0u;
     if (fq) {  // frontier schedule: pop the tile's queued blocks of this class (if any)
       unsigned *qw = a.qbits + ((long long)t * 9 + phase) * kQueueWords;
@@ -501,7 +501,7 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
     for (int it = lane; it < nitems; it += 32) {
       const int j = W.items[it];
       const int lx = lx0 + 3 * (j % nx), ly = ly0 + 3 * (j / nx);
-      decide_block<kFrontier>(a, im, W, (ly + 1) * kWinW + (lx + 1), j, bx0 + lx, by0 + ly, g, lc);
+      decide_block<kSched>(a, im, W, (ly + 1) * kWinW + (lx + 1), j, bx0 + lx, by0 + ly, g, lc);
     }
     const int de = warp_sum(lc.elig - e0), dv = warp_sum(lc.eval - v0);
     __syncwarp();
@@ -528,7 +528,7 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
 // (32 consecutive entries per warp, warps spread over the CTAs first), no tile walk.  The
 // listed blocks are exactly the queued blocks of the class; each leaves the queue here.
 // Counts go through the CTA's per-image shared counters s_cnt[image * 6 + ...].
-template <bool kBatch>
+template <bool kBatch, int kSched>
 __device__ __forceinline__ void eval_queue(const StageArgs &a, const ImageDesc *imgs, const unsigned char *active,
                                            int *s_cnt, int phase, int g, int slot, int nq) {
   const int nimg = kBatch ? a.nimg : 1;
@@ -585,7 +585,7 @@ __device__ __forceinline__ void eval_queue(const StageArgs &a, const ImageDesc *
     atomicAnd(w, ~bit);  // off the queue
     Local lc = {0, 0, 0, 0, 0, 0};
     if (block_tests(a, lbl, nN, nW, nE, nS, nNW, nNE, nSE, nSW, nullptr, 0, lc))
-      decide_block_at<true>(a, im, lbl, nN, nW, nE, nS, bx, by, g, lc);
+      decide_block_at<kSched>(a, im, lbl, nN, nW, nE, nS, bx, by, g, lc);
     int *c = s_cnt + ii * 6;
     if (lc.elig) atomicAdd(c + 0, lc.elig);
     if (lc.eval) atomicAdd(c + 1, lc.eval);

@@ -185,6 +185,16 @@ struct StageArgs {
   int wl_cap;         // entries one class can hold (its blocks over all images)
 };
 
+// Which schedule a stage-kernel instantiation runs: the sweeps only, the queue only, or the
+// one a.frontier names (the build with both, whose register allocation measured faster
+// for batches under the sweep schedule).
+enum { kSchedSweeps = 0, kSchedQueue = 1, kSchedRuntime = 2 };
+template <int kSched>
+__device__ __forceinline__ bool queue_schedule(const StageArgs &a) {
+  return kSched == kSchedQueue || (kSched == kSchedRuntime && a.frontier);
+}
+
+
 // Box-sum levels kept for block sums: the method's level factors (> 1) plus 4, 16 and 64
 // when a stage block is at least that large, so a block's colour sum never needs more than
 // a few cells (the sums are exact integers whichever level supplies them).  Returns the
