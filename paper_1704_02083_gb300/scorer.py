@@ -2,8 +2,9 @@
 
 Training data are the move logs of plain runs (rapid_set_logging) on tiles of the 4096^2
 tile's generator and schedule with other seeds; training is rapid_trainer_fit.  The plain
-method is the judge: boundary recall and undersegmentation error against the generator's
-ground truth, and the fraction of pixels whose label differs from the plain run's.
+method is the reference it is measured against: boundary recall and undersegmentation error
+against the generator's ground truth, and the fraction of pixels whose label differs from
+the plain run's.
 """
 from __future__ import annotations
 
