@@ -22,14 +22,20 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in SRC + HDR + [__file__])
 
 
+def compile_to(out: str, sources=SRC) -> str:
+    """Compile the oracle's C sources into the shared library ``out``."""
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-Wall", "-Wextra", "-Wno-unused-parameter", "-o", out] + list(sources) + ["-lm"]
+    subprocess.run(cmd, check=True)
+    return out
+
+
 def build(force: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-Wall", "-Wextra", "-Wno-unused-parameter", "-o", tmp] + SRC + ["-lm"]
-    subprocess.run(cmd, check=True)
+    compile_to(tmp)
     os.replace(tmp, LIB)
     return LIB
 

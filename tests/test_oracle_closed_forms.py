@@ -62,3 +62,24 @@ def test_seed_grid_counts():
     o = oracle.Oracle(synth.flat_image(64, 64), K=4096, init_block=32)  # clamped to 2x2 blocks
     o.seed()
     assert o.grid()["M"] == 4
+
+
+@pytest.mark.parametrize("seed", [0, 3, 5])
+def test_pixel_replicated_image_refines_to_replicated_labels(seed):
+    """lambda_pos per unit of initial superpixel area: replicating every pixel 2 x 2, with
+    blocks twice as large and no boundary term, multiplies the colour part of every energy
+    difference of Eq. equa:energy1 by 4 and its position part by 16 (positions double, Eq.
+    eq:mu; the sub-pixel offsets add a label-independent constant), so only lambda_pos =
+    lambda_pos0 M / (H W), which falls by 4, keeps every decision, move and merge the same.  Pins the position weight's scaling, the position sums and the
+    merge cost's position term."""
+    for rgb, K, b in ((synth.he_image(48, 64, 6, seed).rgb, 12, 8),
+                      (synth.random_image(20, 28, seed, levels=4), 6, 4)):
+        big = np.repeat(np.repeat(rgb, 2, 0), 2, 1)
+        p = dict(K=K, final_grain=1, lambda_b=0.0, lambda_pos0=400.0, size_mode=2)
+        o1 = oracle.Oracle(rgb, init_block=b, **p).run()
+        o2 = oracle.Oracle(big, init_block=2 * b, **{**p, "final_grain": 2}).run()
+        np.testing.assert_array_equal(o2.labels(), np.repeat(np.repeat(o1.labels(), 2, 0), 2, 1))
+        c1, c2 = o1.counters(), o2.counters()
+        np.testing.assert_array_equal(c1[:, 2:], c2[:, 2:])
+        assert c1[:, 5].sum() > 50
+        assert o2.lambda_pos() * 4 == o1.lambda_pos()

@@ -81,28 +81,46 @@ def test_energy_never_rises(size_mode):
     assert prev is not None
 
 
-def test_size_mode_1_respects_bound_per_move():
-    """size_mode 1 (lambda_s = inf, Sec. 3.1 case 2): no executed move takes its superpixel
-    below l * InitSize as judged from the phase's snapshot."""
-    rgb = _image()
+@pytest.mark.parametrize("size_mode,K,seed", [(1, 24, 11), (2, 24, 11), (2, 60, 4), (2, 100, 3)])
+def test_size_rule_against_phase_start_counts(size_mode, K, seed):
+    """Sec. 3.1, judged against the counts at the start of the phase (the snapshot every
+    block of the phase decides against): no executed move takes its superpixel below
+    l * InitSize (case 2, lambda_s infinite, and the merge mode alike), and every merge
+    request comes from a block whose removal would (the merge mode).  Blocks of one label
+    that move in the same phase must not see each other's moves."""
+    rgb = synth.he_image(72, 100, n_cells=8, seed=seed).rgb
     H, W = rgb.shape[:2]
-    o = oracle.Oracle(rgb, K=24, init_block=16, size_mode=1)
+    o = oracle.Oracle(rgb, K=K, init_block=16, size_mode=size_mode)
     o.seed()
+    checked = 0
     for st in range(o.num_stages()):
         if st > 0:
             o.next_stage()
-        for sw in range(4):
+        for sw in range(6):
             for ph in range(9):
-                g = o.grid()
+                side = o.grid()["side"]
                 bl0 = o.block_labels()
                 s0, _, _ = o.stats()
-                o.phase(ph)
+
+                def w(by, bx):
+                    return (min(side * (bx + 1), W) - side * bx) * (min(side * (by + 1), H) - side * by)
+
+                o.phase_moves(ph)
                 bl1 = o.block_labels()
-                side = g["side"]
                 for by, bx in np.argwhere(bl0 != bl1):
                     a = bl0[by, bx]
-                    w = (min(side * (bx + 1), W) - side * bx) * (min(side * (by + 1), H) - side * by)
-                    assert 4 * (s0[a, 0] - w) >= s0[a, 6]
+                    assert 4 * (s0[a, 0] - w(by, bx)) >= s0[a, 6]
+                    checked += 1
+                blk, lab = o.pending_requests()
+                nbx = bl0.shape[1]
+                for b, a in zip(blk.tolist(), lab.tolist()):
+                    by, bx = divmod(b, nbx)
+                    assert bl0[by, bx] == a and 4 * (s0[a, 0] - w(by, bx)) < s0[a, 6]
+                    checked += 1
+                if size_mode == 1:
+                    assert len(blk) == 0
+                o.phase_merges()
+    assert checked > 100
 
 
 def test_counters_consistent():

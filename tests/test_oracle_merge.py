@@ -32,9 +32,12 @@ def ward_exact(s, a, n, lam_pos):
 
 
 @pytest.mark.parametrize("H,W,cells,K,seed", [(96, 128, 10, 40, 3), (96, 128, 10, 40, 7),
-                                              (96, 128, 10, 40, 12), (160, 200, 12, 200, 6)])
+                                              (96, 128, 10, 40, 12), (160, 200, 12, 200, 6),
+                                              (96, 128, 10, 100, 3), (96, 128, 10, 60, 4)])
 def test_merges_rederived(H, W, cells, K, seed):
-    """(160 x 200, K 200, seed 6) contains a phase where two requests pick the same target."""
+    """(160 x 200, K 200, seed 6) contains a phase where two requests pick the same target;
+    in (96 x 128, K 100, seed 3) and (K 60, seed 4) the weight Na Nn / (Na + Nn) changes
+    some request's target (without it another neighbour would be the cheapest)."""
     rgb = synth.he_image(H, W, n_cells=cells, seed=seed).rgb
     o = oracle.Oracle(rgb, K=K, init_block=8, size_mode=2)
     o.seed()
