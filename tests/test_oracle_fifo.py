@@ -1,0 +1,192 @@
+"""The oracle's sequential FIFO variant (Sec. 2.1's boundary queue, Algorithm RAPID's order:
+one block at a time, statistics updated after every move), pinned by a replay in exact
+rational arithmetic on tiny images.
+
+The replay keeps its own label map and statistics.  It rebuilds the queue from the boundary
+blocks in raster order at every stage, pops one block at a time, and decides it from the
+per-pixel energy of Eq. equa:energy1 under the current means (Eq. operation).  It applies
+the size rule of Sec. 3.1 with the current counts, and merges at once into the neighbour
+of least Ward increase within u * InitSize (Eqs. eqa:merge, condtion).  It then queues the
+4-neighbours of a block that changed, in the order N, W, E, S.  It follows the oracle's
+run to the same labels, statistics and counters.  Near ties, which double precision may
+break either way, stop the replay and are counted instead."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import helpers
+import oracle
+from paper_1704_02083_gb300 import synth
+from test_oracle_bruteforce import simple_classical
+
+N4 = ((0, -1), (-1, 0), (1, 0), (0, 1))  # N, W, E, S
+
+
+class NearTie(Exception):
+    pass
+
+
+def _means(S, k):
+    n = S[k][0]
+    return [Fraction(S[k][1 + c], n) for c in range(3)], Fraction(S[k][4], n), Fraction(S[k][5], n)
+
+
+def _block_pixels(bx, by, side, H, W):
+    return [(x, y) for y in range(by * side, min(by * side + side, H)) for x in range(bx * side, min(bx * side + side, W))]
+
+
+def _delta_energy(rgb, full, pix, a, k, S, lam_pos, lam_b):
+    """Energy change of Eq. equa:energy1 when the pixels pix go from label a to k, means
+    fixed: the data terms of those pixels and the unequal 4-adjacent pairs around them."""
+    ca, xa, ya = _means(S, a)
+    ck, xk, yk = _means(S, k)
+    d = Fraction(0)
+    for x, y in pix:
+        I = [int(v) for v in rgb[y, x]]
+        d += sum((I[c] - ck[c]) ** 2 for c in range(3)) + lam_pos * ((x - xk) ** 2 + (y - yk) ** 2)
+        d -= sum((I[c] - ca[c]) ** 2 for c in range(3)) + lam_pos * ((x - xa) ** 2 + (y - ya) ** 2)
+    H, W = full.shape
+    inside = set(pix)
+    before = after = 0
+    for x, y in pix:
+        for dx, dy in N4:
+            u, v = x + dx, y + dy
+            if not (0 <= u < W and 0 <= v < H) or (u, v) in inside:
+                continue
+            q = full[v, u]
+            before += q != a
+            after += q != k
+    return d + 2 * lam_b * (after - before)  # E_b counts each unordered pair from both sides
+
+
+def _ward(S, a, n, lam_pos):
+    ca, xa, ya = _means(S, a)
+    cn, xn, yn = _means(S, n)
+    Na, Nn = S[a][0], S[n][0]
+    return Fraction(Na * Nn, Na + Nn) * (sum((ca[c] - cn[c]) ** 2 for c in range(3))
+                                         + lam_pos * ((xa - xn) ** 2 + (ya - yn) ** 2))
+
+
+def replay(rgb, o, lam_b, size_mode, max_sweeps):
+    """Run the FIFO on the oracle's stage schedule; returns (labels, S, counters)."""
+    H, W = rgb.shape[:2]
+    o.seed()
+    lam_pos = Fraction(o.lambda_pos())
+    stages = o.stages()
+    side = stages[0][1]
+    bl = o.block_labels().copy()  # the seed grid (pinned elsewhere)
+    M = int(bl.max()) + 1
+    S0 = helpers.stats_from_labels(rgb, helpers.upsample(bl, side, H, W), M)
+    S = [[int(v) for v in row] for row in S0]
+    init = [row[0] for row in S]
+    counters = []
+    for si, (level, side) in enumerate(stages):
+        if si > 0:
+            r = stages[si - 1][1] // side
+            bl = np.repeat(np.repeat(bl, r, 0), r, 1)
+            nby, nbx = -(-H // side), -(-W // side)
+            bl = np.ascontiguousarray(bl[:nby, :nbx])
+        nby, nbx = bl.shape
+        full = helpers.upsample(bl, side, H, W).copy()
+        c = dict(pops=0, elig=0, eval=0, moves=0, req=0, merges=0)
+
+        def boundary(bx, by):
+            a = bl[by, bx]
+            return any(0 <= bx + dx < nbx and 0 <= by + dy < nby and bl[by + dy, bx + dx] != a for dx, dy in N4)
+
+        queue = [(bx, by) for by in range(nby) for bx in range(nbx) if boundary(bx, by)]
+        inq = set(queue)
+        head = 0
+        while head < len(queue) and c["pops"] < max_sweeps * nbx * nby:
+            bx, by = queue[head]
+            head += 1
+            inq.discard((bx, by))
+            c["pops"] += 1
+            if not boundary(bx, by):
+                continue
+            c["elig"] += 1
+            if not simple_classical(bl, bx, by):
+                continue
+            c["eval"] += 1
+            a = int(bl[by, bx])
+            pix = _block_pixels(bx, by, side, H, W)
+            cands = sorted({int(bl[by + dy, bx + dx]) for dx, dy in N4
+                            if 0 <= bx + dx < nbx and 0 <= by + dy < nby} - {a})
+            dE = {k: _delta_energy(rgb, full, pix, a, k, S, lam_pos, Fraction(lam_b)) for k in cands}
+            best = min(dE.values())
+            vals = sorted(dE.values())
+            tol = Fraction(1, 10**6)
+            if abs(best) < tol or (len(vals) > 1 and vals[1] - vals[0] < tol):
+                raise NearTie
+            if best >= 0:
+                continue
+            k = min(kk for kk, v in dE.items() if v == best)
+            w = len(pix)
+            if size_mode != 0 and 4 * (S[a][0] - w) < init[a]:
+                if size_mode == 1:
+                    continue
+                c["req"] += 1
+                adj = {int(full[v, u]) for y in range(H) for x in range(W) if full[y, x] == a
+                       for u, v in ((x + dx, y + dy) for dx, dy in N4) if 0 <= u < W and 0 <= v < H} - {a}
+                ok = [n for n in adj if 2 * (S[n][0] + S[a][0]) <= 3 * init[n]]
+                if not ok:
+                    continue
+                wd = {n: _ward(S, a, n, lam_pos) for n in ok}
+                wv = sorted(wd.values())
+                if len(wv) > 1 and wv[1] - wv[0] < tol:
+                    raise NearTie
+                n = min(nn for nn, v in wd.items() if v == wv[0])
+                bl[bl == a] = n
+                full[full == a] = n
+                S[n] = [S[n][i] + S[a][i] for i in range(6)]
+                S[a] = [0] * 6
+                c["merges"] += 1
+            else:
+                bs = [len(pix)] + [sum(int(rgb[y, x, ch]) for x, y in pix) for ch in range(3)] + \
+                     [sum(x for x, _ in pix), sum(y for _, y in pix)]
+                S[a] = [S[a][i] - bs[i] for i in range(6)]
+                S[k] = [S[k][i] + bs[i] for i in range(6)]
+                bl[by, bx] = k
+                for x, y in pix:
+                    full[y, x] = k
+                c["moves"] += 1
+            for dx, dy in N4:
+                q = (bx + dx, by + dy)
+                if 0 <= q[0] < nbx and 0 <= q[1] < nby and q not in inq:
+                    queue.append(q)
+                    inq.add(q)
+        counters.append([level, side, c["pops"], c["elig"], c["eval"], c["moves"], c["req"], c["merges"]])
+    S = np.array([row + [init[i]] for i, row in enumerate(S)], np.int64)
+    return helpers.upsample(bl, stages[-1][1], H, W), S, np.array(counters, np.int64)
+
+
+# the last four contain a merge
+CASES = [(10, 14, 6, 4, s, m, 4, 50.0) for s in range(4) for m in (0, 1, 2)] + \
+        [(9, 12, 4, 2, s, 2, 2, 10.0) for s in range(4)] + [(12, 12, 9, 4, 9, 1, 4, 10.0)] + \
+        [(10, 14, 6, 4, 10, 2, 4, 50.0), (12, 16, 12, 4, 9, 2, 4, 10.0), (16, 16, 16, 4, 9, 2, 4, 5.0),
+         (16, 16, 16, 4, 11, 2, 4, 5.0)]
+DECIDED = []
+
+
+@pytest.mark.parametrize("H,W,K,ib,seed,size_mode,levels,lamb", CASES)
+def test_fifo_follows_its_replay(H, W, K, ib, seed, size_mode, levels, lamb):
+    rgb = synth.random_image(H, W, seed, levels=levels)
+    p = dict(K=K, init_block=ib, size_mode=size_mode, lambda_b=lamb, max_sweeps=8)
+    o = oracle.Oracle(rgb, **p)
+    try:
+        lab, S, cnt = replay(rgb, o, lamb, size_mode, 8)
+    except NearTie:
+        return
+    DECIDED.append((size_mode, int(cnt[:, 5].sum()), int(cnt[:, 7].sum())))
+    f = oracle.Oracle(rgb, **p).run_fifo()
+    np.testing.assert_array_equal(f.labels(), lab)
+    np.testing.assert_array_equal(f.stats()[0], S)
+    np.testing.assert_array_equal(f.counters(), cnt)
+
+
+def test_fifo_replays_cover_moves_and_merges():
+    """Most cases decide without a near tie, and between them they move and merge."""
+    assert len(DECIDED) >= len(CASES) * 3 // 4
+    assert sum(m for _, m, _ in DECIDED) > 100
+    assert sum(g for s, _, g in DECIDED if s == 2) > 0

@@ -35,6 +35,7 @@ FT = "test_oracle_features.py"
 INV = "test_oracle_invariants.py"
 LV = "test_oracle_levels.py"
 MG = "test_oracle_merge.py"
+FF = "test_oracle_fifo.py"
 SP = "test_oracle_simple_point.py"
 
 
@@ -190,6 +191,22 @@ MUTANTS = [
     Mutant("queue_never_pops", "a popped block leaves the queue", "st->queued[blk] = 0;", "", (FR,)),
     Mutant("queue_push_misses_west", "all four neighbours are queued",
            "if (bx > 0) st->queued[blk - 1] = 1;", "", (FR,)),
+]
+
+MUTANTS += [
+    # the sequential FIFO (Sec. 2.1, Algorithm RAPID's order), the quality comparator
+    Mutant("fifo_no_push_after_merge", "a merge re-queues the requesting block's neighbours",
+           "      c[C_MERGES]++;\n    } else {", "      c[C_MERGES]++;\n      continue;\n    } else {", (FF,)),
+    Mutant("fifo_move_skips_statistics", "statistics follow every move at once",
+           "      apply_move(st, i, a, k);\n      c[C_MOVES]++;", "      st->lab[i] = k;\n      c[C_MOVES]++;", (FF,)),
+    Mutant("fifo_queues_duplicates", "a block is on the queue at most once",
+           "      if (inq[ni]) continue;\n", "", (FF,)),
+    Mutant("fifo_push_order_reversed", "neighbours are queued N, W, E, S",
+           "    const int dx[4] = {0, -1, 1, 0}, dy[4] = {-1, 0, 0, 1};\n    for (int j = 0; j < 4; j++) {\n      int32_t nx",
+           "    const int dx[4] = {0, 1, -1, 0}, dy[4] = {1, 0, 0, -1};\n    for (int j = 0; j < 4; j++) {\n      int32_t nx",
+           (FF,)),
+    Mutant("fifo_queues_every_block", "the first queue holds the boundary blocks",
+           "      if (eligible(st, bx, by, label_at(st, bx, by))) {", "      {", (FF,)),
 ]
 
 CONTROL_PINS = tuple(sorted({p for m in MUTANTS for p in m.pins}))
