@@ -67,8 +67,9 @@ def dist_env():
 
 # ---------------------------------------------------------------- CPU sample (oracle legs)
 def cpu_sample(workload: str):
-    """A bounded sample of the workload for the CPU oracle: a 1024 x 1024 tile of the same
-    generator with the same superpixel size and parameters."""
+    """A bounded sample of the workload for the CPU oracle: a tile of at most 1024 x 1024
+    pixels of the same generator with the same superpixel size, region density and
+    parameters (the whole image when it fits)."""
     from paper_1704_02083_gb300 import synth
     if workload in synth.SLIDES:
         sd = synth.SLIDES[workload]
@@ -86,14 +87,14 @@ def cpu_sample(workload: str):
         side_h = side_w = SAMPLE_SIDE
     else:
         w = synth.WORKLOADS[workload]
-        frac = (SAMPLE_SIDE * SAMPLE_SIDE) / float(w["H"] * w["W"])
         side_h, side_w = min(SAMPLE_SIDE, w["H"]), min(SAMPLE_SIDE, w["W"])
+        frac = (side_h * side_w) / float(w["H"] * w["W"])  # 1 when the image fits the sample: the workload itself
         params = dict(w["params"])
         params["K"] = max(1, int(round(params["K"] * frac)))
         cells = max(1, int(round(w["n_cells"] * frac)))
         seed = w["seed"]
     img = synth.he_image(side_h, side_w, cells, seed)
-    desc = (f"{side_w}x{side_h} tile of the same generator (seed {seed}, {cells} regions) and parameters "
+    desc = (f"{side_h}x{side_w} tile of the same generator (seed {seed}, {cells} regions) and parameters "
             f"(K={params['K']}, superpixel size and density as the workload), full schedule")
     return img.rgb, params, desc
 

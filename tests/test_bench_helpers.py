@@ -38,3 +38,24 @@ def test_stage_alg_bytes_both_schedules():
     coarse = types.SimpleNamespace(block=32, level=1, sweeps=6, moves=10, eligible=100)
     nbc = (H // 32) * (W // 32)
     assert bench.stage_alg_bytes(H, W, coarse, lf) == 4 * nbc * 6 + 40 + 12 * (H // 16) * (W // 16)
+
+
+def test_cpu_sample_keeps_the_workload_density():
+    """The CPU legs time a sample with the workload's pixels per superpixel and per region;
+    an image that fits the sample is sampled whole (the workload itself)."""
+    import numpy as np
+
+    from paper_1704_02083_gb300 import synth
+    rgb, params, desc = bench.cpu_sample("he321x481_k200")
+    w = synth.WORKLOADS["he321x481_k200"]
+    assert rgb.shape == (w["H"], w["W"], 3) and params == w["params"]
+    np.testing.assert_array_equal(rgb, synth.workload_image("he321x481_k200").rgb)
+    assert desc.startswith("321x481 tile") and "K=200" in desc
+    rgb, params, desc = bench.cpu_sample("he4096_k4096_l3")
+    w = synth.WORKLOADS["he4096_k4096_l3"]
+    assert rgb.shape == (bench.SAMPLE_SIDE, bench.SAMPLE_SIDE, 3)
+    npx = bench.SAMPLE_SIDE ** 2
+    assert npx / params["K"] == w["H"] * w["W"] / w["params"]["K"]
+    assert f"{round(w['n_cells'] * npx / (w['H'] * w['W']))} regions" in desc
+    rgb, params, _ = bench.cpu_sample("batch64_l3")
+    assert params["K"] == npx // synth.BATCHES["batch64_l3"]["px_per_superpixel"]
