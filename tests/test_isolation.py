@@ -76,3 +76,15 @@ def test_missing_library_fails_loudly(tmp_path):
         "    print('no error')\n" % (ROOT, str(tmp_path / "librapid.so")))
     out = subprocess.run([sys.executable, "-c", prog], capture_output=True, text=True, timeout=300)
     assert out.stdout.strip() == "raised True", out.stdout + out.stderr
+
+
+def test_stored_expected_values_come_from_the_oracle_alone():
+    """The script that writes tests/golden/ imports the oracle and the input generator and
+    nothing of the CUDA path."""
+    code = _code(os.path.join(ROOT, "tests", "golden", "make_golden.py"))
+    imports = re.findall(r"^\s*(?:from\s+(\S+)\s+import\s+(.+)|import\s+(\S+))", code, re.M)
+    mods = {(a, b.strip()) if a else (c, "") for a, b, c in imports}
+    pkg_imports = {m for m in mods if m[0].startswith("paper_1704_02083_gb300")}
+    assert pkg_imports == {("paper_1704_02083_gb300", "synth")}, pkg_imports
+    assert ("oracle", "") in mods
+    assert "librapid" not in code and "Context(" not in code and "rapid_" not in code
