@@ -263,6 +263,35 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
+def golden_parity(workload: str, imgs, ctx, gpath=None):
+    """The refined images' labels and statistics against the oracle's golden hashes
+    (tests/golden/<workload>.json, written by make_golden.py from the oracle alone; a batch
+    keeps one record per tile).  None when there is no record for this workload."""
+    import numpy as np
+
+    gpath = gpath or os.path.join(ROOT, "tests", "golden", f"{workload}.json")
+    if not os.path.exists(gpath):
+        return None
+    g = json.load(open(gpath))
+    records = g["tiles"] if "tiles" in g else [g]
+    if len(records) != len(imgs):
+        return None
+    fields = ("n", "sum_r", "sum_g", "sum_b", "sum_x", "sum_y", "init_size")
+
+    def sha(a):
+        return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+    def matches(i, rec):
+        st_np = ctx.image_stats(i)
+        stats7 = np.stack([st_np[f] for f in fields], 1).astype("<i8")
+        return (sha(imgs[i]) == rec["image_sha256"] and sha(ctx.image_labels(i).astype("<i4")) == rec["labels_sha256"]
+                and sha(stats7) == rec["stats_sha256"])
+
+    ok = all(matches(i, rec) for i, rec in enumerate(records))
+    what = "labels, S" if len(imgs) == 1 else f"labels, S of all {len(imgs)} tiles"
+    return f"bit-exact vs the oracle's golden hashes ({what})" if ok else "MISMATCH vs the oracle's golden hashes"
+
+
 # ---------------------------------------------------------------- arms
 def run_reference(args, rank, world):
     if rank != 0:
@@ -406,16 +435,8 @@ def run_rapid(args, rank, world, local):
     # parity in the same run: the plain path's labels and statistics against the oracle's
     # golden hashes (written by tests/golden/make_golden.py from the oracle alone)
     parity = None
-    gpath = os.path.join(ROOT, "tests", "golden", f"{args.workload}.json")
-    if n == 1 and scorer is None and classifier is None and os.path.exists(gpath):
-        g = json.load(open(gpath))
-        st_np = ctx.image_stats(0)
-        fields = ("n", "sum_r", "sum_g", "sum_b", "sum_x", "sum_y", "init_size")
-        stats7 = np.stack([st_np[f] for f in fields], 1).astype("<i8")
-        sha = lambda a: hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
-        ok = (sha(imgs[0]) == g["image_sha256"] and sha(ctx.image_labels(0).astype("<i4")) == g["labels_sha256"]
-              and sha(stats7) == g["stats_sha256"])
-        parity = "bit-exact vs the oracle's golden hashes (labels, S)" if ok else "MISMATCH vs the oracle's golden hashes"
+    if scorer is None and classifier is None:
+        parity = golden_parity(args.workload, imgs, ctx)
 
     if scorer is not None:  # judged by the plain method: its labels, and the ground truth
         from paper_1704_02083_gb300 import quality, synth

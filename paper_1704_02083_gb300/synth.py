@@ -270,17 +270,20 @@ def batch_sizes(n: int, seed: int):
     return sizes
 
 
+def batch_tile(name: str, i: int):
+    """Tile i of a batch workload: its RGB array and superpixel count K."""
+    b = BATCHES[name]
+    H, W = batch_sizes(b["n"], b["seed"])[i]
+    cells = max(1, (H * W) // b["px_per_cell"])
+    return he_image(H, W, cells, b["seed"] * 1000 + i).rgb, max(1, (H * W) // b["px_per_superpixel"])
+
+
 def batch_workload(name: str, count: int | None = None):
     """The tiles of a batch workload (the first ``count`` when given): RGB arrays and the
     superpixel count K of each."""
-    b = BATCHES[name]
-    sizes = batch_sizes(b["n"], b["seed"])[:count]
-    imgs, K = [], []
-    for i, (H, W) in enumerate(sizes):
-        cells = max(1, (H * W) // b["px_per_cell"])
-        imgs.append(he_image(H, W, cells, b["seed"] * 1000 + i).rgb)
-        K.append(max(1, (H * W) // b["px_per_superpixel"]))
-    return imgs, K
+    n = BATCHES[name]["n"] if count is None else min(count, BATCHES[name]["n"])
+    tiles = [batch_tile(name, i) for i in range(n)]
+    return [t[0] for t in tiles], [t[1] for t in tiles]
 
 
 def workload_image(name: str) -> SynthImage:

@@ -2,8 +2,10 @@
 
 For each full-size workload: SHA-256 of the generated image, of the oracle's full-res
 label map (int32 little-endian, row-major) and of its statistics (M x 7 int64: N, R, G, B,
-X, Y, InitSize), the per-stage counters, and a few sampled labels.  The CUDA path is
-never run here.  Usage: python tests/golden/make_golden.py [workload ...]
+X, Y, InitSize), the per-stage counters, and a few sampled labels.  A batch workload gets
+the same record for each of its tiles, each refined alone (tiles run in parallel worker
+processes).  The CUDA path is never run here.
+Usage: python tests/golden/make_golden.py [workload ...]
 """
 import hashlib
 import json
@@ -26,21 +28,19 @@ def sha(a: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
 
 
-def make(name: str) -> dict:
-    w = synth.WORKLOADS[name]
-    img = synth.workload_image(name)
+def record(rgb: np.ndarray, params: dict, n_samples: int = 64) -> dict:
+    """The oracle's run on one image, as hashes, counters and n_samples sampled labels."""
+    H, W = rgb.shape[:2]
     t = time.time()
-    o = oracle.Oracle(img.rgb, **w["params"]).run()
+    o = oracle.Oracle(rgb, **params).run()
     dt = time.time() - t
     lab = o.labels().astype("<i4")
     s, y, imp = o.stats()
     rng = np.random.default_rng(0)
-    ys = rng.integers(0, w["H"], 64)
-    xs = rng.integers(0, w["W"], 64)
+    ys = rng.integers(0, H, n_samples)
+    xs = rng.integers(0, W, n_samples)
     return {
-        "workload": name,
-        "params": w["params"],
-        "image_sha256": sha(img.rgb),
+        "image_sha256": sha(rgb),
         "labels_sha256": sha(lab),
         "stats_sha256": sha(s.astype("<i8")),
         "y_sha256": sha(y.astype("i1")),
@@ -53,10 +53,38 @@ def make(name: str) -> dict:
     }
 
 
+def make(name: str) -> dict:
+    w = synth.WORKLOADS[name]
+    return {"workload": name, "params": w["params"], **record(synth.workload_image(name).rgb, w["params"])}
+
+
+def _tile(job):
+    name, i = job
+    rgb, K = synth.batch_tile(name, i)
+    return {"tile": i, "H": int(rgb.shape[0]), "W": int(rgb.shape[1]), "K": K,
+            **record(rgb, dict(synth.BATCHES[name]["params"], K=K), n_samples=16)}
+
+
+def make_batch(name: str, workers: int) -> dict:
+    import multiprocessing as mp
+    b = synth.BATCHES[name]
+    jobs = [(name, i) for i in range(b["n"])]
+    sizes = synth.batch_sizes(b["n"], b["seed"])
+    jobs.sort(key=lambda j: -sizes[j[1]][0] * sizes[j[1]][1])  # largest first
+    with mp.get_context("spawn").Pool(workers) as pool:
+        tiles = sorted(pool.map(_tile, jobs, chunksize=1), key=lambda d: d["tile"])
+    return {"workload": name, "params": b["params"], "tiles": tiles}
+
+
 if __name__ == "__main__":
     names = sys.argv[1:] or ["he4096_k4096_l3"]
     for n in names:
-        d = make(n)
+        if n in synth.BATCHES:
+            d = make_batch(n, max(1, min(8, os.cpu_count() or 1)))
+            summary = (len(d["tiles"]), round(sum(t["oracle_seconds_on_writer"] for t in d["tiles"]), 1))
+        else:
+            d = make(n)
+            summary = (d["labels_sha256"][:16], d["oracle_seconds_on_writer"])
         with open(os.path.join(HERE, f"{n}.json"), "w") as f:
-            json.dump(d, f, indent=1)
-        print(n, d["labels_sha256"][:16], d["oracle_seconds_on_writer"], "s")
+            json.dump(d, f, indent=None if "tiles" in d else 1)
+        print(n, *summary)

@@ -59,3 +59,55 @@ def test_cpu_sample_keeps_the_workload_density():
     assert f"{round(w['n_cells'] * npx / (w['H'] * w['W']))} regions" in desc
     rgb, params, _ = bench.cpu_sample("batch64_l3")
     assert params["K"] == npx // synth.BATCHES["batch64_l3"]["px_per_superpixel"]
+
+
+class _OracleCtx:
+    """Stands in for a context: each image's labels and statistics from the oracle."""
+
+    def __init__(self, imgs, params_per_image):
+        import numpy as np
+        import oracle
+
+        self.out = []
+        for rgb, p in zip(imgs, params_per_image):
+            o = oracle.Oracle(rgb, **p).run()
+            s, y, imp = o.stats()
+            st = np.zeros(s.shape[0], [(f, "<i8") for f in ("n", "sum_r", "sum_g", "sum_b", "sum_x", "sum_y",
+                                                             "init_size")])
+            for j, f in enumerate(st.dtype.names):
+                st[f] = s[:, j]
+            self.out.append((o.labels(), st))
+
+    def image_labels(self, i):
+        return self.out[i][0]
+
+    def image_stats(self, i):
+        return self.out[i][1]
+
+
+def test_golden_parity_single_and_batch(tmp_path):
+    import json
+    import sys
+
+    from paper_1704_02083_gb300 import synth
+    sys.path.insert(0, os.path.join(bench.ROOT, "tests", "golden"))
+    import make_golden
+
+    w = synth.WORKLOADS["he321x481_k200"]
+    img = synth.workload_image("he321x481_k200").rgb
+    ctx = _OracleCtx([img], [w["params"]])
+    assert bench.golden_parity("he321x481_k200", [img], ctx) == "bit-exact vs the oracle's golden hashes (labels, S)"
+    ctx.out[0][0][5, 7] += 1
+    assert bench.golden_parity("he321x481_k200", [img], ctx) == "MISMATCH vs the oracle's golden hashes"
+    assert bench.golden_parity("no_such_workload", [img], ctx) is None
+    # a batch record: one entry per tile
+    imgs = [synth.he_image(40, 56, 4, 1).rgb, synth.he_image(33, 20, 3, 2).rgb]
+    params = [dict(K=12, init_block=8), dict(K=5, init_block=4)]
+    path = tmp_path / "b.json"
+    path.write_text(json.dumps({"tiles": [make_golden.record(x, p) for x, p in zip(imgs, params)]}))
+    ctx = _OracleCtx(imgs, params)
+    assert bench.golden_parity("b", imgs, ctx, str(path)) == \
+        "bit-exact vs the oracle's golden hashes (labels, S of all 2 tiles)"
+    ctx.out[1][1]["sum_x"][0] += 1
+    assert bench.golden_parity("b", imgs, ctx, str(path)) == "MISMATCH vs the oracle's golden hashes"
+    assert bench.golden_parity("b", imgs[:1], ctx, str(path)) is None
