@@ -1,0 +1,227 @@
+// eval_sweep.cuh — block decisions of one phase of the sweep schedule, from a bitmap of the
+// blocks of the phase class that may be eligible (included by stage_impl.cuh, inside the
+// shape's namespace).
+//
+// A sweep examines every block of every class (Sec. 2.1: relabel the boundary blocks; the
+// 9-phase reading R10).  Only eligible blocks -- boundary blocks (Eq. bound) of important
+// labels at the finer levels (Eq. new_bound) -- can move, and they are a small share of
+// the grid, so a phase walks a per-class bitmap `cbits` that holds a superset of the
+// class's eligible blocks, kept so by three rules:
+//   * when the stage starts every bit is set;
+//   * a block that is visited and found not eligible has its bit cleared;
+//   * a block whose label changes (a move, or the relabelling of an accepted merge) sets
+//     the bits of its 4-neighbours (its own stays set).
+// Eligibility depends only on the block's label, its 4-neighbours' labels and per-label
+// flags that are fixed during a stage (importance, class y), so a block can become
+// eligible only when a label of its 4-neighbourhood changes, which sets its bit.  Every
+// eligible block is therefore visited in every sweep, and the eligible and evaluated
+// counts equal those of a walk over the whole class.
+//
+// A visited block that passes the tests skips the decision when neither its label nor a
+// 4-neighbour label has changed S since its class's previous phase (g - 9) and it did not
+// request a merge then (`rbits`): a label change in its 3x3 window changes the S of the
+// old and the new label, one of which is then the block's own label or a 4-neighbour
+// label whenever the change reaches the boundary test, the topology mask or the energy.
+// Its window, candidates and snapshot means are then those of the previous phase, whose
+// decision was no move (a move would have changed its own label).
+#pragma once
+
+// Per-warp scratch of the bitmap walk (overlays the warp's WarpTile).
+struct SweepScratch {
+  unsigned bits[32];                // the words the lanes loaded
+  int pre[32];                      // inclusive prefix sums of their set-bit counts
+  unsigned clr[32];                 // bits to clear: blocks found not eligible, bits past the row
+  unsigned req[32];                 // request-memo words as this phase leaves them
+  int img[32], row[32], col0[32];   // image, lattice row and first lattice column of each word
+};
+static_assert(sizeof(SweepScratch) <= sizeof(WarpTile), "the bitmap walk's scratch overlays the warp's tile");
+
+// Block (x, y) of image im may be eligible (no-op outside the block grid).
+__device__ __forceinline__ void sweep_mark(const StageArgs &a, const ImageDesc &im, int x, int y) {
+  if (x < 0 || y < 0 || x >= im.nbx || y >= im.nby) return;
+  const int px = x % 3, i = x / 3;
+  const long long w = (long long)im.cw0[(y % 3) * 3 + px] + (long long)(y / 3) * class_wpr(im.nbx, px) + (i >> 5);
+  atomicOr(a.cbits + w, 1u << (i & 31));
+}
+
+// The 4-neighbours of block (x, y), and the block itself when `self`.
+__device__ __forceinline__ void sweep_mark_plus(const StageArgs &a, const ImageDesc &im, int x, int y, bool self) {
+  if (self) sweep_mark(a, im, x, y);
+  sweep_mark(a, im, x, y - 1);
+  sweep_mark(a, im, x - 1, y);
+  sweep_mark(a, im, x + 1, y);
+  sweep_mark(a, im, x, y + 1);
+}
+
+// Adds a lane's counts to the CTA's per-image shared counters (8 per image: eligible,
+// evaluated, moves, requests, fallbacks, filter mismatches, visited blocks, skipped
+// decisions) and clears them.
+__device__ __forceinline__ void flush_sweep_counts(int *s_cnt, int ii, Local &lc, int &visited, int &skipped) {
+  int *c = s_cnt + ii * 8;
+  if (lc.elig) atomicAdd(c + 0, lc.elig);
+  if (lc.eval) atomicAdd(c + 1, lc.eval);
+  if (lc.moves) atomicAdd(c + 2, lc.moves);
+  if (lc.req) atomicAdd(c + 3, lc.req);
+  if (lc.fallback) atomicAdd(c + 4, lc.fallback);
+  if (lc.mismatch) atomicAdd(c + 5, lc.mismatch);
+  if (visited) atomicAdd(c + 6, visited);
+  if (skipped) atomicAdd(c + 7, skipped);
+  lc = Local{0, 0, 0, 0, 0, 0};
+  visited = skipped = 0;
+}
+
+// The CTA's per-image shared counters into the image counters (after a CTA barrier).
+__device__ __forceinline__ void store_sweep_counts(const StageArgs &a, const int *s_cnt, int nimg, int slot) {
+  for (int i = threadIdx.x; i < nimg; i += blockDim.x) {
+    const int *c = s_cnt + i * 8;
+    long long *cnt = a.ctl.cnt + (long long)i * kCntStride;
+    if (c[0]) atomic_add_i64(&cnt[CNT_ELIG], c[0]);
+    if (c[1]) atomic_add_i64(&cnt[CNT_EVAL], c[1]);
+    if (c[2]) {
+      atomic_add_i64(&cnt[CNT_MOVES], c[2]);
+      atomicAdd(&a.ctl.changes[3 * i + slot], (unsigned long long)c[2]);
+    }
+    if (c[3]) atomic_add_i64(&cnt[CNT_REQ], c[3]);
+    if (c[4]) atomic_add_i64(&cnt[CNT_FALLBACK], c[4]);
+    if (c[5]) atomic_add_i64(&cnt[CNT_MISMATCH], c[5]);
+    if (c[6]) atomic_add_i64(&cnt[CNT_SCANNED], c[6]);
+    if (c[7]) atomic_add_i64(&cnt[CNT_SKIPPED], c[7]);
+  }
+}
+
+// Phase `phase` (class py = phase / 3, px = phase % 3) of sweep `sweep`; g is the phase
+// number in the launch.  The class's words (all images) are split into equal contiguous
+// ranges, one per warp of the grid.  A warp loads up to 32 words at a time (a lane each),
+// spreads their set bits over its lanes (prefix sums in shared memory) and gives each lane
+// one block at a time: tests, then the decision.
+template <bool kBatch, int kSched>
+__device__ __forceinline__ void eval_sweep(const StageArgs &a, const ImageDesc *imgs, const unsigned char *active,
+                                           const unsigned char *pruned, const int *valid_from, WarpTile *wts,
+                                           int *s_cnt, int phase, int g, int slot, int sweep) {
+  const int nimg = kBatch ? a.nimg : 1;
+  for (int i = threadIdx.x; i < nimg * 8; i += blockDim.x) s_cnt[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  SweepScratch &X = *reinterpret_cast<SweepScratch *>(&wts[warp]);
+  const int py = phase / 3, px = phase % 3;
+  const int w_first = a.cwb[phase];
+  const long long nw = (long long)a.cwb[phase + 1] - w_first;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+  const int wb = w_first + (int)(nw * gw / nwarps), we = w_first + (int)(nw * (gw + 1) / nwarps);
+  const int prev2 = 2 * (g - 9);  // stamps >= this changed since the class's previous phase
+  const DevStats &s = a.st;
+  Local lc = {0, 0, 0, 0, 0, 0};
+  int cur = 0, visited = 0, skipped = 0;
+  for (int base = wb; base < we; base += 32) {
+    const int w = base + lane;
+    unsigned word = 0u, rw = 0u;
+    int ii = 0, row = 0, col0 = 0;
+    if (w < we) {
+      if (kBatch) {  // the image: the last one whose class words start at or before w
+        int lo = 0, hi = nimg - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (imgs[mid].cw0[phase] <= w) lo = mid;
+          else hi = mid - 1;
+        }
+        ii = lo;
+      }
+      if (active[ii]) {  // (an image that finished the stage is not visited again)
+        const ImageDesc &im = kBatch ? imgs[ii] : a.img0;
+        word = a.cbits[w];
+        rw = a.rbits[w];
+        const int wpr = class_wpr(im.nbx, px);
+        const int local = w - im.cw0[phase];
+        row = local / wpr;
+        col0 = (local - row * wpr) * 32;
+      }
+    }
+    int pre = __popc(word);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, pre, o);
+      if (lane >= o) pre += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, pre, 31);
+    if (total == 0) continue;  // (warp-uniform)
+    X.bits[lane] = word;
+    X.pre[lane] = pre;
+    X.clr[lane] = 0u;
+    X.req[lane] = rw;
+    X.img[lane] = ii;
+    X.row[lane] = row;
+    X.col0[lane] = col0;
+    __syncwarp();
+    for (int e = lane; e < total; e += 32) {
+      int q = 0;
+      {  // the word that holds set bit number e: the first with a prefix sum above e
+        int lo = 0, hi = 31;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (X.pre[mid] > e) hi = mid;
+          else lo = mid + 1;
+        }
+        q = lo;
+      }
+      const unsigned wq = X.bits[q];
+      const int b = select_bit(wq, e - (X.pre[q] - __popc(wq)));
+      const unsigned bit = 1u << b;
+      const int qi = X.img[q];
+      const ImageDesc &im = kBatch ? imgs[qi] : a.img0;
+      const int bx = px + 3 * (X.col0[q] + b), by = py + 3 * X.row[q];
+      if (bx >= im.nbx) {  // a bit past the last column of the lattice row: no block
+        atomicOr(&X.clr[q], bit);
+        continue;
+      }
+      if (kBatch && qi != cur) {
+        flush_sweep_counts(s_cnt, cur, lc, visited, skipped);
+        cur = qi;
+      }
+      visited++;
+      const int *lab = im.lab;
+      const int nbx = im.nbx;
+      const long long idx = (long long)by * nbx + bx;
+      const bool n_ok = by > 0, s_ok = by + 1 < im.nby, w_ok = bx > 0, e_ok = bx + 1 < nbx;
+      const int lbl = lab[idx];
+      const int nN = n_ok ? lab[idx - nbx] : -1, nS = s_ok ? lab[idx + nbx] : -1;
+      const int nW = w_ok ? lab[idx - 1] : -1, nE = e_ok ? lab[idx + 1] : -1;
+      const int nNW = (n_ok && w_ok) ? lab[idx - nbx - 1] : -1, nNE = (n_ok && e_ok) ? lab[idx - nbx + 1] : -1;
+      const int nSW = (s_ok && w_ok) ? lab[idx + nbx - 1] : -1, nSE = (s_ok && e_ok) ? lab[idx + nbx + 1] : -1;
+      const int e0 = lc.elig;
+      const unsigned char *mask = pruned[qi] ? im.mask : nullptr;
+      const bool need = block_tests(a, lbl, nN, nW, nE, nS, nNW, nNE, nSE, nSW, mask, idx, lc);
+      if (lc.elig == e0) atomicOr(&X.clr[q], bit);  // not eligible: off the bitmap
+      bool req = false;
+      if (need) {
+        bool same = a.skip_tiles && sweep > 0 && g - 9 >= valid_from[qi] && !(X.req[q] & bit);
+        if (same) {
+          same = s.chg[lbl] < prev2;
+          if (nN >= 0) same &= s.chg[nN] < prev2;
+          if (nW >= 0) same &= s.chg[nW] < prev2;
+          if (nE >= 0) same &= s.chg[nE] < prev2;
+          if (nS >= 0) same &= s.chg[nS] < prev2;
+        }
+        if (same) {
+          skipped++;
+        } else {
+          const int m0 = lc.moves;
+          req = decide_block_at<kSched>(a, im, lbl, nN, nW, nE, nS, bx, by, g, lc);
+          if (lc.moves != m0) sweep_mark_plus(a, im, bx, by, false);
+        }
+      }
+      if (req) atomicOr(&X.req[q], bit);
+      else if (X.req[q] & bit) atomicAnd(&X.req[q], ~bit);
+    }
+    __syncwarp();
+    if (w < we && word) {
+      const unsigned c = X.clr[lane];
+      if (c) atomicAnd(a.cbits + w, ~c);
+      if (X.req[lane] != rw) a.rbits[w] = X.req[lane];
+    }
+    __syncwarp();
+  }
+  flush_sweep_counts(s_cnt, cur, lc, visited, skipped);
+  __syncthreads();
+  store_sweep_counts(a, s_cnt, nimg, slot);
+}

@@ -527,12 +527,12 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
 // Frontier schedule, phase class `phase` with nq listed blocks: one thread per listed block
 // (32 consecutive entries per warp, warps spread over the CTAs first), no tile walk.  The
 // listed blocks are exactly the queued blocks of the class; each leaves the queue here.
-// Counts go through the CTA's per-image shared counters s_cnt[image * 6 + ...].
+// Counts go through the CTA's per-image shared counters s_cnt[image * 8 + ...].
 template <bool kBatch, int kSched>
 __device__ __forceinline__ void eval_queue(const StageArgs &a, const ImageDesc *imgs, const unsigned char *active,
                                            int *s_cnt, int phase, int g, int slot, int nq) {
   const int nimg = kBatch ? a.nimg : 1;
-  for (int i = threadIdx.x; i < nimg * 6; i += blockDim.x) s_cnt[i] = 0;
+  for (int i = threadIdx.x; i < nimg * 8; i += blockDim.x) s_cnt[i] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
@@ -586,7 +586,7 @@ __device__ __forceinline__ void eval_queue(const StageArgs &a, const ImageDesc *
     Local lc = {0, 0, 0, 0, 0, 0};
     if (block_tests(a, lbl, nN, nW, nE, nS, nNW, nNE, nSE, nSW, nullptr, 0, lc))
       decide_block_at<kSched>(a, im, lbl, nN, nW, nE, nS, bx, by, g, lc);
-    int *c = s_cnt + ii * 6;
+    int *c = s_cnt + ii * 8;
     if (lc.elig) atomicAdd(c + 0, lc.elig);
     if (lc.eval) atomicAdd(c + 1, lc.eval);
     if (lc.moves) atomicAdd(c + 2, lc.moves);
@@ -596,7 +596,7 @@ __device__ __forceinline__ void eval_queue(const StageArgs &a, const ImageDesc *
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nimg; i += blockDim.x) {
-    const int *c = s_cnt + i * 6;
+    const int *c = s_cnt + i * 8;
     long long *cnt = a.ctl.cnt + (long long)i * kCntStride;
     if (c[0]) atomic_add_i64(&cnt[CNT_ELIG], c[0]);
     if (c[1]) atomic_add_i64(&cnt[CNT_EVAL], c[1]);

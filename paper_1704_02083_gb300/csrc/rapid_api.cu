@@ -80,6 +80,9 @@ struct rapid_ctx {
   int *d_wl;          // frontier worklists (9 * wl_cap) and their 9 counts
   size_t wl_bytes_cap;
   int wl_cap;
+  unsigned *d_cbits, *d_rbits;  // sweep schedule: per-class block bitmaps, sized for the largest stage
+  size_t cbits_cap, rbits_cap;
+  int cwb[RAPID_MAX_STAGES][10];  // per stage: first word of each class's bitmaps (all images)
   // per (stage, image) descriptors
   ImageDesc *h_desc;  // [nstages * nimg]
   ImageDesc *d_desc;
@@ -289,6 +292,12 @@ static void free_image_buffers(rapid_ctx *ctx) {
   cudaFree(ctx->d_wl);
   ctx->d_wl = nullptr;
   ctx->wl_bytes_cap = 0;
+  cudaFree(ctx->d_cbits);
+  ctx->d_cbits = nullptr;
+  ctx->cbits_cap = 0;
+  cudaFree(ctx->d_rbits);
+  ctx->d_rbits = nullptr;
+  ctx->rbits_cap = 0;
   cudaFree(ctx->d_desc);
   ctx->d_desc = nullptr;
   ctx->desc_cap = 0;
@@ -402,6 +411,7 @@ static rapid_status build_descriptors(rapid_ctx *ctx) {
   ctx->h_desc = (ImageDesc *)std::calloc(n, sizeof(ImageDesc));
   if (!ctx->h_desc) return RAPID_ENOMEM;
   if (!grow(&ctx->d_desc, &ctx->desc_cap, n * sizeof(ImageDesc))) return RAPID_ENOMEM;
+  long long words_max = 0;
   for (int s = 0; s < ctx->nstages; s++) {
     const int side = ctx->st_side[s];
     const int f = stage_sum_factor(ctx, side);
@@ -439,7 +449,23 @@ static rapid_status build_descriptors(rapid_ctx *ctx) {
     }
     if (tile0 >= INT_MAX / 9 || blk0 >= INT_MAX) return RAPID_ERANGE;
     ctx->ntiles[s] = (int)tile0;
+    // sweep-schedule bitmaps: class-major, images in order within a class
+    long long w = 0;
+    for (int c = 0; c < 9; c++) {
+      ctx->cwb[s][c] = (int)w;
+      for (int i = 0; i < ctx->nimg; i++) {
+        ImageDesc &d = ctx->h_desc[(size_t)s * ctx->nimg + i];
+        d.cw0[c] = (int)w;
+        w += class_words(d.nbx, d.nby, c);
+        if (w >= INT_MAX) return RAPID_ERANGE;
+      }
+    }
+    ctx->cwb[s][9] = (int)w;
+    words_max = std::max(words_max, w);
   }
+  if (!grow(&ctx->d_cbits, &ctx->cbits_cap, (size_t)words_max * sizeof(unsigned)) ||
+      !grow(&ctx->d_rbits, &ctx->rbits_cap, (size_t)words_max * sizeof(unsigned)))
+    return RAPID_ENOMEM;
   if (cudaMemcpy(ctx->d_desc, ctx->h_desc, n * sizeof(ImageDesc), cudaMemcpyHostToDevice) != cudaSuccess)
     return cuda_fail(ctx);
   return RAPID_OK;
@@ -594,6 +620,9 @@ static StageArgs stage_args(rapid_ctx *ctx, int s) {
   a.wl = ctx->d_wl;
   a.wl_count = ctx->d_wl ? ctx->d_wl + (size_t)ctx->wl_cap * 9 : nullptr;
   a.wl_cap = ctx->wl_cap;
+  a.cbits = ctx->d_cbits;
+  a.rbits = ctx->d_rbits;
+  for (int c = 0; c < 10; c++) a.cwb[c] = ctx->cwb[s][c];
   return a;
 }
 

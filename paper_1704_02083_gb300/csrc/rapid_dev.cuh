@@ -155,6 +155,8 @@ struct ImageDesc {
   double lam_pos;
   float lam_pos_f;
   float pad2;
+  int cw0[9];         // sweep schedule: first word of this image's bitmap of each phase class
+  int pad3;
 };
 
 struct StageArgs {
@@ -183,6 +185,11 @@ struct StageArgs {
                       // their class's last phase (each listed once)
   int *wl_count;      // [9] entries of each class's worklist
   int wl_cap;         // entries one class can hold (its blocks over all images)
+  // sweep schedule: per phase class, one bit per block of the class lattice (class_words
+  // below), class-major over the images: class c's words are [cwb[c], cwb[c + 1])
+  unsigned *cbits;    // 1 = the block may be eligible (a superset of the eligible blocks)
+  unsigned *rbits;    // 1 = the block requested a merge at its last evaluation
+  int cwb[10];
 };
 
 // Which schedule a stage-kernel instantiation runs: the sweeps only, the queue only, or the
@@ -194,6 +201,42 @@ __device__ __forceinline__ bool queue_schedule(const StageArgs &a) {
   return kSched == kSchedQueue || (kSched == kSchedRuntime && a.frontier);
 }
 
+
+// Sweep-schedule bitmaps.  Phase class c = py * 3 + px holds the blocks (px + 3 i, py + 3 j)
+// of a block grid nbx x nby, i < class_cols, j < class_rows; lattice row j is class_wpr
+// 32-bit words, bit (i & 31) of word j * class_wpr + i / 32.  Bits past class_cols in a
+// row's last word belong to no block.
+__host__ __device__ inline int class_cols(int nbx, int px) { return nbx > px ? (nbx - px + 2) / 3 : 0; }
+__host__ __device__ inline int class_rows(int nby, int py) { return nby > py ? (nby - py + 2) / 3 : 0; }
+__host__ __device__ inline int class_wpr(int nbx, int px) { return (class_cols(nbx, px) + 31) >> 5; }
+__host__ __device__ inline long long class_words(int nbx, int nby, int c) {
+  return (long long)class_rows(nby, c / 3) * class_wpr(nbx, c % 3);
+}
+
+__host__ __device__ inline int popc32(unsigned v) {
+#ifdef __CUDA_ARCH__
+  return __popc(v);
+#else
+  int c = 0;
+  for (; v; v &= v - 1u) c++;
+  return c;
+#endif
+}
+
+// Position of the k-th (0-based) set bit of m, which has more than k set bits: a binary
+// search over the halves by their set-bit counts.
+__host__ __device__ inline int select_bit(unsigned m, int k) {
+  int pos = 0;
+  for (int h = 16; h > 0; h >>= 1) {
+    const int c = popc32(m & ((1u << h) - 1u));
+    if (k >= c) {
+      k -= c;
+      m >>= h;
+      pos += h;
+    }
+  }
+  return pos;
+}
 
 // Box-sum levels kept for block sums: the method's level factors (> 1) plus 4, 16 and 64
 // when a stage block is at least that large, so a block's colour sum never needs more than

@@ -48,19 +48,49 @@ constexpr int kMaxLevelsStatic = 8;
 __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
 
 std::mutex g_setup_mutex;
-unsigned char *g_scratch_addr[kMaxDevices];  // device address of g_scratch per device
+unsigned char *g_scratch_addr[kMaxDevices];    // device address of g_scratch per device
+unsigned long long g_scratch_ctx[kMaxDevices];  // id of the context it was looked up in
 
-// Device address of g_scratch on the current device, looked up once per device.  In host
-// code the name g_scratch is only a host-side stand-in, never a device address.
+// Unique id of the calling thread's current context (ids are never reused in a process),
+// through the driver entry points the runtime hands out; 0 when unavailable.
+unsigned long long current_context_id() {
+  typedef int (*GetCurrent)(void **);
+  typedef int (*GetId)(void *, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = (GetCurrent)f1;
+      get_id = (GetId)f2;
+    }
+    looked_up = true;
+  }
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of g_scratch on the current device, looked up at the first call on each
+// device (with that device current) and again whenever the device's context is a new one
+// (after cudaDeviceReset the module is loaded again and the array moves).  In host code the
+// name g_scratch is only a host-side stand-in, never a device address.
 rapid_status scratch_on_current_device(unsigned char **out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RAPID_ECUDA;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  const unsigned long long id = current_context_id();  // 0 before the runtime made a context current
+  if (!g_scratch_addr[dev] || id == 0 || id != g_scratch_ctx[dev]) {
     void *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess || p == nullptr) return RAPID_ECUDA;
     g_scratch_addr[dev] = (unsigned char *)p;
+    g_scratch_ctx[dev] = current_context_id();
   }
   *out = g_scratch_addr[dev];
   return RAPID_OK;
@@ -97,7 +127,9 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   if (p->K < 1 || p->size_mode < 0 || p->size_mode > 2 || p->max_sweeps < 1) return RAPID_EINVAL;
   if (p->lo_den <= 0 || p->hi_den <= 0 || p->lo_num < 0 || p->hi_num < 0) return RAPID_EINVAL;
   if (!std::isfinite(p->lambda_pos0) || !std::isfinite(p->lambda_b)) return RAPID_EINVAL;
-  if ((p->predict | p->reuse | p->importance_rule | p->schedule) & ~1) return RAPID_EINVAL;
+  if ((p->predict | p->reuse | p->importance_rule | p->schedule | p->use_filter | p->skip_tiles | p->verify_filter) &
+      ~1)
+    return RAPID_EINVAL;
   if (p->spin_limit_ns < 0 || p->h_T < 0 || p->h_T > (1ll << 40)) return RAPID_EINVAL;
   if ((long long)H * W > RAPID_STATIC_MAX_PIXELS) return RAPID_ERANGE;
   cudaStream_t stream = (cudaStream_t)cuda_stream;
@@ -165,6 +197,15 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
                         : nullptr;
   const int wl_cap = ((cdiv(W, side[nst - 1]) + 2) / 3) * ((cdiv(H, side[nst - 1]) + 2) / 3);
   int *wl = p->schedule == 1 ? (int *)cv.take(((size_t)wl_cap * 9 + 16) * sizeof(int)) : nullptr;
+  // sweep-schedule bitmaps, sized for the largest stage
+  long long words_max = 0;
+  for (int i = 0; i < nst; i++) {
+    long long w = 0;
+    for (int c = 0; c < 9; c++) w += class_words(cdiv(W, side[i]), cdiv(H, side[i]), c);
+    if (w > words_max) words_max = w;
+  }
+  unsigned *cbits = (unsigned *)cv.take((size_t)words_max * sizeof(unsigned));
+  unsigned *rbits = (unsigned *)cv.take((size_t)words_max * sizeof(unsigned));
   ImageDesc *d_desc = (ImageDesc *)cv.take((size_t)nst * sizeof(ImageDesc));
   DevStats st;
   DevMerge mg;
@@ -172,7 +213,7 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   std::memset(&mg, 0, sizeof mg);
   const size_t lbytes = label_arrays_bytes(M);
   void *lblock = cv.take(lbytes);
-  bool ok = ctl && lab[0] && lab[1] && trec && d_desc && lblock && ((qbits && wl) || p->schedule != 1);
+  bool ok = ctl && lab[0] && lab[1] && trec && cbits && rbits && d_desc && lblock && ((qbits && wl) || p->schedule != 1);
   for (int l = 0; l < nsf; l++) ok = ok && pyr[l];
   if (!ok) return RAPID_ERANGE;  // this image and parameter set need more than the fixed array
   carve_label_arrays(lblock, lbytes, M, &st, &mg);
@@ -218,6 +259,11 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
     d.lab = lab[i & 1];
     d.lam_pos = lam_pos;
     d.lam_pos_f = (float)lam_pos;
+    int w = 0;
+    for (int c = 0; c < 9; c++) {
+      d.cw0[c] = w;
+      w += (int)class_words(d.nbx, d.nby, c);
+    }
   }
 
   // Cooperative grid size for the stage kernel (no allocation involved).
@@ -270,6 +316,8 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   a.wl_cap = wl_cap;
   a.verify_filter = p->verify_filter;
   a.skip_tiles = p->skip_tiles;
+  a.cbits = cbits;
+  a.rbits = rbits;
   int launches = 0;
   auto set_stage = [&](int i) {
     a.side = side[i];
@@ -281,6 +329,8 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
     a.ntiles = desc[i].ntx * desc[i].nty;
     a.ctl = c;
     a.ctl.cnt = c.cnt + (long long)CNT_N * i;
+    for (int cl9 = 0; cl9 < 9; cl9++) a.cwb[cl9] = desc[i].cw0[cl9];
+    a.cwb[9] = desc[i].cw0[8] + (int)class_words(desc[i].nbx, desc[i].nby, 8);
   };
   set_stage(0);
   const int gxa[1] = {gx}, gya[1] = {gy};

@@ -174,6 +174,14 @@ __device__ __forceinline__ float eps64(const float4 &h, const float2 &hy, float 
 }
 
 #include "eval_tile.cuh"
+#include "eval_sweep.cuh"
+
+// The sweep schedule walks the per-class bitmaps (eval_sweep.cuh); the queue schedule pops
+// its queue by tiles or worklists (eval_tile.cuh).
+template <int kSched>
+__device__ __forceinline__ bool sweep_schedule(const StageArgs &a) {
+  return kSched == kSchedSweeps || (kSched == kSchedRuntime && !a.frontier);
+}
 
 // Refresh the snapshot means and counts of the labels the phase's moves changed (S itself
 // already holds the moves) and stamp them (2g).
@@ -497,9 +505,14 @@ __device__ __forceinline__ void merge_apply(const StageArgs &a, const ImageDesc 
     const int bx0 = ba.x / a.side, bx1 = ba.z / a.side, by0 = ba.y / a.side, by1 = ba.w / a.side;
     const int bw = bx1 - bx0 + 1;
     const long long total = (long long)bw * (by1 - by0 + 1);
+    const bool marks = sweep_schedule<kSched>(a);
     for (long long t = threadIdx.x; t < total; t += blockDim.x) {
-      const long long idx = (long long)(by0 + (int)(t / bw)) * im.nbx + bx0 + (int)(t % bw);
-      if (im.lab[idx] == al) im.lab[idx] = n;
+      const int cx = bx0 + (int)(t % bw), cy = by0 + (int)(t / bw);
+      const long long idx = (long long)cy * im.nbx + cx;
+      if (im.lab[idx] == al) {
+        im.lab[idx] = n;
+        if (marks) sweep_mark_plus(a, im, cx, cy, true);  // the cell and its 4-neighbours may turn eligible
+      }
     }
   }
 }
@@ -533,7 +546,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
   __shared__ int s_tile0[kImgs], s_label0[kImgs];
   __shared__ unsigned char s_active[kImgs], s_pruned[kImgs];
   __shared__ int s_valid_from[kImgs];
-  __shared__ int s_cnt[kImgs * 6];
+  __shared__ int s_cnt[kImgs * 8];
   __shared__ int s_draw, s_any;
   unsigned epoch = 0;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
@@ -557,6 +570,12 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
   }
   const long long nrec = (long long)a.ntiles * 9;
   for (long long i = gtid; i < nrec; i += gstride) a.trec[i * kRecInts] = 0;
+  if (sweep_schedule<kSched>(a)) {  // sweep schedule: every block may be eligible when the stage starts
+    for (int i = gtid; i < a.cwb[9]; i += gstride) {
+      a.cbits[i] = ~0u;
+      a.rbits[i] = 0u;
+    }
+  }
   if (queue_schedule<kSched>(a)) {  // frontier schedule: every block is queued when the stage starts
     for (long long i = gtid; i < nrec * kQueueWords; i += gstride) a.qbits[i] = ~0u;
     if (gtid < 9) a.wl_count[gtid] = 0;  // blocks queued from the start are not listed
@@ -572,14 +591,14 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
       g++;
       // frontier schedule: after the first sweep every queued block is on its class's list;
       // a short list is worked off one thread per block, a long one by the tile walk
-      if constexpr (kSched != kSchedSweeps) {
-        const int nq = (queue_schedule<kSched>(a) && sweep > 0) ? ld_volatile_i32(a.wl_count + ph) : INT_MAX;
+      if (sweep_schedule<kSched>(a)) {
+        eval_sweep<kBatch, kSched>(a, s_img, s_active, s_pruned, s_valid_from, wts, s_cnt, ph, g, slot, sweep);
+      } else if constexpr (kSched != kSchedSweeps) {
+        const int nq = sweep > 0 ? ld_volatile_i32(a.wl_count + ph) : INT_MAX;
         if (nq <= 4 * (int)(gridDim.x * blockDim.x))
           eval_queue<kBatch, kSched>(a, s_img, s_active, s_cnt, ph, g, slot, nq);
         else
           eval_phase<kBatch, kSched>(a, s_img, s_tile0, s_active, s_pruned, s_valid_from, wts, &s_draw, ph, g, slot);
-      } else {
-        eval_phase<kBatch, kSched>(a, s_img, s_tile0, s_active, s_pruned, s_valid_from, wts, &s_draw, ph, g, slot);
       }
 
       tm.lap(PROF_EVAL);
