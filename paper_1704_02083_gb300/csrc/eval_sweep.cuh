@@ -26,6 +26,9 @@
 // decision was no move (a move would have changed its own label).
 #pragma once
 
+// Blocks a lane tests at once: their loads are issued together.
+constexpr int kPer = kThreads >= 1024 ? 2 : 4;
+
 // Per-warp scratch of the bitmap walk (overlays the warp's WarpTile).
 struct SweepScratch {
   unsigned bits[32];                // the words the lanes loaded
@@ -33,8 +36,39 @@ struct SweepScratch {
   unsigned clr[32];                 // bits to clear: blocks found not eligible, bits past the row
   unsigned req[32];                 // request-memo words as this phase leaves them
   int img[32], row[32], col0[32];   // image, lattice row and first lattice column of each word
+  int dec[32 * kPer];               // blocks that need a decision: word << 5 | bit
 };
 static_assert(sizeof(SweepScratch) <= sizeof(WarpTile), "the bitmap walk's scratch overlays the warp's tile");
+
+// The word that holds set bit number e of the warp's words: the first whose prefix sum
+// exceeds e.
+__device__ __forceinline__ int word_of_entry(const SweepScratch &X, int e) {
+  int lo = 0, hi = 31;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (X.pre[mid] > e) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Labels of block (x, y) and its 8 neighbours: own, N, W, E, S, NW, NE, SE, SW (-1 outside
+// the grid).
+__device__ __forceinline__ void load_window(const ImageDesc &im, int x, int y, int *l) {
+  const int *lab = im.lab;
+  const int nbx = im.nbx;
+  const long long idx = (long long)y * nbx + x;
+  const bool n_ok = y > 0, s_ok = y + 1 < im.nby, w_ok = x > 0, e_ok = x + 1 < nbx;
+  l[0] = lab[idx];
+  l[1] = n_ok ? lab[idx - nbx] : -1;
+  l[2] = w_ok ? lab[idx - 1] : -1;
+  l[3] = e_ok ? lab[idx + 1] : -1;
+  l[4] = s_ok ? lab[idx + nbx] : -1;
+  l[5] = (n_ok && w_ok) ? lab[idx - nbx - 1] : -1;
+  l[6] = (n_ok && e_ok) ? lab[idx - nbx + 1] : -1;
+  l[7] = (s_ok && e_ok) ? lab[idx + nbx + 1] : -1;
+  l[8] = (s_ok && w_ok) ? lab[idx + nbx - 1] : -1;
+}
 
 // Block (x, y) of image im may be eligible (no-op outside the block grid).
 __device__ __forceinline__ void sweep_mark(const StageArgs &a, const ImageDesc &im, int x, int y) {
@@ -153,65 +187,112 @@ __device__ __forceinline__ void eval_sweep(const StageArgs &a, const ImageDesc *
     X.row[lane] = row;
     X.col0[lane] = col0;
     __syncwarp();
-    for (int e = lane; e < total; e += 32) {
-      int q = 0;
-      {  // the word that holds set bit number e: the first with a prefix sum above e
-        int lo = 0, hi = 31;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (X.pre[mid] > e) hi = mid;
-          else lo = mid + 1;
-        }
-        q = lo;
-      }
-      const unsigned wq = X.bits[q];
-      const int b = select_bit(wq, e - (X.pre[q] - __popc(wq)));
-      const unsigned bit = 1u << b;
-      const int qi = X.img[q];
-      const ImageDesc &im = kBatch ? imgs[qi] : a.img0;
-      const int bx = px + 3 * (X.col0[q] + b), by = py + 3 * X.row[q];
-      if (bx >= im.nbx) {  // a bit past the last column of the lattice row: no block
-        atomicOr(&X.clr[q], bit);
-        continue;
-      }
-      if (kBatch && qi != cur) {
-        flush_sweep_counts(s_cnt, cur, lc, visited, skipped);
-        cur = qi;
-      }
-      visited++;
-      const int *lab = im.lab;
-      const int nbx = im.nbx;
-      const long long idx = (long long)by * nbx + bx;
-      const bool n_ok = by > 0, s_ok = by + 1 < im.nby, w_ok = bx > 0, e_ok = bx + 1 < nbx;
-      const int lbl = lab[idx];
-      const int nN = n_ok ? lab[idx - nbx] : -1, nS = s_ok ? lab[idx + nbx] : -1;
-      const int nW = w_ok ? lab[idx - 1] : -1, nE = e_ok ? lab[idx + 1] : -1;
-      const int nNW = (n_ok && w_ok) ? lab[idx - nbx - 1] : -1, nNE = (n_ok && e_ok) ? lab[idx - nbx + 1] : -1;
-      const int nSW = (s_ok && w_ok) ? lab[idx + nbx - 1] : -1, nSE = (s_ok && e_ok) ? lab[idx + nbx + 1] : -1;
-      const int e0 = lc.elig;
-      const unsigned char *mask = pruned[qi] ? im.mask : nullptr;
-      const bool need = block_tests(a, lbl, nN, nW, nE, nS, nNW, nNE, nSE, nSW, mask, idx, lc);
-      if (lc.elig == e0) atomicOr(&X.clr[q], bit);  // not eligible: off the bitmap
-      bool req = false;
-      if (need) {
-        bool same = a.skip_tiles && sweep > 0 && g - 9 >= valid_from[qi] && !(X.req[q] & bit);
-        if (same) {
-          same = s.chg[lbl] < prev2;
-          if (nN >= 0) same &= s.chg[nN] < prev2;
-          if (nW >= 0) same &= s.chg[nW] < prev2;
-          if (nE >= 0) same &= s.chg[nE] < prev2;
-          if (nS >= 0) same &= s.chg[nS] < prev2;
-        }
-        if (same) {
-          skipped++;
-        } else {
-          const int m0 = lc.moves;
-          req = decide_block_at<kSched>(a, im, lbl, nN, nW, nE, nS, bx, by, g, lc);
-          if (lc.moves != m0) sweep_mark_plus(a, im, bx, by, false);
+    // Up to kPer * 32 set bits at a time: each lane first runs the tests of kPer blocks
+    // (their window loads, then their flag loads, issued together), and the blocks that need
+    // a decision are compacted into X.dec and shared out again, one per lane at a time.
+    for (int c0 = 0; c0 < total; c0 += 32 * kPer) {
+      int qv[kPer], bv[kPer], xv[kPer], yv[kPer];
+      int L[kPer][9];  // label, N, W, E, S, NW, NE, SE, SW (-1 outside the grid)
+      bool okv[kPer];
+#pragma unroll
+      for (int u = 0; u < kPer; u++) {
+        const int e = c0 + u * 32 + lane;
+        okv[u] = false;
+        qv[u] = bv[u] = xv[u] = yv[u] = 0;
+        if (e < total) {
+          const int q = word_of_entry(X, e);
+          const unsigned wq = X.bits[q];
+          const int b = select_bit(wq, e - (X.pre[q] - __popc(wq)));
+          const ImageDesc &im = kBatch ? imgs[X.img[q]] : a.img0;
+          qv[u] = q;
+          bv[u] = b;
+          xv[u] = px + 3 * (X.col0[q] + b);
+          yv[u] = py + 3 * X.row[q];
+          if (xv[u] >= im.nbx) atomicOr(&X.clr[q], 1u << b);  // a bit past the row's last column: no block
+          else okv[u] = true;
         }
       }
-      if (req) atomicOr(&X.req[q], bit);
-      else if (X.req[q] & bit) atomicAnd(&X.req[q], ~bit);
+#pragma unroll
+      for (int u = 0; u < kPer; u++) {
+        if (!okv[u]) continue;
+        const ImageDesc &im = kBatch ? imgs[X.img[qv[u]]] : a.img0;
+        load_window(im, xv[u], yv[u], L[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kPer; u++) {  // what the tests and the skip check read next
+        if (!okv[u]) continue;
+        if (a.imp_on) prefetch_l1(s.imp + L[u][0]);
+#pragma unroll
+        for (int t = 0; t < 5; t++)
+          if (L[u][t] >= 0) prefetch_l1(s.chg + L[u][t]);
+      }
+      int nd = 0;
+#pragma unroll
+      for (int u = 0; u < kPer; u++) {
+        bool dec = false;
+        if (okv[u]) {
+          const int q = qv[u], qi = X.img[q];
+          const unsigned bit = 1u << bv[u];
+          const ImageDesc &im = kBatch ? imgs[qi] : a.img0;
+          if (kBatch && qi != cur) {
+            flush_sweep_counts(s_cnt, cur, lc, visited, skipped);
+            cur = qi;
+          }
+          visited++;
+          const int *l = L[u];
+          const int e0 = lc.elig;
+          const unsigned char *mask = pruned[qi] ? im.mask : nullptr;
+          const long long idx = (long long)yv[u] * im.nbx + xv[u];
+          const bool need = block_tests(a, l[0], l[1], l[2], l[3], l[4], l[5], l[6], l[7], l[8], mask, idx, lc);
+          if (lc.elig == e0) atomicOr(&X.clr[q], bit);  // not eligible: off the bitmap
+          const bool memo = (X.req[q] & bit) != 0;
+          if (memo) atomicAnd(&X.req[q], ~bit);  // set again below if it requests again
+          if (need) {
+            bool same = a.skip_tiles && sweep > 0 && g - 9 >= valid_from[qi] && !memo;
+            if (same) {
+#pragma unroll
+              for (int t = 0; t < 5; t++)
+                if (l[t] >= 0) same &= s.chg[l[t]] < prev2;
+            }
+            if (same) skipped++;
+            else dec = true;
+          }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, dec);
+        if (dec) X.dec[nd + __popc(bal & ((1u << lane) - 1u))] = (qv[u] << 5) | bv[u];
+        nd += __popc(bal);
+      }
+      __syncwarp();
+      for (int d = lane; d < nd; d += 32) {
+        const int q = X.dec[d] >> 5, b = X.dec[d] & 31, qi = X.img[q];
+        const ImageDesc &im = kBatch ? imgs[qi] : a.img0;
+        if (kBatch && qi != cur) {
+          flush_sweep_counts(s_cnt, cur, lc, visited, skipped);
+          cur = qi;
+        }
+        const int bx = px + 3 * (X.col0[q] + b), by = py + 3 * X.row[q];
+        const long long idx = (long long)by * im.nbx + bx;
+        const int *lab = im.lab;
+        const int lbl = lab[idx];
+        const int nN = by > 0 ? lab[idx - im.nbx] : -1, nS = by + 1 < im.nby ? lab[idx + im.nbx] : -1;
+        const int nW = bx > 0 ? lab[idx - 1] : -1, nE = bx + 1 < im.nbx ? lab[idx + 1] : -1;
+        // the decision's reads (snapshot means, counts, the block's pixels), fetched together
+        const int nb5[5] = {lbl, nN, nW, nE, nS};
+#pragma unroll
+        for (int t = 0; t < 5; t++)
+          if (nb5[t] >= 0 && (t == 0 || nb5[t] != lbl)) {
+            prefetch_l1(s.fhi + nb5[t]);
+            prefetch_l1(s.flo + nb5[t]);
+            prefetch_l1(s.fy + nb5[t]);
+          }
+        prefetch_l1(s.mN + lbl);
+        prefetch_l1(s.init + lbl);
+        if (a.f == 1) prefetch_l1(im.img + (long long)by * a.side * im.img_pitch + 3ll * bx * a.side);
+        const int m0 = lc.moves;
+        if (decide_block_at<kSched>(a, im, lbl, nN, nW, nE, nS, bx, by, g, lc)) atomicOr(&X.req[q], 1u << b);
+        if (lc.moves != m0) sweep_mark_plus(a, im, bx, by, false);
+      }
+      __syncwarp();
     }
     __syncwarp();
     if (w < we && word) {

@@ -76,13 +76,14 @@ __device__ __forceinline__ int decide(const StageArgs &a, const ImageDesc &im, c
   const float pby = (float)in.y0 + 0.5f * (float)(bs.bh - 1);
   const float lamf = im.lam_pos_f, lamb2f = a.lam_b2_f;
   const float rlam = 1.0001f * kU * lamf, rlamb = 1.0001f * kU * lamb2f;  // |float - binary64| weights
-  const float4 ha = s.fhi[lbl], la = s.flo[lbl];
+  const float4 ha = s.fhi[lbl];
   const float2 ya = s.fy[lbl];
   int Ba = 0;
   if (in.nb[0] >= 0 && in.nb[0] != lbl) Ba += bs.bw;
   if (in.nb[1] >= 0 && in.nb[1] != lbl) Ba += bs.bh;
   if (in.nb[2] >= 0 && in.nb[2] != lbl) Ba += bs.bh;
   if (in.nb[3] >= 0 && in.nb[3] != lbl) Ba += bs.bw;
+  const float4 la = s.flo[lbl];
   const float eps_a = eps64(ha, ya, wf, r2f, g2f, b2f, x2f, y2f, lamf, lamb2f, (float)Ba);
 
   int bk = -1;
