@@ -272,6 +272,22 @@ rapid_status rapid_read_features(rapid_ctx *ctx, int32_t i, double *dst_host);
  * against it); with threshold 0 they are the same.  Synchronises. */
 rapid_status rapid_set_scorer(rapid_ctx *ctx, const float *weights, float threshold);
 
+/* Pruned refinement with keep masks the caller gives instead of the scorer's: the same
+ * pruned sweeps as rapid_set_scorer runs (a stage sweeps testing and deciding only the kept
+ * eligible blocks until a sweep changes nothing, then sweeps every block until a sweep
+ * changes nothing, within max_sweeps), with the boundary-superpixel pruning of Sec. 3.2
+ * generalised to an arbitrary per-block mask.  It lets the pruned machinery be checked
+ * against a reference on the same masks, and serves callers with a pruning rule of their
+ * own.  mask: image i's mask for stage s, n = nbx * nby bytes of that stage's block grid
+ * (row-major, nonzero = kept), host memory or device memory by mask_is_device (1), copied
+ * before return.  A stage with a mask set for any image sweeps pruned; the images without
+ * one at that stage keep every block.  rapid_set_keep_mask(ctx, -1, -1, NULL, 0, 0) clears
+ * every mask; rapid_set_images clears them too.  ESTATE before rapid_set_images; EINVAL on
+ * a wrong size, image or stage index, under the queue schedule (schedule 1) or while a
+ * scorer is set (rapid_set_scorer likewise refuses while masks are set).  Synchronises. */
+rapid_status rapid_set_keep_mask(rapid_ctx *ctx, int32_t i, int32_t s, const uint8_t *mask, int64_t n,
+                                 int32_t mask_is_device);
+
 /* The current stage's features of image i ([nby][nbx][RAPID_SCORER_FEATURES] fp32, device
  * buffer dst of nby*nbx*9 floats), and scores ([nby][nbx] fp32, device buffer) under the
  * given weights (host).  Stream-ordered.  ESTATE before seeding. */
@@ -288,7 +304,9 @@ rapid_status rapid_scorer_scores(rapid_ctx *ctx, int32_t i, const float *weights
  * `batch` over `epochs` shuffled passes (shuffle seeded by `seed`), starting from `init`
  * (host, NULL = a seeded random start) and writes the weights to `weights_out` (host) and
  * the mean loss of each epoch to `epoch_loss` (host, `epochs` floats, may be NULL).
- * Synchronises. */
+ * Both are deterministic: samples take their slots in a fixed order (not by thread
+ * timing), and gradients are summed in a fixed order, so the same runs and the same seed
+ * give bit-identical weights.  Synchronises. */
 typedef struct rapid_trainer rapid_trainer;
 rapid_status rapid_trainer_create(int64_t capacity, float neg_rate, rapid_trainer **out);
 rapid_status rapid_set_logging(rapid_ctx *ctx, rapid_trainer *t);
@@ -296,6 +314,25 @@ rapid_status rapid_trainer_count(rapid_trainer *t, int64_t *samples, int64_t *po
 rapid_status rapid_trainer_fit(rapid_trainer *t, int32_t epochs, int32_t batch, float lr, float pos_weight,
                                uint64_t seed, const float *init, float *weights_out, float *epoch_loss);
 void rapid_trainer_destroy(rapid_trainer *t);
+
+/* The stored samples first .. first + count - 1 (in the order logging appended them:
+ * logged stage by logged stage, image by image, blocks in row-major order, so the same
+ * runs log the same samples in the same slots): their feature patches (count x 7 x 7 x 9
+ * floats, host x_out), in-image masks (bit p = patch position p is inside the image, host
+ * inb_out) and labels (host y_out); any of the three may be NULL.  ERANGE past the stored
+ * samples.  Synchronises. */
+rapid_status rapid_trainer_samples(rapid_trainer *t, int64_t first, int32_t count, float *x_out, uint64_t *inb_out,
+                                   float *y_out);
+
+/* The gradient rapid_trainer_fit follows, for checking it: the sum over the samples first
+ * .. first + count - 1 of the gradient of their loss (as in rapid_trainer_fit) at the master
+ * weights `weights` (host, RAPID_SCORER_PARAMS floats; bf16-rounded for the forward pass as
+ * in training), written to grad_out (host, RAPID_SCORER_PARAMS floats, same layout), and
+ * the summed loss to loss_out (host, may be NULL).  The sums are taken in a fixed order, so
+ * the result does not depend on thread timing.  ERANGE past the stored samples, EINVAL on
+ * non-finite weights.  Synchronises. */
+rapid_status rapid_trainer_gradient(rapid_trainer *t, const float *weights, int64_t first, int32_t count,
+                                    float pos_weight, float *grad_out, float *loss_out);
 
 /* Whole slide.  The slide (device, H x W interleaved RGB, rows rgb_pitch_bytes apart; any
  * size) is cut into tiles by even row and column bands of at most max_tile pixels

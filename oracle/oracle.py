@@ -71,6 +71,8 @@ def lib():
         L.orc_lambda_pos.restype = C.c_double
         L.orc_simple_lut.argtypes = [P]
         L.orc_set_classifier.argtypes = [P, P]
+        L.orc_set_keep_mask.argtypes = [P, C.c_int32, P, C.c_int64]
+        L.orc_set_keep_mask.restype = C.c_int32
         L.orc_read_features.argtypes = [P, P]
         for name in ("orc_stage_info", "orc_phase", "orc_get_grid", "orc_read_block_labels",
                      "orc_read_labels", "orc_read_stats", "orc_read_counters", "orc_read_pyramid",
@@ -176,6 +178,16 @@ class Oracle:
         self._theta = np.ascontiguousarray(theta, dtype=np.float64)
         assert self._theta.shape == (5,)
         self._ok(lib().orc_set_classifier(self.h, self._theta.ctypes.data))
+        return self
+
+    def set_keep_mask(self, stage: int, mask):
+        """Pruned sweeps of stage `stage` with this keep mask over its block grid (nby x nbx,
+        nonzero = kept); None sweeps the stage in full."""
+        if mask is None:
+            self._ok(lib().orc_set_keep_mask(self.h, stage, None, 0))
+            return self
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        self._ok(lib().orc_set_keep_mask(self.h, stage, m.ctypes.data, m.size))
         return self
 
     def features(self) -> np.ndarray:

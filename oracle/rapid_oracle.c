@@ -70,6 +70,8 @@ struct orc_state {
   int32_t use_theta; /* 1: Eq. predict evaluates the linear classifier theta on F */
   double theta[5];
   double *feat;      /* M x 4 features of the last prediction */
+  uint8_t *keep[MAXSTAGES]; /* pruned sweeps: the stage's keep mask over its block grid (NULL: none) */
+  int32_t pruned;           /* 1 while the current stage sweeps with its keep mask */
 };
 
 enum { C_LEVEL, C_SIDE, C_SWEEPS, C_ELIG, C_EVAL, C_MOVES, C_REQ, C_MERGES };
@@ -240,6 +242,7 @@ void orc_destroy(orc_state *st) {
   free(st->req_lab);
   free(st->N); free(st->R); free(st->G); free(st->B); free(st->X); free(st->Y); free(st->init);
   free(st->y); free(st->imp); free(st->feat);
+  for (int i = 0; i < MAXSTAGES; i++) free(st->keep[i]);
   free(st);
 }
 
@@ -254,6 +257,7 @@ int32_t orc_stage_info(const orc_state *st, int32_t i, int32_t *level, int32_t *
 
 static void set_stage_grid(orc_state *st, int32_t i) {
   st->cur = i;
+  st->pruned = st->keep[i] != NULL; /* a stage with a keep mask starts with pruned sweeps */
   st->level = st->st_level[i];
   st->side = st->st_side[i];
   st->nbx = ceil_div(st->W, st->side);
@@ -403,6 +407,9 @@ static int decide(const orc_state *st, int32_t bx, int32_t by, const double *cR,
   int32_t a = st->lab[(int64_t)by * st->nbx + bx];
   if (!eligible(st, bx, by, a)) return 0;
   (*elig)++;
+  /* pruned sweeps: an eligible block that the stage's keep mask leaves out gets neither
+   * the topology test nor a decision (it stays as it is) */
+  if (st->pruned && !st->keep[st->cur][(int64_t)by * st->nbx + bx]) return 0;
   if (!st->lut[neighbour_mask(st, bx, by, a)]) return 0;
   (*eval)++;
   int64_t b[6];
@@ -608,7 +615,10 @@ int32_t orc_phase(orc_state *st, int32_t phase, int64_t *moves_out, int64_t *mer
 }
 
 /* Sweeps of the current stage until one makes no move and no merge ("until the queue is
- * empty"), or max_sweeps. */
+ * empty"), or max_sweeps.  A stage with a keep mask first sweeps pruned (only the kept
+ * eligible blocks are tested and decided) until a pruned sweep changes nothing, then goes
+ * on with full sweeps until a full sweep changes nothing; all sweeps count against
+ * max_sweeps. */
 int32_t orc_refine_stage(orc_state *st) {
   if (st->cur < 0) return 4;
   memset(st->queued, 1, (size_t)st->nbx * st->nby); /* schedule 1: every block queued */
@@ -620,8 +630,29 @@ int32_t orc_refine_stage(orc_state *st) {
       changes += mv + mg;
     }
     st->cnt[st->cur][C_SWEEPS]++;
-    if (changes == 0) break;
+    if (changes == 0) {
+      if (!st->pruned) break;
+      st->pruned = 0; /* the fallback: full sweeps from here on */
+    }
   }
+  return 0;
+}
+
+/* Keep mask of stage i (nbx * nby bytes of that stage's block grid, row-major; nonzero =
+ * kept), or NULL to sweep the stage in full.  The schedule of the pruned sweeps is the
+ * sweep schedule (schedule 0). */
+int32_t orc_set_keep_mask(orc_state *st, int32_t i, const uint8_t *mask, int64_t n) {
+  if (i < 0 || i >= st->nstages) return 1;
+  free(st->keep[i]);
+  st->keep[i] = NULL;
+  if (!mask) return 0;
+  if (st->p.schedule != 0) return 1;
+  int64_t nb = (int64_t)ceil_div(st->W, st->st_side[i]) * ceil_div(st->H, st->st_side[i]);
+  if (n != nb) return 1;
+  st->keep[i] = (uint8_t *)malloc((size_t)nb);
+  if (!st->keep[i]) return 2;
+  memcpy(st->keep[i], mask, (size_t)nb);
+  if (st->cur == i) st->pruned = 1;
   return 0;
 }
 
@@ -765,6 +796,7 @@ int32_t orc_run(orc_state *st) {
  * moved block are pushed (N, W, E, S) when not already queued.  Used only to compare
  * quality with the phased schedule. */
 static void fifo_stage(orc_state *st) {
+  st->pruned = 0; /* keep masks belong to the phased sweeps only */
   int64_t nb = (int64_t)st->nbx * st->nby;
   int64_t cap = nb + 1;
   int64_t *q = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);

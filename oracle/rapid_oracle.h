@@ -79,6 +79,12 @@ int32_t orc_run_fifo(orc_state *st);
  * prediction (M x 4: absolute brightness, comparative brightness, extra-region and
  * intra-region dissimilarity). */
 int32_t orc_set_classifier(orc_state *st, const double *theta5);
+/* Pruned sweeps (the pruning that the learned block scorer drives): keep mask of stage i
+ * over its block grid (nbx * nby bytes, nonzero = kept), or NULL for full sweeps.  The
+ * stage then sweeps testing and deciding only the kept eligible blocks until a sweep
+ * changes nothing, then full sweeps until a full sweep changes nothing, within max_sweeps.
+ * Sweep schedule only. */
+int32_t orc_set_keep_mask(orc_state *st, int32_t i, const uint8_t *mask, int64_t n);
 int32_t orc_read_features(const orc_state *st, double *dst4);
 
 #ifdef __cplusplus

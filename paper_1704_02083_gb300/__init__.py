@@ -105,12 +105,15 @@ def lib() -> C.CDLL:
         "rapid_set_graph": (i32, [P, i32]),
         "rapid_set_stage_grids": (i32, [P, pi32, i32]),
         "rapid_set_scorer": (i32, [P, P, C.c_float]),
+        "rapid_set_keep_mask": (i32, [P, i32, i32, P, i64, i32]),
         "rapid_set_classifier": (i32, [P, P]),
         "rapid_read_features": (i32, [P, i32, P]),
         "rapid_refine_slide": (i32, [P, P, i64, i64, i64, i32, i32, i32, P, i64, P, i64, pi64, pi32]),
         "rapid_scorer_features": (i32, [P, i32, P]),
         "rapid_scorer_scores": (i32, [P, i32, P, P]),
         "rapid_trainer_create": (i32, [i64, C.c_float, C.POINTER(P)]),
+        "rapid_trainer_samples": (i32, [P, i64, i32, P, P, P]),
+        "rapid_trainer_gradient": (i32, [P, P, i64, i32, C.c_float, P, P]),
         "rapid_set_logging": (i32, [P, P]),
         "rapid_trainer_count": (i32, [P, pi64, pi64]),
         "rapid_trainer_fit": (i32, [P, i32, i32, C.c_float, C.c_float, C.c_uint64, P, P, P]),
@@ -302,6 +305,21 @@ def rapid_set_scorer(ctx: int, weights, threshold: float):
     _check(lib().rapid_set_scorer(ctx, w.ctypes.data, float(threshold)), "rapid_set_scorer")
 
 
+def rapid_set_keep_mask(ctx: int, i: int, s: int, mask):
+    """Pruned sweeps of stage s with image i's keep mask (nby x nbx uint8, nonzero = kept;
+    a numpy array or a CUDA tensor); mask None (with i = s = -1) clears every mask."""
+    if mask is None:
+        _check(lib().rapid_set_keep_mask(ctx, i, s, None, 0, 0), "rapid_set_keep_mask")
+        return
+    if hasattr(mask, "data_ptr"):
+        m = mask.contiguous()
+        _check(lib().rapid_set_keep_mask(ctx, i, s, m.data_ptr(), m.numel(), 1 if m.is_cuda else 0),
+               "rapid_set_keep_mask")
+        return
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    _check(lib().rapid_set_keep_mask(ctx, i, s, m.ctypes.data, m.size, 0), "rapid_set_keep_mask")
+
+
 def rapid_set_classifier(ctx: int, theta):
     """Eq. predict with h = theta[0] + theta[1:] . F over the superpixel features (None: the
     brightness stand-in)."""
@@ -350,12 +368,34 @@ def rapid_trainer_fit(trainer: int, epochs: int, batch: int, lr: float, pos_weig
     """Returns (weights, per-epoch mean loss)."""
     w = np.zeros(RAPID_SCORER_PARAMS, np.float32)
     loss = np.zeros(epochs, np.float32)
-    ip = _f32(init).ctypes.data if init is not None else None
-    keep = init
+    keep = _f32(init) if init is not None else None  # held until the call returns
+    ip = keep.ctypes.data if keep is not None else None
     _check(lib().rapid_trainer_fit(trainer, epochs, batch, float(lr), float(pos_weight), seed, ip, w.ctypes.data,
                                    loss.ctypes.data), "rapid_trainer_fit")
     del keep
     return w, loss
+
+
+def rapid_trainer_samples(trainer: int, first: int, count: int):
+    """Stored samples first .. first + count - 1: patches (count x 7 x 7 x 9 float32),
+    in-image masks (count uint64, bit p = patch position p) and labels (count float32)."""
+    x = np.zeros((count, 7, 7, 9), np.float32)
+    inb = np.zeros(count, np.uint64)
+    y = np.zeros(count, np.float32)
+    _check(lib().rapid_trainer_samples(trainer, first, count, x.ctypes.data, inb.ctypes.data, y.ctypes.data),
+           "rapid_trainer_samples")
+    return x, inb, y
+
+
+def rapid_trainer_gradient(trainer: int, weights, first: int, count: int, pos_weight: float):
+    """Summed gradient (RAPID_SCORER_PARAMS float32) and loss of samples first .. first +
+    count - 1 at the master weights `weights`."""
+    w = _f32(weights)
+    g = np.zeros(RAPID_SCORER_PARAMS, np.float32)
+    loss = C.c_float()
+    _check(lib().rapid_trainer_gradient(trainer, w.ctypes.data, first, count, float(pos_weight), g.ctypes.data,
+                                        C.byref(loss)), "rapid_trainer_gradient")
+    return g, loss.value
 
 
 def rapid_trainer_destroy(trainer: int):
@@ -560,6 +600,11 @@ class Context:
     def set_scorer(self, weights, threshold: float = 0.3):
         rapid_set_scorer(self.h, weights, threshold)
 
+    def set_keep_mask(self, i: int, s: int, mask):
+        """Image i's keep mask for stage s (pruned sweeps); None with i = s = -1 clears."""
+        rapid_set_keep_mask(self.h, i, s, mask)
+        return self
+
     def set_classifier(self, theta):
         """theta (5 floats) for Eq. predict over the superpixel features, or None."""
         rapid_set_classifier(self.h, theta)
@@ -617,6 +662,12 @@ class Trainer:
 
     def fit(self, epochs=8, batch=2048, lr=3e-3, pos_weight=4.0, seed=0, init=None):
         return rapid_trainer_fit(self.h, epochs, batch, lr, pos_weight, seed, init)
+
+    def samples(self, first: int, count: int):
+        return rapid_trainer_samples(self.h, first, count)
+
+    def gradient(self, weights, first: int, count: int, pos_weight: float = 4.0):
+        return rapid_trainer_gradient(self.h, weights, first, count, pos_weight)
 
     def close(self):
         if getattr(self, "h", 0):

@@ -209,17 +209,77 @@ __device__ __forceinline__ unsigned hash3(unsigned a, unsigned b, unsigned c) {
   return h;
 }
 
-__global__ void collect_kernel(const float *feat, const int *before, const int *after, int nbx, int nby, int img,
-                               int stage, unsigned neg_threshold, TrainSet ts) {
+// Whether block i becomes a sample, and its label y.
+__device__ __forceinline__ bool is_sample(const float *feat, const int *before, const int *after, long long i,
+                                          int img, int stage, unsigned neg_threshold, float *y) {
+  if (feat[i * kFeat + 4] <= 0.f) return false;  // not a boundary block at the stage start
+  *y = before[i] != after[i] ? 1.f : 0.f;
+  return *y != 0.f || hash3((unsigned)img, (unsigned)stage, (unsigned)i) <= neg_threshold;
+}
+
+// The samples of one logged stage take consecutive slots in block order, whatever the
+// thread timing: a count per CTA of kCollectThreads blocks, an exclusive scan over those
+// counts (one CTA), then each CTA writes its samples at its base plus their rank in it.
+constexpr int kCollectThreads = 256, kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kCollectThreads) collect_count_kernel(const float *feat, const int *before,
+                                                                         const int *after, long long nb, int img,
+                                                                         int stage, unsigned neg_threshold,
+                                                                         int *cta_count) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)nbx * nby) return;
-  if (feat[i * kFeat + 4] <= 0.f) return;  // not a boundary block at the stage start
-  const float y = before[i] != after[i] ? 1.f : 0.f;
-  if (y == 0.f && hash3((unsigned)img, (unsigned)stage, (unsigned)i) > neg_threshold) return;
-  const int slot = atomicAdd(ts.count, 1);
-  if (slot >= ts.cap) return;
+  float y;
+  const bool take = i < nb && is_sample(feat, before, after, i, img, stage, neg_threshold, &y);
+  const int c = __syncthreads_count(take);
+  if (threadIdx.x == 0) cta_count[blockIdx.x] = c;
+}
+
+// cta_base[j] = *ts.count + sum of cta_count[0 .. j); then *ts.count grows by the total.
+__global__ void __launch_bounds__(kScanThreads) collect_scan_kernel(const int *cta_count, int nctas, int *cta_base,
+                                                                    TrainSet ts) {
+  __shared__ long long s_part[kScanThreads];
+  const int per = (nctas + kScanThreads - 1) / kScanThreads;
+  const int b0 = threadIdx.x * per, b1 = min(nctas, b0 + per);
+  long long sum = 0;
+  for (int j = b0; j < b1; j++) sum += cta_count[j];
+  s_part[threadIdx.x] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {  // exclusive prefix over the threads' chunks, in order
+    long long run = *ts.count;
+    for (int t = 0; t < kScanThreads; t++) {
+      const long long v = s_part[t];
+      s_part[t] = run;
+      run += v;
+    }
+    *ts.count = (int)min(run, (long long)INT_MAX);
+  }
+  __syncthreads();
+  long long run = s_part[threadIdx.x];
+  for (int j = b0; j < b1; j++) {
+    cta_base[j] = (int)min(run, (long long)INT_MAX);
+    run += cta_count[j];
+  }
+}
+
+__global__ void __launch_bounds__(kCollectThreads) collect_write_kernel(const float *feat, const int *before,
+                                                                         const int *after, int nbx, int nby, int img,
+                                                                         int stage, unsigned neg_threshold,
+                                                                         const int *cta_base, TrainSet ts) {
+  __shared__ int s_warp[kCollectThreads / 32];
+  const long long nb = (long long)nbx * nby;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float y = 0.f;
+  const bool take = i < nb && is_sample(feat, before, after, i, img, stage, neg_threshold, &y);
+  const unsigned ball = __ballot_sync(0xffffffffu, take);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) s_warp[warp] = __popc(ball);
+  __syncthreads();
+  int rank = __popc(ball & ((1u << lane) - 1u));
+  for (int w = 0; w < warp; w++) rank += s_warp[w];
+  if (!take) return;
+  const long long slot = (long long)cta_base[blockIdx.x] + rank;
+  if (slot >= ts.cap) return;  // the store is full: the extra samples are dropped
   const int bx = (int)(i % nbx), by = (int)(i / nbx);
-  float *x = ts.x + (long long)slot * kPatchFeat;
+  float *x = ts.x + slot * kPatchFeat;
   unsigned long long inb = 0;
   for (int p = 0; p < kPatch * kPatch; p++) {
     const int qx = bx - 3 + p % kPatch, qy = by - 3 + p / kPatch;
@@ -233,9 +293,10 @@ __global__ void collect_kernel(const float *feat, const int *before, const int *
 
 // ---------------------------------------------------------------- training
 // Forward and backward of the net on one sample's patch, one warp per sample, fp32 with
-// bf16-rounded weights in the forward pass (the inference precision) and fp32 master
-// weights updated by Adam.  Loss: pos_weight * y * -log p + (1 - y) * -log(1 - p).
-constexpr int kTrainWarps = 8;
+// bf16-rounded weights, inputs and activations and fp32 biases (the inference precision),
+// and fp32 master weights updated by Adam.  The bf16 roundings pass gradients through
+// unchanged.  Loss: pos_weight * y * -log p + (1 - y) * -log(1 - p).
+constexpr int kTrainWarps = 8, kTrainMaxCtas = 1024;
 
 struct WarpScratch {
   float z1[25 * kHid], h1[25 * kHid];  // layer 1 on the 5 x 5 positions around the sample
@@ -247,19 +308,35 @@ struct WarpScratch {
 
 __device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
+// Gradients are summed in a fixed order, so that a training run is reproducible: each warp
+// adds its samples' gradients, one after another, into a buffer of its own (every
+// parameter of a sample is written by one lane), the CTA then adds its warps' buffers in
+// warp order into its row of `part`, and train_reduce_kernel adds the rows in CTA order.
+struct TrainSmem {
+  float w[kNParams];
+  float g[kTrainWarps][kNParams];
+  float loss[kTrainWarps];
+  WarpScratch ws[kTrainWarps];
+};
+constexpr size_t kTrainSmem = sizeof(TrainSmem);
+static_assert(kTrainSmem <= 227 * 1024, "the training kernel's shared memory");
+
 __global__ void __launch_bounds__(kTrainWarps * 32) train_grad_kernel(TrainSet ts, int n, const float *wmaster,
                                                                       const int *order, int off, int batch,
-                                                                      float pos_weight, float *grad, float *loss) {
-  __shared__ float s_w[kNParams];
-  __shared__ float s_g[kNParams];
-  __shared__ WarpScratch s_ws[kTrainWarps];
-  for (int i = threadIdx.x; i < kNParams; i += blockDim.x) {
-    s_w[i] = bf(wmaster[i]);
-    s_g[i] = 0.f;
+                                                                      float pos_weight, float *part,
+                                                                      float *part_loss) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TrainSmem &T = *reinterpret_cast<TrainSmem *>(smem_raw);
+  float *s_w = T.w;
+  for (int i = threadIdx.x; i < kNParams; i += blockDim.x) {  // bf16 weights, fp32 biases: the inference precision
+    const bool bias = (i >= kOffB1 && i < kOffW2) || (i >= kOffB2 && i < kOffW3) || i == kOffB3;
+    s_w[i] = bias ? wmaster[i] : bf(wmaster[i]);
   }
+  for (int i = threadIdx.x; i < kTrainWarps * kNParams; i += blockDim.x) (&T.g[0][0])[i] = 0.f;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  WarpScratch &S = s_ws[warp];
+  WarpScratch &S = T.ws[warp];
+  float *s_g = T.g[warp];
   float lsum = 0.f;
   for (int b = blockIdx.x * kTrainWarps + warp; b < batch; b += gridDim.x * kTrainWarps) {
     const int sidx = order[(off + b) % n];
@@ -303,12 +380,12 @@ __global__ void __launch_bounds__(kTrainWarps * 32) train_grad_kernel(TrainSet t
     const float dz3 = y > 0.5f ? pos_weight * (p - 1.f) : p;
     if (lane == 0) {
       lsum += y > 0.5f ? -pos_weight * logf(fmaxf(p, 1e-12f)) : -logf(fmaxf(1.f - p, 1e-12f));
-      atomicAdd(&s_g[kOffB3], dz3);
+      s_g[kOffB3] += dz3;
     }
     // layer 3 gradients; layer 2 pre-activation gradients
     for (int j = lane; j < 9 * kHid; j += 32) {
       const int p2 = j / kHid, ci = j % kHid;
-      atomicAdd(&s_g[kOffW3 + ci * 9 + p2], dz3 * S.h2[j]);
+      s_g[kOffW3 + ci * 9 + p2] += dz3 * S.h2[j];
       const bool in = (inb >> ((p2 / 3 + 2) * kPatch + (p2 % 3 + 2))) & 1ull;
       S.d2[j] = (in && S.z2[j] > 0.f) ? dz3 * s_w[kOffW3 + ci * 9 + p2] : 0.f;
     }
@@ -322,12 +399,12 @@ __global__ void __launch_bounds__(kTrainWarps * 32) train_grad_kernel(TrainSet t
           const int q = (p2 / 3 + tap / 3) * 5 + (p2 % 3 + tap % 3);
           gsum += S.d2[p2 * kHid + co] * S.h1[q * kHid + ci];
         }
-        if (gsum != 0.f) atomicAdd(&s_g[kOffW2 + j], gsum);
+        s_g[kOffW2 + j] += gsum;
       } else {
         const int co = j - kHid * kHid * 9;
         float gsum = 0.f;
         for (int p2 = 0; p2 < 9; p2++) gsum += S.d2[p2 * kHid + co];
-        if (gsum != 0.f) atomicAdd(&s_g[kOffB2 + co], gsum);
+        s_g[kOffB2 + co] += gsum;
       }
     }
     // layer 1 pre-activation gradients
@@ -352,29 +429,51 @@ __global__ void __launch_bounds__(kTrainWarps * 32) train_grad_kernel(TrainSet t
           const int q = (p1 / 5 + tap / 3) * kPatch + (p1 % 5 + tap % 3);
           gsum += S.d1[p1 * kHid + co] * S.x[q * kFeat + ci];
         }
-        if (gsum != 0.f) atomicAdd(&s_g[kOffW1 + j], gsum);
+        s_g[kOffW1 + j] += gsum;
       } else {
         const int co = j - kHid * kFeat * 9;
         float gsum = 0.f;
         for (int p1 = 0; p1 < 25; p1++) gsum += S.d1[p1 * kHid + co];
-        if (gsum != 0.f) atomicAdd(&s_g[kOffB1 + co], gsum);
+        s_g[kOffB1 + co] += gsum;
       }
     }
     __syncwarp();
   }
+  if (lane == 0) T.loss[warp] = lsum;
   __syncthreads();
-  for (int i = threadIdx.x; i < kNParams; i += blockDim.x)
-    if (s_g[i] != 0.f) atomicAdd(&grad[i], s_g[i]);
-  if (lane == 0 && lsum != 0.f) atomicAdd(loss, lsum);
+  for (int i = threadIdx.x; i < kNParams; i += blockDim.x) {
+    float g = 0.f;
+    for (int w = 0; w < kTrainWarps; w++) g += T.g[w][i];
+    part[(long long)blockIdx.x * kNParams + i] = g;
+  }
+  if (threadIdx.x == 0) {
+    float l = 0.f;
+    for (int w = 0; w < kTrainWarps; w++) l += T.loss[w];
+    part_loss[blockIdx.x] = l;
+  }
 }
 
-// Adam on the fp32 master weights (gradient averaged over the batch); clears the gradient.
+// grad[i] = sum over the CTAs' rows in CTA order; *loss += their losses in the same order.
+__global__ void train_reduce_kernel(const float *part, const float *part_loss, int ctas, float *grad, float *loss) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kNParams) {
+    float g = 0.f;
+    for (int c = 0; c < ctas; c++) g += part[(long long)c * kNParams + i];
+    grad[i] = g;
+  }
+  if (i == 0) {
+    float l = 0.f;
+    for (int c = 0; c < ctas; c++) l += part_loss[c];
+    *loss += l;
+  }
+}
+
+// Adam on the fp32 master weights (gradient averaged over the batch).
 __global__ void adam_kernel(float *w, float *m, float *v, float *grad, int n, float lr, float b1, float b2,
                             float eps, float bc1, float bc2, float inv_batch) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float gi = grad[i] * inv_batch;
-  grad[i] = 0.f;
   m[i] = b1 * m[i] + (1.f - b1) * gi;
   v[i] = b2 * v[i] + (1.f - b2) * gi * gi;
   w[i] -= lr * (m[i] / bc1) / (sqrtf(v[i] / bc2) + eps);
@@ -439,19 +538,34 @@ cudaError_t launch_score(const StageArgs &a, const ImageDesc &im, int L, const S
   return cudaGetLastError();
 }
 
+size_t collect_scratch_ints(long long blocks) { return 2 * (size_t)blocks_for(blocks, kCollectThreads) + 2; }
+
 cudaError_t launch_collect(const float *feat, const int *before, const int *after, int nbx, int nby, int img,
-                           int stage, float neg_rate, const TrainSet &ts, cudaStream_t s) {
+                           int stage, float neg_rate, const TrainSet &ts, int *scratch, cudaStream_t s) {
   const double q = neg_rate <= 0.f ? 0.0 : neg_rate >= 1.f ? 4294967295.0 : (double)neg_rate * 4294967296.0;
-  collect_kernel<<<blocks_for((long long)nbx * nby, 256), 256, 0, s>>>(feat, before, after, nbx, nby, img, stage,
-                                                                      (unsigned)q, ts);
+  const long long nb = (long long)nbx * nby;
+  const unsigned nctas = blocks_for(nb, kCollectThreads);
+  int *cnt = scratch, *base = scratch + nctas;
+  collect_count_kernel<<<nctas, kCollectThreads, 0, s>>>(feat, before, after, nb, img, stage, (unsigned)q, cnt);
+  collect_scan_kernel<<<1, kScanThreads, 0, s>>>(cnt, (int)nctas, base, ts);
+  collect_write_kernel<<<nctas, kCollectThreads, 0, s>>>(feat, before, after, nbx, nby, img, stage, (unsigned)q,
+                                                         base, ts);
   return cudaGetLastError();
 }
 
+int train_max_ctas() { return kTrainMaxCtas; }
+
 cudaError_t launch_train_step(const TrainSet &ts, int n, const float *w, const int *order, int off, int batch,
-                              float pos_weight, float *grad, float *loss, cudaStream_t s) {
-  const int ctas = (batch + kTrainWarps - 1) / kTrainWarps;
-  train_grad_kernel<<<ctas < 1024 ? ctas : 1024, kTrainWarps * 32, 0, s>>>(ts, n, w, order, off, batch, pos_weight,
-                                                                          grad, loss);
+                              float pos_weight, float *part, float *part_loss, float *grad, float *loss,
+                              cudaStream_t s) {
+  const cudaError_t e =
+      cudaFuncSetAttribute(train_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem);
+  if (e != cudaSuccess) return e;
+  const int want = (batch + kTrainWarps - 1) / kTrainWarps;
+  const int ctas = want < kTrainMaxCtas ? want : kTrainMaxCtas;
+  train_grad_kernel<<<ctas, kTrainWarps * 32, kTrainSmem, s>>>(ts, n, w, order, off, batch, pos_weight, part,
+                                                                part_loss);
+  train_reduce_kernel<<<blocks_for(kNParams, 256), 256, 0, s>>>(part, part_loss, ctas, grad, loss);
   return cudaGetLastError();
 }
 

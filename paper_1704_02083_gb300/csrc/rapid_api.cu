@@ -123,12 +123,20 @@ struct rapid_ctx {
   ScorerDev sdev;
   unsigned char *d_mask;
   size_t mask_cap;
+  // caller-given keep masks (rapid_set_keep_mask): per (stage, image) at keep_off, 1 = kept
+  unsigned char *d_keep;
+  size_t keep_cap;
+  size_t keep_off[RAPID_MAX_STAGES][kMaxBatch];
+  int keep_stage[RAPID_MAX_STAGES];  // 1: the stage sweeps pruned with its masks
+  int keep_on;
   // training-data logging
   rapid_trainer *logger;
   float *d_feat;
   size_t feat_cap;
   int *d_before;
   size_t before_cap;
+  int *d_collect;  // scratch of the sample collection (per-CTA counts and bases)
+  size_t collect_cap;
 };
 
 struct rapid_trainer {
@@ -303,6 +311,11 @@ static void free_image_buffers(rapid_ctx *ctx) {
   ctx->desc_cap = 0;
   std::free(ctx->h_desc);
   ctx->h_desc = nullptr;
+  cudaFree(ctx->d_keep);
+  ctx->d_keep = nullptr;
+  ctx->keep_cap = 0;
+  ctx->keep_on = 0;
+  std::memset(ctx->keep_stage, 0, sizeof ctx->keep_stage);
   cudaFree(ctx->d_mask);
   ctx->d_mask = nullptr;
   ctx->mask_cap = 0;
@@ -312,6 +325,9 @@ static void free_image_buffers(rapid_ctx *ctx) {
   cudaFree(ctx->d_before);
   ctx->d_before = nullptr;
   ctx->before_cap = 0;
+  cudaFree(ctx->d_collect);
+  ctx->d_collect = nullptr;
+  ctx->collect_cap = 0;
 }
 
 extern "C" void rapid_destroy(rapid_ctx *ctx) {
@@ -488,6 +504,8 @@ extern "C" rapid_status rapid_set_images(rapid_ctx *ctx, int32_t n, const uint8_
   }
   drop_graph(ctx);
   ctx->image_set = false;
+  ctx->keep_on = 0;  // keep masks belong to the previous images' block grids
+  std::memset(ctx->keep_stage, 0, sizeof ctx->keep_stage);
   ctx->cur = -1;
   rapid_status rs = make_schedule(ctx);
   if (rs != RAPID_OK) return rs;
@@ -562,6 +580,8 @@ extern "C" rapid_status rapid_set_images(rapid_ctx *ctx, int32_t n, const uint8_
   if (ctx->logger) {
     if (!grow(&ctx->d_feat, &ctx->feat_cap, lab_n * kScorerFeatures() * sizeof(float))) return RAPID_ENOMEM;
     if (!grow(&ctx->d_before, &ctx->before_cap, lab_n * sizeof(int))) return RAPID_ENOMEM;
+    if (!grow(&ctx->d_collect, &ctx->collect_cap, collect_scratch_ints((long long)lab_n) * sizeof(int)))
+      return RAPID_ENOMEM;
   }
   rs = build_descriptors(ctx);
   if (rs != RAPID_OK) return rs;
@@ -614,7 +634,7 @@ static StageArgs stage_args(rapid_ctx *ctx, int s) {
   a.max_sweeps = ctx->p.max_sweeps;
   a.verify_filter = ctx->p.verify_filter;
   a.skip_tiles = ctx->p.skip_tiles;
-  a.prune = ctx->scorer_on;
+  a.prune = ctx->scorer_on || (ctx->keep_on && ctx->keep_stage[s]);
   a.frontier = ctx->p.schedule == 1;
   a.qbits = ctx->d_qbits;
   a.wl = ctx->d_wl;
@@ -714,6 +734,10 @@ extern "C" rapid_status rapid_refine_stage(rapid_ctx *ctx, int32_t *sweeps_out, 
                       ctx->stream));
       ctx->launches++;
     }
+  else if (a.prune)  // the caller's keep masks for this stage
+    for (int m = 0; m < ctx->nimg; m++)
+      CK(cudaMemcpyAsync(ctx->d_mask + ctx->im[m].lab_off, ctx->d_keep + ctx->keep_off[i][m],
+                         (size_t)ds[m].nbx * ds[m].nby, cudaMemcpyDeviceToDevice, ctx->stream));
   if (ctx->logger)  // training data: features and labels at the stage start
     for (int m = 0; m < ctx->nimg; m++) {
       const size_t off = ctx->im[m].lab_off;
@@ -731,7 +755,7 @@ extern "C" rapid_status rapid_refine_stage(rapid_ctx *ctx, int32_t *sweeps_out, 
       const size_t off = ctx->im[m].lab_off;
       CK(launch_collect(ctx->d_feat + off * kScorerFeatures(), ctx->d_before + off, ds[m].lab, ds[m].nbx,
                         ds[m].nby, ctx->logger->runs * kMaxBatch + m, i, ctx->logger->neg_rate, ctx->logger->ts,
-                        ctx->stream));
+                        ctx->d_collect, ctx->stream));
       ctx->launches++;
     }
   if (sweeps_out || moves_out || merges_out) {
@@ -962,6 +986,7 @@ extern "C" rapid_status rapid_set_scorer(rapid_ctx *ctx, const float *weights, f
   }
   if (!(threshold >= 0.f && threshold <= 1.f)) return RAPID_EINVAL;
   if (ctx->p.schedule != 0) return RAPID_EINVAL;  // pruned sweeps are defined for schedule 0 only
+  if (ctx->keep_on) return RAPID_EINVAL;          // one source of masks at a time
   for (int i = 0; i < RAPID_SCORER_PARAMS; i++)
     if (!std::isfinite(weights[i])) return RAPID_EINVAL;
   if (!ctx->d_scorer && cudaMalloc(&ctx->d_scorer, scorer_dev_bytes()) != cudaSuccess) return RAPID_ENOMEM;
@@ -972,6 +997,46 @@ extern "C" rapid_status rapid_set_scorer(rapid_ctx *ctx, const float *weights, f
     if (!grow(&ctx->d_mask, &ctx->mask_cap, ctx->lab_total)) return RAPID_ENOMEM;
     return build_descriptors(ctx);
   }
+  return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_set_keep_mask(rapid_ctx *ctx, int32_t i, int32_t s, const uint8_t *mask, int64_t n,
+                                            int32_t mask_is_device) {
+  if (!ctx) return RAPID_EINVAL;
+  if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  if (!mask) {  // clear every mask
+    if (i != -1 || s != -1) return RAPID_EINVAL;
+    if (ctx->keep_on) drop_graph(ctx);
+    ctx->keep_on = 0;
+    std::memset(ctx->keep_stage, 0, sizeof ctx->keep_stage);
+    return RAPID_OK;
+  }
+  if (!ctx->image_set) return RAPID_ESTATE;
+  if (i < 0 || i >= ctx->nimg || s < 0 || s >= ctx->nstages || (mask_is_device & ~1)) return RAPID_EINVAL;
+  if (ctx->p.schedule != 0 || ctx->scorer_on) return RAPID_EINVAL;
+  const ImageDesc &d = ctx->h_desc[(size_t)s * ctx->nimg + i];
+  if (n != (int64_t)d.nbx * d.nby) return RAPID_EINVAL;
+  drop_graph(ctx);
+  if (!ctx->keep_on) {  // every (stage, image) mask starts as "keep every block"
+    size_t off = 0;
+    for (int st = 0; st < ctx->nstages; st++)
+      for (int m = 0; m < ctx->nimg; m++) {
+        const ImageDesc &e = ctx->h_desc[(size_t)st * ctx->nimg + m];
+        ctx->keep_off[st][m] = off;
+        off = round_up(off + (size_t)e.nbx * e.nby, 256);
+      }
+    if (!grow(&ctx->d_keep, &ctx->keep_cap, off)) return RAPID_ENOMEM;
+    if (!grow(&ctx->d_mask, &ctx->mask_cap, ctx->lab_total)) return RAPID_ENOMEM;
+    CK(cudaMemsetAsync(ctx->d_keep, 1, off, ctx->stream));
+    ctx->keep_on = 1;
+    std::memset(ctx->keep_stage, 0, sizeof ctx->keep_stage);
+    rapid_status rs = build_descriptors(ctx);  // the descriptors now point at the mask buffer
+    if (rs != RAPID_OK) return rs;
+  }
+  CK(cudaMemcpyAsync(ctx->d_keep + ctx->keep_off[s][i], mask, (size_t)n,
+                     mask_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->keep_stage[s] = 1;
   return RAPID_OK;
 }
 
@@ -1044,6 +1109,8 @@ extern "C" rapid_status rapid_set_logging(rapid_ctx *ctx, rapid_trainer *t) {
   if (t && ctx->image_set) {
     if (!grow(&ctx->d_feat, &ctx->feat_cap, ctx->lab_total * kScorerFeatures() * sizeof(float))) return RAPID_ENOMEM;
     if (!grow(&ctx->d_before, &ctx->before_cap, ctx->lab_total * sizeof(int))) return RAPID_ENOMEM;
+    if (!grow(&ctx->d_collect, &ctx->collect_cap, collect_scratch_ints((long long)ctx->lab_total) * sizeof(int)))
+      return RAPID_ENOMEM;
   }
   return RAPID_OK;
 }
@@ -1106,13 +1173,17 @@ extern "C" rapid_status rapid_trainer_fit(rapid_trainer *t, int32_t epochs, int3
     fill(16 * 9 * 9 + 16 + 16 * 16 * 9 + 16, 16 * 9, 16 * 9, 9);
   }
   float *d = nullptr;  // w, m, v, grad, loss
+  float *part = nullptr;  // per-CTA gradient rows and losses of a minibatch
   int *order = nullptr;
   int *horder = (int *)std::malloc((size_t)n * sizeof(int));
   rapid_status rs = RAPID_OK;
+  const size_t nparts = (size_t)train_max_ctas();
   if (!horder || cudaMalloc(&d, (4 * (size_t)nP + 1) * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&part, nparts * (nP + 1) * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&order, (size_t)n * sizeof(int)) != cudaSuccess)
     rs = RAPID_ENOMEM;
   float *w = d, *m = d + nP, *v = d + 2 * nP, *grad = d + 3 * nP, *loss = d + 4 * nP;
+  float *part_loss = part + nparts * nP;
   if (rs == RAPID_OK && (cudaMemcpy(w, w0, nP * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
                          cudaMemset(m, 0, (3 * (size_t)nP + 1) * sizeof(float)) != cudaSuccess))
     rs = RAPID_ECUDA;
@@ -1132,7 +1203,8 @@ extern "C" rapid_status rapid_trainer_fit(rapid_trainer *t, int32_t epochs, int3
       const int bs = (int)std::min<long long>(batch, n - off);
       step++;
       const float bc1 = 1.f - std::pow(0.9f, (float)step), bc2 = 1.f - std::pow(0.999f, (float)step);
-      if (launch_train_step(t->ts, (int)n, w, order, (int)off, bs, pos_weight, grad, loss, 0) != cudaSuccess ||
+      if (launch_train_step(t->ts, (int)n, w, order, (int)off, bs, pos_weight, part, part_loss, grad, loss, 0) !=
+              cudaSuccess ||
           launch_adam(w, m, v, grad, lr, bc1, bc2, 1.f / (float)bs, 0) != cudaSuccess) {
         rs = RAPID_ECUDA;
         break;
@@ -1145,6 +1217,61 @@ extern "C" rapid_status rapid_trainer_fit(rapid_trainer *t, int32_t epochs, int3
   if (rs == RAPID_OK && cudaMemcpy(weights_out, w, nP * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
     rs = RAPID_ECUDA;
   cudaFree(d);
+  cudaFree(part);
+  cudaFree(order);
+  std::free(horder);
+  return rs;
+}
+
+extern "C" rapid_status rapid_trainer_samples(rapid_trainer *t, int64_t first, int32_t count, float *x_out,
+                                              uint64_t *inb_out, float *y_out) {
+  if (!t || first < 0 || count < 1) return RAPID_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return RAPID_ECUDA;
+  const long long n = trainer_samples(t);
+  if (n < 0) return RAPID_ECUDA;
+  if (first + count > n) return RAPID_ERANGE;
+  if (x_out && cudaMemcpy(x_out, t->buf_x + first * kScorerPatchFloats, (size_t)count * kScorerPatchFloats * 4,
+                          cudaMemcpyDeviceToHost) != cudaSuccess)
+    return RAPID_ECUDA;
+  if (inb_out && cudaMemcpy(inb_out, t->buf_inb + first, (size_t)count * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return RAPID_ECUDA;
+  if (y_out && cudaMemcpy(y_out, t->buf_y + first, (size_t)count * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return RAPID_ECUDA;
+  return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_trainer_gradient(rapid_trainer *t, const float *weights, int64_t first, int32_t count,
+                                               float pos_weight, float *grad_out, float *loss_out) {
+  if (!t || !weights || !grad_out || first < 0 || count < 1 || !(pos_weight > 0.f)) return RAPID_EINVAL;
+  for (int i = 0; i < RAPID_SCORER_PARAMS; i++)
+    if (!std::isfinite(weights[i])) return RAPID_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return RAPID_ECUDA;
+  const long long n = trainer_samples(t);
+  if (n < 0) return RAPID_ECUDA;
+  if (first + count > n) return RAPID_ERANGE;
+  const int nP = RAPID_SCORER_PARAMS;
+  const size_t nparts = (size_t)train_max_ctas();
+  float *d = nullptr, *part = nullptr;
+  int *order = nullptr;
+  int *horder = (int *)std::malloc((size_t)count * sizeof(int));
+  rapid_status rs = RAPID_OK;
+  if (!horder || cudaMalloc(&d, (2 * (size_t)nP + 1) * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&part, nparts * (nP + 1) * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&order, (size_t)count * sizeof(int)) != cudaSuccess)
+    rs = RAPID_ENOMEM;
+  for (int i = 0; i < count && horder; i++) horder[i] = (int)(first + i);
+  float *w = d, *grad = d + nP, *loss = d + 2 * nP;
+  if (rs == RAPID_OK &&
+      (cudaMemcpy(w, weights, nP * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(order, horder, (size_t)count * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemset(loss, 0, sizeof(float)) != cudaSuccess ||
+       launch_train_step(t->ts, count, w, order, 0, count, pos_weight, part, part + nparts * nP, grad, loss, 0) !=
+           cudaSuccess ||
+       cudaMemcpy(grad_out, grad, nP * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess ||
+       (loss_out && cudaMemcpy(loss_out, loss, sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)))
+    rs = RAPID_ECUDA;
+  cudaFree(d);
+  cudaFree(part);
   cudaFree(order);
   std::free(horder);
   return rs;

@@ -515,10 +515,18 @@ size_t scorer_dev_bytes();
 cudaError_t launch_features(const StageArgs &a, const ImageDesc &im, int L, float *out, cudaStream_t s);
 cudaError_t launch_score(const StageArgs &a, const ImageDesc &im, int L, const ScorerDev &W, float threshold,
                          float *score, unsigned char *mask, cudaStream_t s);
+// Training samples of one logged stage of one image, appended in block order (scratch:
+// collect_scratch_ints(nbx * nby) ints of device memory).
+size_t collect_scratch_ints(long long blocks);
 cudaError_t launch_collect(const float *feat, const int *before, const int *after, int nbx, int nby, int img,
-                           int stage, float neg_rate, const TrainSet &ts, cudaStream_t s);
+                           int stage, float neg_rate, const TrainSet &ts, int *scratch, cudaStream_t s);
+// One minibatch: samples order[(off + b) % n], b < batch; grad = the sum of their gradients
+// at the master weights w (summed in a fixed order), *loss += the sum of their losses.
+// part: train_max_ctas() * RAPID_SCORER_PARAMS floats, part_loss: train_max_ctas() floats.
+int train_max_ctas();
 cudaError_t launch_train_step(const TrainSet &ts, int n, const float *w, const int *order, int off, int batch,
-                              float pos_weight, float *grad, float *loss, cudaStream_t s);
+                              float pos_weight, float *part, float *part_loss, float *grad, float *loss,
+                              cudaStream_t s);
 cudaError_t launch_adam(float *w, float *m, float *v, float *grad, float lr, float bc1, float bc2, float inv_batch,
                         cudaStream_t s);
 

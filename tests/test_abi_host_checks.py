@@ -46,6 +46,7 @@ def _null_calls(pkg):
         "rapid_set_stage_shapes": (None, None, 0),
         "rapid_autotune": (None, None, None),
         "rapid_set_scorer": (None, None, C.c_float(0.5)),
+        "rapid_set_keep_mask": (None, 0, 0, buf, 16, 0),
         "rapid_set_classifier": (None, None),
         "rapid_read_features": (None, 0, buf),
         "rapid_scorer_features": (None, 0, buf),
@@ -53,6 +54,8 @@ def _null_calls(pkg):
         "rapid_set_logging": (None, None),
         "rapid_trainer_count": (None, C.byref(i64), C.byref(i64)),
         "rapid_trainer_fit": (None, 1, 1, C.c_float(1e-3), C.c_float(1.0), 0, None, buf, None),
+        "rapid_trainer_samples": (None, 0, 1, buf, buf, buf),
+        "rapid_trainer_gradient": (None, buf, 0, 1, C.c_float(1.0), buf, None),
         "rapid_refine_slide": (None, buf, 8, 8, 24, 64, 16, 0, buf, 32, None, 0, None, None),
         "rapid_simple_table": (None,),
         "rapid_create": (None, None, None),
@@ -73,6 +76,18 @@ def test_null_handles_are_refused(pkg):
                     if n not in ("rapid_default_params", "rapid_status_string", "rapid_destroy",
                                  "rapid_trainer_destroy", "rapid_trainer_create", "rapid_run_static")}
     assert takes_handle <= set(calls), sorted(takes_handle - set(calls))
+
+
+def test_static_entry_refuses_non_boolean_flags(pkg):
+    """rapid_run_static takes the same 0/1 flags as rapid_create and refuses other values
+    before any CUDA call."""
+    L = pkg.lib()
+    fake = C.c_void_p(256)
+    M = C.c_int32()
+    for flag in ("use_filter", "skip_tiles", "verify_filter", "predict", "reuse", "importance_rule", "schedule"):
+        p = pkg.rapid_default_params(**{flag: 2})
+        assert L.rapid_run_static(C.byref(p), fake, 8, 8, 24, fake, 32, fake, 16, C.byref(M), None) == \
+            pkg.RAPID_EINVAL, flag
 
 
 BAD = [dict(num_levels=0), dict(num_levels=9), dict(num_levels=2, ratio_C=3), dict(num_levels=2, ratio_C=1),

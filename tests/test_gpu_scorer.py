@@ -215,3 +215,136 @@ def test_pruned_batch_equals_pruned_single_runs():
         lab, _, cnt = _run(x, W, 0.5, **p)
         np.testing.assert_array_equal(got[i][0], lab)
         np.testing.assert_array_equal(got[i][1], cnt)
+
+
+def _log(imgs, K, trainer):
+    import torch
+
+    import paper_1704_02083_gb300 as pkg
+
+    with pkg.Context(stream=torch.cuda.current_stream(), **PARAMS) as ctx:
+        ctx.set_logging(trainer)
+        ctx.set_images([torch.from_numpy(x).cuda() for x in imgs], K)
+        ctx.run()
+        ctx.sync()
+        ctx.set_logging(None)
+
+
+def test_logging_and_training_are_reproducible():
+    """The same runs log the same samples in the same slots, and the same seed trains
+    bit-identical weights (samples take their slots in block order, gradients are summed
+    in a fixed order)."""
+    import paper_1704_02083_gb300 as pkg
+
+    imgs = [synth.he_image(160, 160, 10, 70 + i).rgb for i in range(2)]
+    K = [60, 60]
+    out = []
+    for rep in range(2):
+        with pkg.Trainer(100_000, neg_rate=0.3) as tr:
+            _log(imgs, K, tr)
+            n, pos = tr.count()
+            x, inb, y = tr.samples(0, int(n))
+            w, loss = tr.fit(epochs=3, batch=512, lr=3e-3, pos_weight=3.0, seed=5)
+            out.append((n, x, inb, y, w, loss))
+    (n0, x0, i0, y0, w0, l0), (n1, x1, i1, y1, w1, l1) = out
+    assert n0 == n1 and n0 > 500
+    np.testing.assert_array_equal(x0, x1)
+    np.testing.assert_array_equal(i0, i1)
+    np.testing.assert_array_equal(y0, y1)
+    assert w0.tobytes() == w1.tobytes()
+    assert l0.tobytes() == l1.tobytes()
+
+
+def _bits(v, p):
+    return (int(v) >> p) & 1
+
+
+def _grad_float64(W, x, inb, y, pos_weight):
+    """Summed loss gradient of samples (x: n x 7 x 7 x 9 patches, inb: in-image bits, y:
+    labels), restated from the net's definition in float64: bf16 weights, inputs and
+    activations, fp32 biases, zero padding outside the image at every layer, the roundings
+    passed through by the backward pass.  Layout of W: w1 (16 x 9 x 3 x 3), b1 (16),
+    w2 (16 x 16 x 3 x 3), b2 (16), w3 (16 x 3 x 3), b3."""
+    w1 = _bf16(W[:1296]).reshape(16, 9, 3, 3).astype(np.float64)
+    b1 = W[1296:1312].astype(np.float64)
+    w2 = _bf16(W[1312:3616]).reshape(16, 16, 3, 3).astype(np.float64)
+    b2 = W[3616:3632].astype(np.float64)
+    w3 = _bf16(W[3632:3776]).reshape(16, 3, 3).astype(np.float64)
+    b3 = float(W[3776])
+    g = dict(w1=np.zeros_like(w1), b1=np.zeros(16), w2=np.zeros_like(w2), b2=np.zeros(16), w3=np.zeros_like(w3),
+             b3=0.0)
+    loss = 0.0
+    for s in range(x.shape[0]):
+        X = _bf16(x[s]).astype(np.float64)  # 7 x 7 x 9
+        inside = np.array([[_bits(inb[s], r * 7 + c) for c in range(7)] for r in range(7)], bool)
+        z1 = np.zeros((7, 7, 16))
+        h1 = np.zeros((7, 7, 16))
+        for r in range(1, 6):
+            for c in range(1, 6):
+                z1[r, c] = b1 + np.einsum("abk,kcab->c", X[r - 1:r + 2, c - 1:c + 2], w1.transpose(1, 0, 2, 3))
+                if inside[r, c]:
+                    h1[r, c] = _bf16(np.maximum(z1[r, c], 0).astype(np.float32))
+        z2 = np.zeros((7, 7, 16))
+        h2 = np.zeros((7, 7, 16))
+        for r in range(2, 5):
+            for c in range(2, 5):
+                z2[r, c] = b2 + np.einsum("abk,kcab->c", h1[r - 1:r + 2, c - 1:c + 2], w2.transpose(1, 0, 2, 3))
+                if inside[r, c]:
+                    h2[r, c] = _bf16(np.maximum(z2[r, c], 0).astype(np.float32))
+        z3 = b3 + np.einsum("abk,kab->", h2[2:5, 2:5], w3)
+        p = 1.0 / (1.0 + np.exp(-z3))
+        pos = y[s] > 0.5
+        # the loss as training reports it: p in float32, whose 1 - p saturates (clamped at 1e-12)
+        p32 = np.float32(1) / (np.float32(1) + np.exp(np.float32(-z3)))
+        loss += -pos_weight * np.log(max(float(p32), 1e-12)) if pos else -np.log(max(float(np.float32(1) - p32), 1e-12))
+        dz3 = pos_weight * (p - 1.0) if pos else p
+        g["b3"] += dz3
+        g["w3"] += dz3 * h2[2:5, 2:5].transpose(2, 0, 1)
+        d2 = np.zeros((7, 7, 16))
+        for r in range(2, 5):
+            for c in range(2, 5):
+                if inside[r, c]:
+                    d2[r, c] = np.where(z2[r, c] > 0, dz3 * w3[:, r - 2, c - 2], 0.0)
+        d1 = np.zeros((7, 7, 16))
+        for r in range(2, 5):
+            for c in range(2, 5):
+                g["b2"] += d2[r, c]
+                g["w2"] += np.einsum("o,abi->oiab", d2[r, c], h1[r - 1:r + 2, c - 1:c + 2])
+                for ty in range(3):
+                    for tx in range(3):
+                        d1[r - 1 + ty, c - 1 + tx] += w2[:, :, ty, tx].T @ d2[r, c]
+        for r in range(1, 6):
+            for c in range(1, 6):
+                d1[r, c] = np.where(inside[r, c] & (z1[r, c] > 0), d1[r, c], 0.0)
+                g["b1"] += d1[r, c]
+                g["w1"] += np.einsum("o,abi->oiab", d1[r, c], X[r - 1:r + 2, c - 1:c + 2])
+    flat = np.concatenate([g["w1"].ravel(), g["b1"], g["w2"].ravel(), g["b2"], g["w3"].ravel(), [g["b3"]]])
+    return flat, loss
+
+
+def test_training_gradient_matches_a_float64_restatement():
+    """rapid_trainer_gradient (the gradient training follows) against the net's forward and
+    backward pass restated in float64, on 48 logged samples at seeded weights with active
+    units in every layer.  Tolerance: per parameter group, 2e-3 of the group's largest
+    gradient (float32 sums against float64; an activation on a bf16 rounding boundary can
+    round the other way)."""
+    import paper_1704_02083_gb300 as pkg
+
+    imgs = [synth.he_image(128, 128, 8, 90).rgb]
+    with pkg.Trainer(50_000, neg_rate=0.5) as tr:
+        _log(imgs, [40], tr)
+        n, pos = tr.count()
+        assert n >= 48 and pos > 0
+        x, inb, y = tr.samples(0, 48)
+        W = _random_weights(17)
+        g, loss = tr.gradient(W, 0, 48, pos_weight=2.5)
+        g2, _ = tr.gradient(W, 0, 48, pos_weight=2.5)
+    assert g.tobytes() == g2.tobytes()
+    ref, rloss = _grad_float64(W, x, inb, y, 2.5)
+    assert abs(loss - rloss) <= 1e-3 * abs(rloss) + 1e-3
+    groups = [(0, 1296), (1296, 1312), (1312, 3616), (3616, 3632), (3632, 3776), (3776, 3777)]
+    for a, b in groups:
+        scale = np.abs(ref[a:b]).max()
+        assert scale > 0, (a, b)
+        err = np.abs(g[a:b] - ref[a:b]).max()
+        assert err <= 2e-3 * scale + 1e-6, f"parameters {a}..{b}: {err} against scale {scale}"

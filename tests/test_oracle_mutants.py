@@ -37,6 +37,7 @@ LV = "test_oracle_levels.py"
 MG = "test_oracle_merge.py"
 FF = "test_oracle_fifo.py"
 SP = "test_oracle_simple_point.py"
+PR = "test_oracle_pruned.py"
 
 
 class Mutant(NamedTuple):
@@ -207,6 +208,22 @@ MUTANTS += [
            (FF,)),
     Mutant("fifo_queues_every_block", "the first queue holds the boundary blocks",
            "      if (eligible(st, bx, by, label_at(st, bx, by))) {", "      {", (FF,)),
+]
+
+MUTANTS += [
+    # pruned sweeps (a keep mask per stage, the mode the learned scorer drives)
+    Mutant("keep_mask_ignored", "a block the mask leaves out is not tested",
+           "if (st->pruned && !st->keep[st->cur][(int64_t)by * st->nbx + bx]) return 0;", "", (PR,)),
+    Mutant("keep_mask_before_eligible_count", "pruned blocks still count as eligible",
+           "  (*elig)++;\n  /* pruned sweeps",
+           "  if (st->pruned && !st->keep[st->cur][(int64_t)by * st->nbx + bx]) return 0;\n  (*elig)++;\n  /* pruned sweeps",
+           (PR,)),
+    Mutant("pruned_no_fallback", "a converged pruned stage goes on with full sweeps",
+           "      st->pruned = 0; /* the fallback: full sweeps from here on */", "      break;", (PR,)),
+    Mutant("pruned_fallback_skipped_sweep_count", "every sweep counts against max_sweeps",
+           "    st->cnt[st->cur][C_SWEEPS]++;\n    if (changes == 0) {\n      if (!st->pruned) break;",
+           "    if (changes == 0) {\n      if (!st->pruned) { st->cnt[st->cur][C_SWEEPS]++; break; }",
+           (PR,)),
 ]
 
 CONTROL_PINS = tuple(sorted({p for m in MUTANTS for p in m.pins}))
