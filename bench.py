@@ -30,6 +30,8 @@ sys.path.insert(0, ROOT)
 METRIC = "Mpixel/s superpixel refinement (bit-exact) plain vs learned; % of HBM roofline"
 UNIT = "Mpixel/s"
 DEFAULT_WORKLOAD = "he4096_k4096_l3"
+BATCH_WORKLOAD = "batch64_l3"   # the batched sub-object of the default line
+DEFAULT_PRUNE = 0.2             # the learned sub-object's threshold
 L2_FLUSH_BYTES = 256 << 20
 SAMPLE_SIDE = 1024  # CPU legs: a 1024 x 1024 tile of the same generator and parameters
 
@@ -53,6 +55,8 @@ def parse():
                     help="pinned launch geometry instead of autotuning: 'grid,grid,...:shape,shape,...' per stage")
     ap.add_argument("--prune", type=float, default=None,
                     help="the learned path: train the block scorer (untimed) and prune at this threshold")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="the plain line alone, without the learned and batched sub-objects")
     ap.add_argument("--classifier", action="store_true",
                     help="fit the linear classifier of Eq. predict on the superpixel features (untimed) and use it")
     return ap.parse_args()
@@ -137,6 +141,21 @@ def time_oracle(rgb, params, reps=1):
         o.run()
         ts.append(time.perf_counter() - t)
     return ts
+
+
+def time_oracle_all_cores(rgb, params, reps=1):
+    """The oracle's OpenMP build on every core this process may use: (seconds of the last
+    run, threads)."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle
+    threads = len(os.sched_getaffinity(0))
+    t = None
+    for _ in range(reps):
+        o = oracle.Oracle(rgb, omp=True, threads=threads, **params)
+        t0 = time.perf_counter()
+        o.run()
+        t = time.perf_counter() - t0
+    return t, o.threads
 
 
 # ---------------------------------------------------------------- clocks
@@ -227,8 +246,8 @@ def kernel_source_sha256(csrc=None):
     trailing blanks and empty lines removed, so that editing a comment keeps the counters."""
     csrc = csrc or os.path.join(ROOT, "paper_1704_02083_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("stage_impl.cuh", "eval_tile.cuh", "rapid_dev.cuh", "k_stage_s0.cu", "k_stage_s1.cu",
-                 "k_stage_s2.cu"):
+    for name in ("stage_impl.cuh", "eval_tile.cuh", "eval_sweep.cuh", "rapid_dev.cuh", "k_stage_s0.cu",
+                 "k_stage_s1.cu", "k_stage_s2.cu"):
         for line in open(os.path.join(csrc, name), encoding="utf-8"):
             code = line.split("//", 1)[0].rstrip()
             if code:
@@ -294,29 +313,43 @@ def golden_parity(workload: str, imgs, ctx, gpath=None):
 
 # ---------------------------------------------------------------- arms
 def run_reference(args, rank, world):
+    """The reference arm: the oracle (the method has no published implementation) on every
+    host core (its OpenMP build), each step one run of the workload itself; when W + K runs
+    of it would take more than about four minutes, each step is the bounded 1024^2 sample
+    instead (stated in `sample`)."""
     if rank != 0:
         return
-    rgb, params, desc = cpu_sample(args.workload)
+    imgs, Ks, params = load_workload(args.workload)
+    if len(imgs) == 1:
+        rgb, params = imgs[0], dict(params, K=Ks[0])
+        desc = f"the workload itself ({rgb.shape[0]}x{rgb.shape[1]}, K={params['K']}), one full run per step"
+    else:
+        rgb, params, desc = cpu_sample(args.workload)
+    t_first, threads = time_oracle_all_cores(rgb, params)
+    if t_first * (args.warmup + args.steps) > 240.0 and rgb.shape[0] * rgb.shape[1] > SAMPLE_SIDE ** 2:
+        rgb, params, desc = cpu_sample(args.workload)
+        t_first, threads = time_oracle_all_cores(rgb, params)
     npx = rgb.shape[0] * rgb.shape[1]
-    ts = time_oracle(rgb, params, reps=args.warmup + args.steps)[args.warmup:]
+    ts = [t_first] + [time_oracle_all_cores(rgb, params)[0] for _ in range(args.warmup + args.steps - 1)]
+    ts = ts[args.warmup:] if args.steps > 0 else ts
     total = sum(ts)
     value = npx * len(ts) / total / 1e6
+    cpu = {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle (OpenMP build, every host core)",
+           "sample": desc, **dict(host_cpu(), threads_used=threads)}
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ts),
+        "steps": len(ts), "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ts),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": args.workload, "sample": desc},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, **host_cpu()},
+        "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
 def run_rapid(args, rank, world, local):
-    import numpy as np
     import torch
 
     import __graft_entry__
-    import paper_1704_02083_gb300 as pkg
 
     __graft_entry__.build()
     torch.cuda.set_device(local)
@@ -324,16 +357,66 @@ def run_rapid(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    out = measure(args, rank, world, local, dist, args.workload, args.prune, args.classifier, args.geometry)
+    extras = (not args.no_extra and args.workload == DEFAULT_WORKLOAD and args.prune is None
+              and not args.classifier and not args.geometry)
+    if extras:  # plain vs learned vs batched, side by side in the same line
+        learned = measure(args, rank, world, local, dist, args.workload, DEFAULT_PRUNE, False, None)
+        batched = measure(args, rank, world, local, dist, BATCH_WORKLOAD, None, False, None)
+        if rank == 0:
+            out["learned"] = sub_line(learned)
+            out["batched"] = sub_line(batched)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baselines(args.workload)
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
 
-    imgs, Ks, params = load_workload(args.workload)
+
+def sub_line(m):
+    """The parts of a measurement that a side-by-side sub-object keeps."""
+    keep = ("value", "unit", "ms_per_step", "ms_per_step_median", "roofline", "e2e", "gpu_launches", "clocks")
+    out = {k: m[k] for k in keep if k in m}
+    out["config"] = {k: m["config"].get(k) for k in ("workload", "images", "pixels", "K_total", "M_total", "path",
+                                                       "scorer", "parity", "stage_grids", "stage_tiles",
+                                                       "cuda_graph")}
+    return out
+
+
+def cpu_baselines(workload: str):
+    """The oracle on the host cores: single-threaded and on every core (OpenMP over the
+    blocks of a phase), each timing one run of the workload itself."""
+    imgs, Ks, params = load_workload(workload)
+    if len(imgs) != 1:
+        rgb, params, desc = cpu_sample(workload)
+    else:
+        rgb, params = imgs[0], dict(params, K=Ks[0])
+        desc = f"the workload itself ({rgb.shape[0]}x{rgb.shape[1]}, K={params['K']}), one full run"
+    npx = rgb.shape[0] * rgb.shape[1]
+    t1 = time_oracle(rgb, params, reps=1)[0]
+    tn, threads = time_oracle_all_cores(rgb, params)
+    return {"value": npx / t1 / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, **host_cpu(),
+            "all_cores": {"value": npx / tn / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle (OpenMP build)",
+                          "sample": desc, "speedup_over_one_core": t1 / tn}}
+
+
+def measure(args, rank, world, local, dist, workload, prune, use_classifier, geometry):
+    """One workload's measurement (the JSON line without the CPU baseline)."""
+    import numpy as np
+    import torch
+
+    import paper_1704_02083_gb300 as pkg
+
+    imgs, Ks, params = load_workload(workload)
     n = len(imgs)
     scorer = None
-    if args.prune is not None:  # the learned path: move logs of plain runs on other seeds, then training
+    if prune is not None:  # the learned path: move logs of plain runs on other seeds, then training
         from paper_1704_02083_gb300 import scorer as sc
         w_scorer, train_info = sc.collect_and_train(*sc.training_tiles())
-        scorer = dict(threshold=args.prune, train=train_info)
+        scorer = dict(threshold=prune, train=train_info)
     classifier = None
-    if args.classifier:  # features and ground truth at the prediction point of other seeds, then the fit
+    if use_classifier:  # features and ground truth at the prediction point of other seeds, then the fit
         from paper_1704_02083_gb300 import roi
         theta, cls_info = roi.train()
         classifier = dict(train=cls_info)
@@ -346,11 +429,11 @@ def run_rapid(args, rank, world, local):
     ctx = pkg.Context(stream=stream, **params)
     ctx.set_images(dev_imgs, Ks)
     if scorer is not None:
-        ctx.set_scorer(w_scorer, args.prune)
+        ctx.set_scorer(w_scorer, prune)
     if classifier is not None:
         ctx.set_classifier(theta)
-    if args.geometry:
-        g_str, s_str = args.geometry.split(":")
+    if geometry:
+        g_str, s_str = geometry.split(":")
         grids, shapes = [int(x) for x in g_str.split(",")], [int(x) for x in s_str.split(",")]
         ctx.set_stage_grids(grids)
         ctx.set_stage_shapes(shapes)
@@ -413,7 +496,7 @@ def run_rapid(args, rank, world, local):
             e2e_ctx.set_stage_grids(grids)
             e2e_ctx.set_stage_shapes(shapes)
         if scorer is not None:
-            e2e_ctx.set_scorer(w_scorer, args.prune)
+            e2e_ctx.set_scorer(w_scorer, prune)
         ptrs = [p.data_ptr() for p in pins]
         times = []
         for it in range(args.warmup + args.steps):
@@ -436,11 +519,14 @@ def run_rapid(args, rank, world, local):
     # golden hashes (written by tests/golden/make_golden.py from the oracle alone)
     parity = None
     if scorer is None and classifier is None:
-        parity = golden_parity(args.workload, imgs, ctx)
+        parity = golden_parity(workload, imgs, ctx)
+    elif scorer is not None:
+        parity = ("pruned sweeps bit-exact vs the oracle under the same keep masks (tests/test_gpu_keep_mask.py); "
+                  "the masks here are the scorer's, judged by quality against the plain run")
 
     if scorer is not None:  # judged by the plain method: its labels, and the ground truth
         from paper_1704_02083_gb300 import quality, synth
-        gts = [synth.workload_image(args.workload).regions] if n == 1 else None
+        gts = [synth.workload_image(workload).regions] if n == 1 else None
         plain = pkg.Context(stream=stream, **params)
         plain.set_images(dev_imgs, Ks)
         plain.run()
@@ -460,14 +546,14 @@ def run_rapid(args, rank, world, local):
 
     if classifier is not None and n == 1 and rank == 0:  # judged against the brightness stand-in (untimed)
         from paper_1704_02083_gb300 import roi, synth
-        classifier["eval"] = roi.evaluate(theta, synth.workload_image(args.workload), Ks[0], dict(params),
+        classifier["eval"] = roi.evaluate(theta, synth.workload_image(workload), Ks[0], dict(params),
                                           stream=stream)
         classifier["parity"] = "bit-exact vs the oracle in tests/test_gpu_classifier.py (features, y, runs)"
 
     sched_quality = None
     if params.get("schedule", 0) == 1 and n == 1 and rank == 0:  # judged by the sweep schedule (untimed)
         from paper_1704_02083_gb300 import quality, synth
-        gt = synth.workload_image(args.workload).regions
+        gt = synth.workload_image(workload).regions
         sw = pkg.Context(stream=stream, **dict(params, schedule=0))
         sw.set_images(dev_imgs, Ks)
         sw.run()
@@ -481,13 +567,6 @@ def run_rapid(args, rank, world, local):
         sched_quality = {k: (round(v, 5) if isinstance(v, float) else v) for k, v in sched_quality.items()}
         sw.close()
 
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        rgb_s, params_s, desc = cpu_sample(args.workload)
-        ts = time_oracle(rgb_s, params_s, reps=1)
-        cpu = {"value": rgb_s.shape[0] * rgb_s.shape[1] / ts[0] / 1e6, "unit": UNIT, "cores": 1,
-               "kind": "oracle", "sample": desc, **host_cpu()}
-
     # roofline of the dominant launch: the stage launch with the largest device time (the
     # finest stage); its duration from CUDA events around each stage launch on ``stream``
     peak, peak_kind = measured_peak()
@@ -497,10 +576,11 @@ def run_rapid(args, rank, world, local):
     achieved = launch_bytes / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else None
     all_ms, all_bytes = sum(stage_ms), sum(stage_bytes)
     all_achieved = all_bytes / (all_ms / 1e3) / 1e9 if all_ms > 0 else None
-    traffic, _ = kernel_traffic(args.workload)
+    traffic, _ = kernel_traffic(workload)
     st_dom = c1.stage[dom]
+    out = None
     if rank == 0:
-        cfg = {"workload": args.workload, "images": n, "pixels": npx, "K_total": int(sum(Ks)),
+        cfg = {"workload": workload, "images": n, "pixels": npx, "K_total": int(sum(Ks)),
                "M_total": int(sum(ctx.image_info(i)["M"] for i in range(n))),
                "levels": params["num_levels"], "ratio_C": params["ratio_C"], "init_block": params["init_block"],
                "final_grain": params["final_grain"], "size_mode": params["size_mode"],
@@ -533,15 +613,13 @@ def run_rapid(args, rank, world, local):
                                                 "alg_bytes_per_step": all_bytes / args.steps,
                                                 "achieved": all_achieved,
                                                 "frac": (all_achieved / peak) if all_achieved else None}},
-            "cpu_baseline": cpu,
+            "cpu_baseline": None,
             "e2e": e2e,
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clk,
         }
-        print(json.dumps(out), flush=True)
     ctx.close()
-    if dist is not None:
-        dist.destroy_process_group()
+    return out
 
 
 def run_slide(args, rank, world, local):

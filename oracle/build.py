@@ -11,34 +11,38 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
+LIB_OMP = os.path.join(OUT_DIR, "liboracle_omp.so")  # the same source, phase decisions on all cores
 SRC = [os.path.join(HERE, "rapid_oracle.c")]
 HDR = [os.path.join(HERE, "rapid_oracle.h")]
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in SRC + HDR + [__file__])
 
 
-def compile_to(out: str, sources=SRC) -> str:
-    """Compile the oracle's C sources into the shared library ``out``."""
+def compile_to(out: str, sources=SRC, openmp: bool = False) -> str:
+    """Compile the oracle's C sources into the shared library ``out`` (with ``openmp`` the
+    decisions of a phase run on all cores: -fopenmp -DORC_OPENMP)."""
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-Wall", "-Wextra", "-Wno-unused-parameter", "-o", out] + list(sources) + ["-lm"]
+           "-Wall", "-Wextra", "-Wno-unused-parameter"] + (["-fopenmp", "-DORC_OPENMP"] if openmp else []) + \
+          ["-o", out] + list(sources) + ["-lm"]
     subprocess.run(cmd, check=True)
     return out
 
 
-def build(force: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
+def build(force: bool = False, openmp: bool = False) -> str:
+    lib = LIB_OMP if openmp else LIB
+    if not force and not _stale(lib):
+        return lib
     os.makedirs(OUT_DIR, exist_ok=True)
-    tmp = LIB + f".tmp{os.getpid()}"
-    compile_to(tmp)
-    os.replace(tmp, LIB)
-    return LIB
+    tmp = lib + f".tmp{os.getpid()}"
+    compile_to(tmp, openmp=openmp)
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force=True))
+    print(build(force=True), build(force=True, openmp=True))

@@ -38,10 +38,9 @@ DEFAULTS = dict(num_levels=1, ratio_C=4, init_block=16, final_grain=1, K=200, si
 _lib = None
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        path = _build.build()
+def _load(path):
+    """Bind the oracle functions of the shared library at ``path``."""
+    if True:
         L = C.CDLL(path)
         P = C.c_void_p
         i32p, i64p = C.POINTER(C.c_int32), C.POINTER(C.c_int64)
@@ -78,8 +77,29 @@ def lib():
                      "orc_read_labels", "orc_read_stats", "orc_read_counters", "orc_read_pyramid",
                      "orc_level_dims", "orc_simple_lut", "orc_set_classifier", "orc_read_features"):
             getattr(L, name).restype = C.c_int32
-        _lib = L
+        L.orc_set_threads.argtypes = [C.c_int32]
+        L.orc_set_threads.restype = C.c_int32
+    return L
+
+
+def lib():
+    """The oracle (single-threaded build)."""
+    global _lib
+    if _lib is None:
+        _lib = _load(_build.build())
     return _lib
+
+
+_lib_omp = None
+
+
+def lib_omp():
+    """The same oracle with the decisions of a phase on all cores (OpenMP build); its
+    results equal lib()'s for any thread count."""
+    global _lib_omp
+    if _lib_omp is None:
+        _lib_omp = _load(_build.build(openmp=True))
+    return _lib_omp
 
 
 def params(**kw) -> OrcParams:
@@ -100,21 +120,25 @@ def simple_lut() -> np.ndarray:
 class Oracle:
     """One image, one parameter set; mirrors the steps of Algorithm RAPID."""
 
-    def __init__(self, rgb: np.ndarray, **kw):
+    def __init__(self, rgb: np.ndarray, omp: bool = False, threads: int = 0, **kw):
+        """omp: the OpenMP build (phase decisions on `threads` cores, 0 = all)."""
+        self._L = lib_omp() if omp else lib()
+        if omp:
+            self.threads = self._L.orc_set_threads(int(threads))
         rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
         assert rgb.ndim == 3 and rgb.shape[2] == 3
         self.H, self.W = int(rgb.shape[0]), int(rgb.shape[1])
         self.p = params(**kw)
         st = C.c_int32(0)
         self._rgb = rgb
-        self.h = lib().orc_create(rgb.ctypes.data, self.H, self.W, C.byref(self.p), C.byref(st))
+        self.h = self._L.orc_create(rgb.ctypes.data, self.H, self.W, C.byref(self.p), C.byref(st))
         if not self.h:
             raise ValueError(f"orc_create failed with status {st.value}")
 
     def __del__(self):
         h = getattr(self, "h", None)
         if h:
-            lib().orc_destroy(h)
+            self._L.orc_destroy(h)
             self.h = None
 
     def _ok(self, r):
@@ -122,95 +146,95 @@ class Oracle:
             raise RuntimeError(f"oracle call failed with status {r}")
 
     def num_stages(self) -> int:
-        return lib().orc_num_stages(self.h)
+        return self._L.orc_num_stages(self.h)
 
     def stages(self):
         out = []
         for i in range(self.num_stages()):
             lv, s = C.c_int32(), C.c_int32()
-            self._ok(lib().orc_stage_info(self.h, i, C.byref(lv), C.byref(s)))
+            self._ok(self._L.orc_stage_info(self.h, i, C.byref(lv), C.byref(s)))
             out.append((lv.value, s.value))
         return out
 
     def seed(self):
-        self._ok(lib().orc_seed(self.h))
+        self._ok(self._L.orc_seed(self.h))
 
     def phase(self, ph: int):
         mv, mg = C.c_int64(), C.c_int64()
-        self._ok(lib().orc_phase(self.h, ph, C.byref(mv), C.byref(mg)))
+        self._ok(self._L.orc_phase(self.h, ph, C.byref(mv), C.byref(mg)))
         return mv.value, mg.value
 
     def phase_moves(self, ph: int):
         mv, rq = C.c_int64(), C.c_int64()
-        self._ok(lib().orc_phase_moves(self.h, ph, C.byref(mv), C.byref(rq)))
+        self._ok(self._L.orc_phase_moves(self.h, ph, C.byref(mv), C.byref(rq)))
         return mv.value, rq.value
 
     def phase_merges(self):
         mg = C.c_int64()
-        self._ok(lib().orc_phase_merges(self.h, C.byref(mg)))
+        self._ok(self._L.orc_phase_merges(self.h, C.byref(mg)))
         return mg.value
 
     def pending_requests(self, cap: int = 1 << 20):
         blk = np.empty(cap, np.int64)
         lab = np.empty(cap, np.int32)
-        n = lib().orc_pending_requests(self.h, blk.ctypes.data, lab.ctypes.data, cap)
+        n = self._L.orc_pending_requests(self.h, blk.ctypes.data, lab.ctypes.data, cap)
         return blk[:n].copy(), lab[:n].copy()
 
     def refine_stage(self):
-        self._ok(lib().orc_refine_stage(self.h))
+        self._ok(self._L.orc_refine_stage(self.h))
 
     def next_stage(self):
-        self._ok(lib().orc_next_stage(self.h))
+        self._ok(self._L.orc_next_stage(self.h))
 
     def run(self):
-        self._ok(lib().orc_run(self.h))
+        self._ok(self._L.orc_run(self.h))
         return self
 
     def run_fifo(self):
-        self._ok(lib().orc_run_fifo(self.h))
+        self._ok(self._L.orc_run_fifo(self.h))
         return self
 
     def set_classifier(self, theta):
         """Eq. predict with h = theta[0] + theta[1:] . F (None: the brightness stand-in)."""
         if theta is None:
-            self._ok(lib().orc_set_classifier(self.h, None))
+            self._ok(self._L.orc_set_classifier(self.h, None))
             return self
         self._theta = np.ascontiguousarray(theta, dtype=np.float64)
         assert self._theta.shape == (5,)
-        self._ok(lib().orc_set_classifier(self.h, self._theta.ctypes.data))
+        self._ok(self._L.orc_set_classifier(self.h, self._theta.ctypes.data))
         return self
 
     def set_keep_mask(self, stage: int, mask):
         """Pruned sweeps of stage `stage` with this keep mask over its block grid (nby x nbx,
         nonzero = kept); None sweeps the stage in full."""
         if mask is None:
-            self._ok(lib().orc_set_keep_mask(self.h, stage, None, 0))
+            self._ok(self._L.orc_set_keep_mask(self.h, stage, None, 0))
             return self
         m = np.ascontiguousarray(mask, dtype=np.uint8)
-        self._ok(lib().orc_set_keep_mask(self.h, stage, m.ctypes.data, m.size))
+        self._ok(self._L.orc_set_keep_mask(self.h, stage, m.ctypes.data, m.size))
         return self
 
     def features(self) -> np.ndarray:
         """M x 4 features of the last prediction: absolute brightness, comparative
         brightness, extra-region dissimilarity, intra-region dissimilarity."""
         out = np.zeros((self.grid()["M"], 4), np.float64)
-        self._ok(lib().orc_read_features(self.h, out.ctypes.data))
+        self._ok(self._L.orc_read_features(self.h, out.ctypes.data))
         return out
 
     def grid(self):
         v = [C.c_int32() for _ in range(6)]
-        lib().orc_get_grid(self.h, *[C.byref(x) for x in v])
+        self._L.orc_get_grid(self.h, *[C.byref(x) for x in v])
         return dict(zip(("stage", "nbx", "nby", "side", "level", "M"), [x.value for x in v]))
 
     def block_labels(self) -> np.ndarray:
         g = self.grid()
         out = np.empty((g["nby"], g["nbx"]), np.int32)
-        self._ok(lib().orc_read_block_labels(self.h, out.ctypes.data))
+        self._ok(self._L.orc_read_block_labels(self.h, out.ctypes.data))
         return out
 
     def labels(self) -> np.ndarray:
         out = np.empty((self.H, self.W), np.int32)
-        self._ok(lib().orc_read_labels(self.h, out.ctypes.data))
+        self._ok(self._L.orc_read_labels(self.h, out.ctypes.data))
         return out
 
     def stats(self):
@@ -219,27 +243,27 @@ class Oracle:
         s = np.empty((M, 7), np.int64)
         y = np.empty(M, np.int8)
         imp = np.empty(M, np.uint8)
-        self._ok(lib().orc_read_stats(self.h, s.ctypes.data, y.ctypes.data, imp.ctypes.data))
+        self._ok(self._L.orc_read_stats(self.h, s.ctypes.data, y.ctypes.data, imp.ctypes.data))
         return s, y, imp
 
     def counters(self) -> np.ndarray:
         n = self.num_stages()
         out = np.zeros((n, NCOUNT), np.int64)
-        self._ok(lib().orc_read_counters(self.h, out.ctypes.data))
+        self._ok(self._L.orc_read_counters(self.h, out.ctypes.data))
         return out
 
     def lambda_pos(self) -> float:
-        return lib().orc_lambda_pos(self.h)
+        return self._L.orc_lambda_pos(self.h)
 
     def level_dims(self, level: int):
         Wl, Hl, f = C.c_int32(), C.c_int32(), C.c_int32()
-        self._ok(lib().orc_level_dims(self.h, level, C.byref(Wl), C.byref(Hl), C.byref(f)))
+        self._ok(self._L.orc_level_dims(self.h, level, C.byref(Wl), C.byref(Hl), C.byref(f)))
         return Wl.value, Hl.value, f.value
 
     def pyramid(self, level: int) -> np.ndarray:
         Wl, Hl, _ = self.level_dims(level)
         out = np.empty((Hl, Wl, 6), np.int64)
-        self._ok(lib().orc_read_pyramid(self.h, level, out.ctypes.data))
+        self._ok(self._L.orc_read_pyramid(self.h, level, out.ctypes.data))
         return out
 
 

@@ -118,6 +118,21 @@ static int simple_by_bfs(unsigned mask) {
   return 1;
 }
 
+/* Threads of the phase decisions (an ORC_OPENMP build; ignored otherwise); returns the
+ * number in use. */
+#ifdef ORC_OPENMP
+#include <omp.h>
+#endif
+int32_t orc_set_threads(int32_t n) {
+#ifdef ORC_OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return (int32_t)omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 int32_t orc_simple_lut(uint8_t *dst256) {
   for (unsigned m = 0; m < 256; m++) dst256[m] = (uint8_t)simple_by_bfs(m);
   return 0;
@@ -536,18 +551,40 @@ int32_t orc_phase_moves(orc_state *st, int32_t phase, int64_t *moves_out, int64_
   int64_t nmv = 0;
   st->nreq = 0;
   int64_t *c = st->cnt[st->cur];
-  for (int32_t by = py; by < st->nby; by += 3)
-    for (int32_t bx = px; bx < st->nbx; bx += 3) {
-      int32_t k = -1;
-      int64_t blk = (int64_t)by * st->nbx + bx;
-      if (st->p.schedule == 1) { /* only queued blocks, which leave the queue */
-        if (!st->queued[blk]) continue;
-        st->queued[blk] = 0;
-      }
-      int r = decide(st, bx, by, cR, cG, cB, mX, mY, N0, &k, &c[C_ELIG], &c[C_EVAL]);
-      if (r == 1) { mv[nmv].blk = blk; mv[nmv].a = st->lab[blk]; mv[nmv].k = k; nmv++; }
-      if (r == 2) { st->req_blk[st->nreq] = blk; st->req_lab[st->nreq] = st->lab[blk]; st->nreq++; }
+  /* Every block of the phase decides on its own (their windows are disjoint and all read
+   * the phase snapshot): outcome r[j] and target k[j] of the class's j-th block, listed
+   * afterwards in block order.  Built with ORC_OPENMP the decisions run on all cores; the
+   * result is the same for any thread count. */
+  int64_t ncx = ceil_div(st->nbx - px > 0 ? st->nbx - px : 0, 3), ncy = ceil_div(st->nby - py > 0 ? st->nby - py : 0, 3);
+  int8_t *r = (int8_t *)malloc((size_t)nph);
+  int32_t *kk = (int32_t *)malloc(sizeof(int32_t) * (size_t)nph);
+  int64_t elig = 0, eval = 0;
+#ifdef ORC_OPENMP
+#pragma omp parallel for schedule(static) reduction(+ : elig, eval)
+#endif
+  for (int64_t j = 0; j < ncx * ncy; j++) {
+    int32_t by = py + 3 * (int32_t)(j / ncx), bx = px + 3 * (int32_t)(j % ncx);
+    int64_t blk = (int64_t)by * st->nbx + bx;
+    r[j] = 0;
+    kk[j] = -1;
+    if (st->p.schedule == 1) { /* only queued blocks, which leave the queue */
+      if (!st->queued[blk]) continue;
+      st->queued[blk] = 0;
     }
+    int64_t e = 0, v = 0;
+    r[j] = (int8_t)decide(st, bx, by, cR, cG, cB, mX, mY, N0, &kk[j], &e, &v);
+    elig += e;
+    eval += v;
+  }
+  c[C_ELIG] += elig;
+  c[C_EVAL] += eval;
+  for (int64_t j = 0; j < ncx * ncy; j++) {
+    int64_t blk = (int64_t)(py + 3 * (j / ncx)) * st->nbx + px + 3 * (j % ncx);
+    if (r[j] == 1) { mv[nmv].blk = blk; mv[nmv].a = st->lab[blk]; mv[nmv].k = kk[j]; nmv++; }
+    if (r[j] == 2) { st->req_blk[st->nreq] = blk; st->req_lab[st->nreq] = st->lab[blk]; st->nreq++; }
+  }
+  free(r);
+  free(kk);
   for (int64_t i = 0; i < nmv; i++) {
     apply_move(st, mv[i].blk, mv[i].a, mv[i].k);
     if (st->p.schedule == 1) queue_neighbours(st, mv[i].blk);
@@ -571,7 +608,20 @@ int32_t orc_phase_merges(orc_state *st, int64_t *merges_out) {
   int64_t nmerge = 0;
   if (st->nreq > 0) {
     int32_t *tgt = (int32_t *)malloc(sizeof(int32_t) * (size_t)st->nreq);
+#ifdef ORC_OPENMP
+    /* all-core build: one search per requested label (every block of a connected label
+     * reaches the same neighbours, so the target depends on the label alone) */
+    int32_t *memo = (int32_t *)malloc(sizeof(int32_t) * (size_t)M);
+    for (int32_t k = 0; k < M; k++) memo[k] = -2;
+    for (int64_t i = 0; i < st->nreq; i++) {
+      int32_t a = st->req_lab[i];
+      if (memo[a] == -2) memo[a] = merge_target(st, a, st->req_blk[i]);
+      tgt[i] = memo[a];
+    }
+    free(memo);
+#else
     for (int64_t i = 0; i < st->nreq; i++) tgt[i] = merge_target(st, st->req_lab[i], st->req_blk[i]);
+#endif
     uint8_t *inv = (uint8_t *)calloc((size_t)M, 1);
     int32_t *to = (int32_t *)malloc(sizeof(int32_t) * M);
     for (int32_t k = 0; k < M; k++) to[k] = -1;

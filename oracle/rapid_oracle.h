@@ -73,6 +73,10 @@ int32_t orc_read_pyramid(const orc_state *st, int32_t level, int64_t *dst6);
 int32_t orc_level_dims(const orc_state *st, int32_t level, int32_t *Wl, int32_t *Hl, int32_t *f);
 double orc_lambda_pos(const orc_state *st);
 int32_t orc_simple_lut(uint8_t *dst256);
+/* Threads of the phase decisions in a build with ORC_OPENMP (the all-core baseline): n > 0
+ * sets them; returns the number in use (1 in the plain build).  Results do not depend on
+ * it. */
+int32_t orc_set_threads(int32_t n);
 int32_t orc_run_fifo(orc_state *st);
 /* Eq. predict with the linear classifier theta[0] + theta[1..4] . F over the features F of
  * each superpixel (NULL: the integer brightness stand-in), and the features of the last
