@@ -31,7 +31,9 @@ METRIC = "Mpixel/s superpixel refinement (bit-exact) plain vs learned; % of HBM 
 UNIT = "Mpixel/s"
 DEFAULT_WORKLOAD = "he4096_k4096_l3"
 BATCH_WORKLOAD = "batch64_l3"   # the batched sub-object of the default line
-DEFAULT_PRUNE = 0.2             # the learned sub-object's threshold
+DEFAULT_PRUNE = 0.05            # the learned sub-object: threshold, and the stages it prunes
+DEFAULT_PRUNE_STAGES = "finest"  # (the finest stage alone: 0.37 points of boundary recall lost
+                                 # at 0.05 on the 4096^2 tile, profiles/scorer_sweep_he4096_k4096_l3.md)
 L2_FLUSH_BYTES = 256 << 20
 SAMPLE_SIDE = 1024  # CPU legs: a 1024 x 1024 tile of the same generator and parameters
 
@@ -55,6 +57,8 @@ def parse():
                     help="pinned launch geometry instead of autotuning: 'grid,grid,...:shape,shape,...' per stage")
     ap.add_argument("--prune", type=float, default=None,
                     help="the learned path: train the block scorer (untimed) and prune at this threshold")
+    ap.add_argument("--prune-stages", default="all", choices=["all", "finest"],
+                    help="the stages the learned path prunes")
     ap.add_argument("--no-extra", action="store_true",
                     help="the plain line alone, without the learned and batched sub-objects")
     ap.add_argument("--classifier", action="store_true",
@@ -357,11 +361,13 @@ def run_rapid(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    out = measure(args, rank, world, local, dist, args.workload, args.prune, args.classifier, args.geometry)
+    out = measure(args, rank, world, local, dist, args.workload, args.prune, args.classifier, args.geometry,
+                  args.prune_stages)
     extras = (not args.no_extra and args.workload == DEFAULT_WORKLOAD and args.prune is None
               and not args.classifier and not args.geometry)
     if extras:  # plain vs learned vs batched, side by side in the same line
-        learned = measure(args, rank, world, local, dist, args.workload, DEFAULT_PRUNE, False, None)
+        learned = measure(args, rank, world, local, dist, args.workload, DEFAULT_PRUNE, False, None,
+                          DEFAULT_PRUNE_STAGES)
         batched = measure(args, rank, world, local, dist, BATCH_WORKLOAD, None, False, None)
         if rank == 0:
             out["learned"] = sub_line(learned)
@@ -401,7 +407,22 @@ def cpu_baselines(workload: str):
                           "sample": desc, "speedup_over_one_core": t1 / tn}}
 
 
-def measure(args, rank, world, local, dist, workload, prune, use_classifier, geometry):
+def stage_count(params) -> int:
+    """Stages of the schedule: block sides halving from the initial block (at least the
+    coarsest level's factor) to the final grain, each on the coarsest level whose factor
+    divides it."""
+    L, C = params["num_levels"], params.get("ratio_C", 4)
+    f1 = C ** (L - 1)
+    s, n = max(params["init_block"], f1), 0
+    while s >= 1 and s >= params.get("final_grain", 1):
+        if not any(C ** (L - l) <= s for l in range(1, L + 1)):
+            break
+        n += 1
+        s //= 2
+    return max(n, 1)
+
+
+def measure(args, rank, world, local, dist, workload, prune, use_classifier, geometry, prune_stages="all"):
     """One workload's measurement (the JSON line without the CPU baseline)."""
     import numpy as np
     import torch
@@ -414,7 +435,7 @@ def measure(args, rank, world, local, dist, workload, prune, use_classifier, geo
     if prune is not None:  # the learned path: move logs of plain runs on other seeds, then training
         from paper_1704_02083_gb300 import scorer as sc
         w_scorer, train_info = sc.collect_and_train(*sc.training_tiles())
-        scorer = dict(threshold=prune, train=train_info)
+        scorer = dict(threshold=prune, stages=prune_stages, train=train_info)
     classifier = None
     if use_classifier:  # features and ground truth at the prediction point of other seeds, then the fit
         from paper_1704_02083_gb300 import roi
@@ -428,8 +449,14 @@ def measure(args, rank, world, local, dist, workload, prune, use_classifier, geo
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     ctx = pkg.Context(stream=stream, **params)
     ctx.set_images(dev_imgs, Ks)
+    stage_on = None
+    if prune_stages == "finest":
+        nst_p = stage_count(params)
+        stage_on = [0] * (nst_p - 1) + [1]
     if scorer is not None:
         ctx.set_scorer(w_scorer, prune)
+        if stage_on is not None:
+            ctx.set_scorer_stages(stage_on)
     if classifier is not None:
         ctx.set_classifier(theta)
     if geometry:
@@ -497,6 +524,8 @@ def measure(args, rank, world, local, dist, workload, prune, use_classifier, geo
             e2e_ctx.set_stage_shapes(shapes)
         if scorer is not None:
             e2e_ctx.set_scorer(w_scorer, prune)
+            if stage_on is not None:
+                e2e_ctx.set_scorer_stages(stage_on)
         ptrs = [p.data_ptr() for p in pins]
         times = []
         for it in range(args.warmup + args.steps):

@@ -272,6 +272,11 @@ rapid_status rapid_read_features(rapid_ctx *ctx, int32_t i, double *dst_host);
  * against it); with threshold 0 they are the same.  Synchronises. */
 rapid_status rapid_set_scorer(rapid_ctx *ctx, const float *weights, float threshold);
 
+/* The stages the scorer prunes: on[i] = 1 prunes stage i, 0 sweeps it in full without
+ * scoring; stages from n on are pruned (n = 0: every stage, the default).  EINVAL on a flag
+ * other than 0 and 1 or n outside [0, RAPID_MAX_STAGES]. */
+rapid_status rapid_set_scorer_stages(rapid_ctx *ctx, const int32_t *on, int32_t n);
+
 /* Pruned refinement with keep masks the caller gives instead of the scorer's: the same
  * pruned sweeps as rapid_set_scorer runs (a stage sweeps testing and deciding only the kept
  * eligible blocks until a sweep changes nothing, then sweeps every block until a sweep

@@ -106,6 +106,7 @@ def lib() -> C.CDLL:
         "rapid_set_stage_grids": (i32, [P, pi32, i32]),
         "rapid_set_scorer": (i32, [P, P, C.c_float]),
         "rapid_set_keep_mask": (i32, [P, i32, i32, P, i64, i32]),
+        "rapid_set_scorer_stages": (i32, [P, P, i32]),
         "rapid_set_classifier": (i32, [P, P]),
         "rapid_read_features": (i32, [P, i32, P]),
         "rapid_refine_slide": (i32, [P, P, i64, i64, i64, i32, i32, i32, P, i64, P, i64, pi64, pi32]),
@@ -303,6 +304,12 @@ def rapid_set_scorer(ctx: int, weights, threshold: float):
         return
     w = _f32(weights)
     _check(lib().rapid_set_scorer(ctx, w.ctypes.data, float(threshold)), "rapid_set_scorer")
+
+
+def rapid_set_scorer_stages(ctx: int, on):
+    """Which stages the scorer prunes (a sequence of 0/1 per stage; later stages are pruned)."""
+    a = np.ascontiguousarray(on, dtype=np.int32)
+    _check(lib().rapid_set_scorer_stages(ctx, a.ctypes.data if a.size else None, a.size), "rapid_set_scorer_stages")
 
 
 def rapid_set_keep_mask(ctx: int, i: int, s: int, mask):
@@ -599,6 +606,10 @@ class Context:
 
     def set_scorer(self, weights, threshold: float = 0.3):
         rapid_set_scorer(self.h, weights, threshold)
+
+    def set_scorer_stages(self, on):
+        rapid_set_scorer_stages(self.h, on)
+        return self
 
     def set_keep_mask(self, i: int, s: int, mask):
         """Image i's keep mask for stage s (pruned sweeps); None with i = s = -1 clears."""

@@ -119,6 +119,7 @@ struct rapid_ctx {
   int theta_on;       // Eq. predict with the linear classifier over the features
   double theta[5];
   float scorer_thr;
+  int scorer_off[RAPID_MAX_STAGES];  // 1: the scorer leaves this stage unpruned (rapid_set_scorer_stages)
   void *d_scorer, *d_scorer_tmp;
   ScorerDev sdev;
   unsigned char *d_mask;
@@ -634,7 +635,7 @@ static StageArgs stage_args(rapid_ctx *ctx, int s) {
   a.max_sweeps = ctx->p.max_sweeps;
   a.verify_filter = ctx->p.verify_filter;
   a.skip_tiles = ctx->p.skip_tiles;
-  a.prune = ctx->scorer_on || (ctx->keep_on && ctx->keep_stage[s]);
+  a.prune = (ctx->scorer_on && !ctx->scorer_off[s]) || (ctx->keep_on && ctx->keep_stage[s]);
   a.frontier = ctx->p.schedule == 1;
   a.qbits = ctx->d_qbits;
   a.wl = ctx->d_wl;
@@ -728,7 +729,7 @@ extern "C" rapid_status rapid_refine_stage(rapid_ctx *ctx, int32_t *sweeps_out, 
     CK(cudaEventRecordWithFlags(ctx->ev[i][0], ctx->stream, evflags));
   }
   const ImageDesc *ds = host_desc(ctx, i);
-  if (ctx->scorer_on)  // the learned scorer's masks for this stage (pruned sweeps)
+  if (ctx->scorer_on && a.prune)  // the learned scorer's masks for this stage (pruned sweeps)
     for (int m = 0; m < ctx->nimg; m++) {
       CK(launch_score(a, ds[m], ctx->L, ctx->sdev, ctx->scorer_thr, nullptr, ctx->d_mask + ctx->im[m].lab_off,
                       ctx->stream));
@@ -997,6 +998,16 @@ extern "C" rapid_status rapid_set_scorer(rapid_ctx *ctx, const float *weights, f
     if (!grow(&ctx->d_mask, &ctx->mask_cap, ctx->lab_total)) return RAPID_ENOMEM;
     return build_descriptors(ctx);
   }
+  return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_set_scorer_stages(rapid_ctx *ctx, const int32_t *on, int32_t n) {
+  if (!ctx || n < 0 || n > RAPID_MAX_STAGES || (n > 0 && !on)) return RAPID_EINVAL;
+  if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  for (int i = 0; i < n; i++)
+    if (on[i] & ~1) return RAPID_EINVAL;
+  drop_graph(ctx);
+  for (int i = 0; i < RAPID_MAX_STAGES; i++) ctx->scorer_off[i] = i < n ? !on[i] : 0;
   return RAPID_OK;
 }
 

@@ -47,6 +47,7 @@ def _null_calls(pkg):
         "rapid_autotune": (None, None, None),
         "rapid_set_scorer": (None, None, C.c_float(0.5)),
         "rapid_set_keep_mask": (None, 0, 0, buf, 16, 0),
+        "rapid_set_scorer_stages": (None, None, 0),
         "rapid_set_classifier": (None, None),
         "rapid_read_features": (None, 0, buf),
         "rapid_scorer_features": (None, 0, buf),
