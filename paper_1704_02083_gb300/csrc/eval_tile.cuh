@@ -1,15 +1,12 @@
-// eval_tile.cuh — block decisions of one phase, one warp per tile (included by
-// stage_impl.cuh, once per evaluation-tile shape).
+// eval_tile.cuh — the block tests and decisions shared by both schedules, and the queue
+// schedule's phases (included by stage_impl.cuh, once per evaluation-tile shape).
 //
-// A warp takes a kTileW x kTileH-block tile, stages its labels with a 1-block halo in its
-// own shared window ((kTileW + 2) x (kTileH + 2) int32) and gives each lane the tile's
-// blocks of the phase class (at most kPhaseMax; 11 x 6 for 32 x 16 tiles).  Warps never wait for each other inside a phase, so the SM hides the
-// global-memory latency of one warp's tile behind the work of the others.
-//
-// A tile is skipped when its record says that no label present in its window (halo
-// included) has changed since its last scan in this phase class and that scan issued no
-// merge request: every block would decide exactly as before, i.e. not move, so the
-// recorded eligible / evaluated counts are replayed.
+// Dense queue phases: a warp takes a kTileW x kTileH-block tile, pops the tile's queued
+// blocks of the phase class, stages the tile's labels with a 1-block halo in its own shared
+// window ((kTileW + 2) x (kTileH + 2) int32) and gives each lane the popped blocks.  Warps
+// never wait for each other inside a phase, so the SM hides the global-memory latency of
+// one warp's tile behind the work of the others.  Sparse queue phases take their blocks
+// from the class's worklist instead, one thread per block (eval_queue).
 #pragma once
 
 // (included inside namespace rapid)
@@ -17,48 +14,9 @@ static constexpr int kWinW = kTileW + 2, kWinH = kTileH + 2;
 
 struct WarpTile {
   int win[kWinW * kWinH];
-  int hkey[32];             // labels of the window: open-addressing table (-1 = empty)
-  int hval[32];             // 1 when hkey[i] changed since the tile's previous scan
-  unsigned prevreq[kReqWords];  // blocks that requested a merge at the previous scan
-  unsigned req[kReqWords];      // blocks that request one now
   int items[kPhaseMax];         // phase-class blocks (index j) that need a decision
-  unsigned queue[kReqWords];    // frontier schedule: the blocks popped from the queue now
-  int hcount, over;         // labels in the table; more than kTileLabels (or table full)
+  unsigned queue[kReqWords];    // the blocks popped from the queue now
 };
-
-__device__ __forceinline__ int tab_slot(int v) { return (int)(((unsigned)v * 0x9E3779B1u) >> 27); }
-
-// Insert label v into the warp's table (lanes may insert concurrently).
-__device__ __forceinline__ void tab_insert(WarpTile &W, int v) {
-  int h = tab_slot(v);
-  for (int p = 0; p < 32; p++) {
-    int cur = ((volatile int *)W.hkey)[h];
-    if (cur == v) return;
-    if (cur == -1) {
-      cur = atomicCAS(&W.hkey[h], -1, v);
-      if (cur == -1) {
-        if (atomicAdd(&W.hcount, 1) >= kTileLabels) *(volatile int *)&W.over = 1;
-        return;
-      }
-      if (cur == v) return;
-    }
-    h = (h + 1) & 31;
-  }
-  W.over = 1;
-}
-
-// 1 when label k may have changed since the previous scan (labels not in the table count
-// as changed).
-__device__ __forceinline__ bool win_label_changed(const WarpTile &W, int k) {
-  int h = tab_slot(k);
-  for (int p = 0; p < 32; p++) {
-    const int cur = W.hkey[h];
-    if (cur == k) return W.hval[h] != 0;
-    if (cur == -1) return true;
-    h = (h + 1) & 31;
-  }
-  return true;
-}
 
 // Decide a block: the target label, or -1 for no decrease (Eq. operation; ties to the
 // smaller label, a move only on a strict decrease).  The candidates are visited once,
@@ -190,22 +148,6 @@ __device__ __forceinline__ bool block_tests(const StageArgs &a, int lbl, int nN,
   return true;
 }
 
-__device__ __forceinline__ bool block_needs_decision(const StageArgs &a, const WarpTile &W, int c, int j,
-                                                     bool block_skip, const unsigned char *mask, long long blk,
-                                                     Local &lc) {
-  const int *win = W.win;
-  const int lbl = win[c];
-  const int nN = win[c - kWinW], nW = win[c - 1], nE = win[c + 1], nS = win[c + kWinW];
-  if (!block_tests(a, lbl, nN, nW, nE, nS, win[c - kWinW - 1], win[c - kWinW + 1], win[c + kWinW + 1],
-                   win[c + kWinW - 1], mask, blk, lc))
-    return false;
-  if (block_skip && !((W.prevreq[j >> 5] >> (j & 31)) & 1u) && !win_label_changed(W, lbl) &&
-      (nN < 0 || !win_label_changed(W, nN)) && (nW < 0 || !win_label_changed(W, nW)) &&
-      (nE < 0 || !win_label_changed(W, nE)) && (nS < 0 || !win_label_changed(W, nS)))
-    return false;
-  return true;
-}
-
 // Frontier schedule: queue block (gx, gy) of image im (no-op outside the block grid).  Its
 // tile, phase class and index j in the class lattice of the tile are those eval_phase
 // enumerates: the class lattice of a tile starts at (lx % 3, ly % 3).
@@ -310,15 +252,6 @@ __device__ __forceinline__ bool decide_block_at(const StageArgs &a, const ImageD
   return false;
 }
 
-// Pass 2 of the tile path: the block at window index c (phase-class index j).
-template <int kSched>
-__device__ __forceinline__ void decide_block(const StageArgs &a, const ImageDesc &im, WarpTile &W, int c, int j, int bx,
-                                             int by, int g, Local &lc) {
-  const int *win = W.win;
-  if (decide_block_at<kSched>(a, im, win[c], win[c - kWinW], win[c - 1], win[c + 1], win[c + kWinW], bx, by, g, lc))
-    atomicOr(&W.req[j >> 5], 1u << (j & 31));
-}
-
 __device__ inline int warp_sum(int v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -365,13 +298,16 @@ __device__ __forceinline__ void flush_counts(const StageArgs &a, int ii, int slo
   scanned = skipped = 0;
 }
 
-// g: 1-based phase number within the launch; slot: the sweep's change-count slot.  imgs,
+// Frontier schedule, a phase whose class has many queued blocks (and the first sweep of a
+// stage, when every block is queued): one warp per tile of kTileW x kTileH blocks pops the
+// tile's queued blocks of the class (skipping the tile when none is queued), stages the
+// tile's labels with a 1-block halo in shared memory and decides the popped blocks.
+// g: 1-based phase number within the launch; slot: the sweep's change-count slot; imgs,
 // tile0 and active are the CTA's shared copies of the images, their first tiles and
-// whether each still refines in this stage.  kSched: the schedule (kSchedSweeps, ...).
+// whether each still refines in this stage.
 template <bool kBatch, int kSched>
 __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *imgs, const int *tile0,
-                                           const unsigned char *active, const unsigned char *pruned,
-                                           const int *valid_from, WarpTile *wts, int *s_draw, int phase, int g,
+                                           const unsigned char *active, WarpTile *wts, int *s_draw, int phase, int g,
                                            int slot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpTile &W = wts[warp];
@@ -406,70 +342,24 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
     const int lt = t - im.tile0;
     const int tx = lt % im.ntx, ty = lt / im.ntx;
     const int bx0 = tx * kTileW, by0 = ty * kTileH;
-    int *rec = a.trec + ((long long)t * 9 + phase) * kRecInts;
-    const bool fq = queue_schedule<kSched>(a);
-    unsigned qv = 0u;
-    if (fq) {  // frontier schedule: pop the tile's queued blocks of this class (if any)
-      unsigned *qw = a.qbits + ((long long)t * 9 + phase) * kQueueWords;
-      qv = lane < kReqWords ? qw[lane] : 0u;
-      if (!__any_sync(0xffffffffu, qv != 0u)) {
-        if (lane == 0) skipped++;
-        continue;
-      }
-      if (lane < kReqWords) qw[lane] = 0u;
-    }
-    // the tile's record (not used by the frontier schedule)
-    const int rv = (!fq && lane < kRecInts) ? rec[lane] : 0;
-    // a record from before the image's switch from pruned to full sweeps counts as none
-    const int stamp_rec = __shfl_sync(0xffffffffu, rv, 0), nlab = __shfl_sync(0xffffffffu, rv, 1);
-    const int stamp = stamp_rec >= valid_from[cur] ? stamp_rec : 0;
-    const unsigned char *mask = pruned[cur] ? im.mask : nullptr;
-    // lanes 4 + kTileLabels .. hold the merge-request words of the previous scan
-    const bool req_lane = lane >= 4 + kTileLabels && lane < kRecInts;
-    const bool anyreq = __any_sync(0xffffffffu, req_lane && rv != 0);
-    const bool can = a.skip_tiles && stamp > 0 && nlab >= 0 && !anyreq;
-    const int myl = __shfl_sync(0xffffffffu, rv, (4 + lane) & 31);
-    const bool changed = __any_sync(0xffffffffu, can && lane < nlab && a.st.chg[myl] >= 2 * stamp);
-    if (can && !changed) {
-      const int re = __shfl_sync(0xffffffffu, rv, 2), rvv = __shfl_sync(0xffffffffu, rv, 3);
-      if (lane == 0) {
-        lc.elig += re;
-        lc.eval += rvv;
-        skipped++;
-      }
+    // pop the tile's queued blocks of this class (if any)
+    unsigned *qw = a.qbits + ((long long)t * 9 + phase) * kQueueWords;
+    const unsigned qv = lane < kReqWords ? qw[lane] : 0u;
+    if (!__any_sync(0xffffffffu, qv != 0u)) {
+      if (lane == 0) skipped++;
       continue;
     }
+    if (lane < kReqWords) qw[lane] = 0u;
     if (lane == 0) scanned++;
-    W.hkey[lane] = -1;
-    if (lane == 0) {
-      W.over = 0;
-      W.hcount = 0;
-    }
-    if (req_lane) {
-      W.req[lane - 4 - kTileLabels] = 0u;
-      W.prevreq[lane - 4 - kTileLabels] = stamp > 0 ? (unsigned)rv : 0u;
-    }
     if (lane < kReqWords) W.queue[lane] = qv;
-    __syncwarp();
-    // window: lane = column (lanes 0 and 1 also take columns 32 and 33); the label of each
-    // run of equal labels down a column goes into the table
+    // window: lane = column (lanes 0 and 1 also take columns 32 and 33)
     for (int col = lane; col < kWinW; col += 32) {
       const int gx = bx0 - 1 + col;
       const bool inx = gx >= 0 && gx < im.nbx;
-      int vals[kWinH];
 #pragma unroll
       for (int wy = 0; wy < kWinH; wy++) {
         const int gy = by0 - 1 + wy;
-        vals[wy] = (inx && gy >= 0 && gy < im.nby) ? im.lab[(long long)gy * im.nbx + gx] : -1;
-      }
-      int prev = -2;
-#pragma unroll
-      for (int wy = 0; wy < kWinH; wy++) {
-        const int v = vals[wy];
-        W.win[wy * kWinW + col] = v;
-        // once the window has more labels than a record holds the table is not used
-        if (!fq && v != prev && v >= 0 && !*(volatile int *)&W.over) tab_insert(W, v);
-        prev = v;
+        W.win[wy * kWinW + col] = (inx && gy >= 0 && gy < im.nby) ? im.lab[(long long)gy * im.nbx + gx] : -1;
       }
     }
     // the tile's blocks of this phase class
@@ -477,21 +367,17 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
     const int tw = min(kTileW, im.nbx - bx0), th = min(kTileH, im.nby - by0);
     const int nx = tw > lx0 ? (tw - lx0 + 2) / 3 : 0, ny = th > ly0 ? (th - ly0 + 2) / 3 : 0;
     __syncwarp();
-    // which of the window's labels changed since the previous scan of this tile and class
-    const int key = W.hkey[lane];
-    W.hval[lane] = (key >= 0 && stamp > 0) ? (a.st.chg[key] >= 2 * stamp) : 1;
-    __syncwarp();
-    const bool block_skip = a.skip_tiles && stamp > 0 && !W.over;
-    const int e0 = lc.elig, v0 = lc.eval;
-    // pass 1: tests; the blocks that need a decision are compacted into W.items
+    // pass 1: the tests of the popped blocks; those that need a decision are compacted
     int nitems = 0;
     for (int j0 = 0; j0 < nx * ny; j0 += 32) {
       const int j = j0 + lane;
       bool need = false;
-      if (j < nx * ny && (!fq || ((W.queue[j >> 5] >> (j & 31)) & 1u))) {
+      if (j < nx * ny && ((W.queue[j >> 5] >> (j & 31)) & 1u)) {
         const int lx = lx0 + 3 * (j % nx), ly = ly0 + 3 * (j / nx);
-        need = block_needs_decision(a, W, (ly + 1) * kWinW + (lx + 1), j, block_skip, mask,
-                                    (long long)(by0 + ly) * im.nbx + (bx0 + lx), lc);
+        const int c = (ly + 1) * kWinW + (lx + 1);
+        const int *win = W.win;
+        need = block_tests(a, win[c], win[c - kWinW], win[c - 1], win[c + 1], win[c + kWinW], win[c - kWinW - 1],
+                           win[c - kWinW + 1], win[c + kWinW + 1], win[c + kWinW - 1], nullptr, 0, lc);
       }
       const unsigned ball = __ballot_sync(0xffffffffu, need);
       if (need) W.items[nitems + __popc(ball & ((1u << lane) - 1u))] = j;
@@ -502,22 +388,10 @@ __device__ __forceinline__ void eval_phase(const StageArgs &a, const ImageDesc *
     for (int it = lane; it < nitems; it += 32) {
       const int j = W.items[it];
       const int lx = lx0 + 3 * (j % nx), ly = ly0 + 3 * (j / nx);
-      decide_block<kSched>(a, im, W, (ly + 1) * kWinW + (lx + 1), j, bx0 + lx, by0 + ly, g, lc);
-    }
-    const int de = warp_sum(lc.elig - e0), dv = warp_sum(lc.eval - v0);
-    __syncwarp();
-    // record: the table's labels (when at most kTileLabels), counts, request mask
-    if (!fq) {
-      const unsigned present = __ballot_sync(0xffffffffu, key >= 0);
-      const int pos = __popc(present & ((1u << lane) - 1u));
-      if (key >= 0 && pos < kTileLabels) rec[4 + pos] = key;
-      if (lane == 0) {
-        rec[0] = g;
-        rec[2] = (int)de;
-        rec[3] = (int)dv;
-        rec[1] = W.over ? -1 : __popc(present);
-      }
-      if (req_lane) rec[lane] = (int)W.req[lane - 4 - kTileLabels];
+      const int c = (ly + 1) * kWinW + (lx + 1);
+      const int *win = W.win;
+      decide_block_at<kSched>(a, im, win[c], win[c - kWinW], win[c - 1], win[c + 1], win[c + kWinW], bx0 + lx,
+                              by0 + ly, g, lc);
     }
     __syncwarp();
   }

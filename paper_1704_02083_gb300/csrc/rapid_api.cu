@@ -73,9 +73,7 @@ struct rapid_ctx {
   size_t lab_cap[2];
   int *d_full;  // full-res staging for host reads
   size_t full_cap;
-  int *d_trec;  // tile scan records, sized for the finest stage
-  size_t trec_cap;
-  unsigned *d_qbits;  // frontier queue (schedule 1), sized like the tile records
+  unsigned *d_qbits;  // frontier queue (schedule 1): per (tile, class), sized for the finest stage
   size_t qbits_cap;
   int *d_wl;          // frontier worklists (9 * wl_cap) and their 9 counts
   size_t wl_bytes_cap;
@@ -292,9 +290,6 @@ static void free_image_buffers(rapid_ctx *ctx) {
   cudaFree(ctx->d_full);
   ctx->d_full = nullptr;
   ctx->full_cap = 0;
-  cudaFree(ctx->d_trec);
-  ctx->d_trec = nullptr;
-  ctx->trec_cap = 0;
   cudaFree(ctx->d_qbits);
   ctx->d_qbits = nullptr;
   ctx->qbits_cap = 0;
@@ -533,7 +528,7 @@ extern "C" rapid_status rapid_set_images(rapid_ctx *ctx, int32_t n, const uint8_
     const int lnbx = ceil_div(h.W, sl), lnby = ceil_div(h.H, sl);
     h.lab_off = lab_n;
     lab_n = round_up(lab_n + (size_t)lnbx * lnby, 64);
-    long long most = 0;  // tile records: the shape with the most tiles at the finest stage
+    long long most = 0;  // queue words: the shape with the most tiles at the finest stage
     for (int sh = 0; sh < kNumShapes; sh++)
       most = std::max<long long>(most, (long long)((lnbx + kShapes[sh].w - 1) / kShapes[sh].w) *
                                            ((lnby + kShapes[sh].h - 1) / kShapes[sh].h));
@@ -566,7 +561,6 @@ extern "C" rapid_status rapid_set_images(rapid_ctx *ctx, int32_t n, const uint8_
     if (!grow(&ctx->d_pyr[l], &ctx->pyr_cap[l], pyr_n[l] * sizeof(int4))) return RAPID_ENOMEM;
   for (int b = 0; b < 2; b++)
     if (!grow(&ctx->d_lab[b], &ctx->lab_cap[b], lab_n * sizeof(int))) return RAPID_ENOMEM;
-  if (!grow(&ctx->d_trec, &ctx->trec_cap, (size_t)tiles_last * 9 * kRecInts * sizeof(int))) return RAPID_ENOMEM;
   if (ctx->p.schedule == 1) {
     if (!grow(&ctx->d_qbits, &ctx->qbits_cap, (size_t)tiles_last * 9 * kQueueWords * sizeof(unsigned)))
       return RAPID_ENOMEM;
@@ -616,7 +610,6 @@ static StageArgs stage_args(rapid_ctx *ctx, int s) {
   a.img0 = ctx->h_desc[(size_t)s * ctx->nimg];
   a.nimg = ctx->nimg;
   a.ntiles = ctx->ntiles[s];
-  a.trec = ctx->d_trec;
   a.st = ctx->st;
   a.st.M = ctx->M_total;
   a.mg = ctx->mg;

@@ -10,7 +10,9 @@
 //           the phase-start snapshot of the count, snapshot means (5 doubles) and their
 //           single-precision hi/lo splits, last-change stamps, class y (int8),
 //           boundary-superpixel flag (uint8), conservative bounding box (int4)
-//   tiles   per (tile, phase class) scan record: stamp, label set, counts
+//   bitmaps sweep schedule: per phase class, one bit per block that may be eligible, and
+//           one per block that requested a merge at its last evaluation
+//   queue   queue schedule: per (tile, phase class) queue bits, and per-class worklists
 // Position sums of a block are not stored: a block is an axis-aligned rectangle of
 // full-res pixels, so its count and x/y sums follow from its corners.
 //
@@ -34,22 +36,17 @@ enum { PROF_EVAL = 0, PROF_SYNC1, PROF_COMMIT, PROF_SYNC2, PROF_MERGE, PROF_N };
 // Device error word values (0 = fine).
 enum { DERR_TIMEOUT = 1 };
 
-// Evaluation tiles: one warp takes a tile of w x h blocks.  The stage kernel is compiled
-// for each shape below, with `threads` per CTA: 1024 threads hold 64 registers each (some
-// spill), 512 hold 128 (none spill, half the warps per SM).  A launch uses one shape; the
-// result never depends on it.
+// Evaluation tiles of the queue schedule's dense phases: one warp takes a tile of w x h
+// blocks.  The stage kernel is compiled for each shape below, with `threads` per CTA: 1024
+// threads hold 64 registers each (some spill), 512 hold 128 (none spill, half the warps
+// per SM).  A launch uses one shape; the result never depends on it.  (The sweep schedule
+// uses only the thread count.)
 struct TileShape {
   int w, h, threads;
 };
 constexpr int kNumShapes = 6;
 constexpr TileShape kShapes[kNumShapes] = {{32, 16, 1024}, {32, 8, 1024}, {64, 16, 1024},
                                            {32, 16, 512},  {32, 8, 512},  {64, 16, 512}};
-constexpr int kTileLabels = 16;
-// tile record: stamp of the last scan, label count (-1: too many), eligible and evaluated
-// counts, the labels, and a bit per phase-class block that issued a merge request (up to
-// 22 x 6 blocks for the widest shape: 5 words)
-constexpr int kRecInts = 4 + kTileLabels + 5;
-static_assert(kRecInts <= 32, "a warp reads a tile record with one lane per int");
 constexpr int kCacheLabels = 16;           // neighbour labels remembered by a failed merge
 
 struct DevStats {
@@ -166,7 +163,6 @@ struct StageArgs {
   ImageDesc img0;         // imgs[0] (a launch over one image reads it from here)
   int nimg;
   int ntiles;         // tiles of all images
-  int *trec;          // tile records [ntiles * 9 * kRecInts]
   DevStats st;
   DevMerge mg;
   DevCtl ctl;
@@ -174,7 +170,7 @@ struct StageArgs {
   double lam_b2;
   float lam_b2_f;
   int verify_filter;  // 1: also decide every block in binary64 and count disagreements
-  int skip_tiles;     // 1: skip tiles whose inputs did not change since their last scan
+  int skip_tiles;     // 1: skip decisions whose inputs did not change since their last evaluation
   int size_mode, lo_num, lo_den, hi_num, hi_den;
   int max_sweeps;
   int prune;          // 1: sweep with the scorer's masks until a sweep changes nothing, then in full

@@ -191,7 +191,6 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   const TileShape ts = kShapes[0];  // one tile shape for every stage here
   const int ntx_max = (cdiv(W, side[nst - 1]) + ts.w - 1) / ts.w;
   const int nty_max = (cdiv(H, side[nst - 1]) + ts.h - 1) / ts.h;
-  int *trec = (int *)cv.take((size_t)ntx_max * nty_max * 9 * kRecInts * sizeof(int));
   unsigned *qbits = p->schedule == 1
                         ? (unsigned *)cv.take((size_t)ntx_max * nty_max * 9 * kQueueWords * sizeof(unsigned))
                         : nullptr;
@@ -213,7 +212,7 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   std::memset(&mg, 0, sizeof mg);
   const size_t lbytes = label_arrays_bytes(M);
   void *lblock = cv.take(lbytes);
-  bool ok = ctl && lab[0] && lab[1] && trec && cbits && rbits && d_desc && lblock && ((qbits && wl) || p->schedule != 1);
+  bool ok = ctl && lab[0] && lab[1] && cbits && rbits && d_desc && lblock && ((qbits && wl) || p->schedule != 1);
   for (int l = 0; l < nsf; l++) ok = ok && pyr[l];
   if (!ok) return RAPID_ERANGE;  // this image and parameter set need more than the fixed array
   carve_label_arrays(lblock, lbytes, M, &st, &mg);
@@ -308,7 +307,6 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   a.hi_num = p->hi_num;
   a.hi_den = p->hi_den;
   a.max_sweeps = p->max_sweeps;
-  a.trec = trec;
   a.frontier = p->schedule == 1;
   a.qbits = qbits;
   a.wl = wl;

@@ -15,13 +15,11 @@
 // atomically.  Merge requests of the phase (size bound hit, Sec. 3.1) are then resolved
 // against the post-move S while the snapshot is refreshed.
 //
-// Work layout: one persistent CTA of 1024 (or 512) threads per SM.  In the evaluation each warp takes
-// tiles of kTileW x kTileH blocks (32 x 16, 32 x 8 or 64 x 16 by unit; CTA b takes tiles
-// b, b + grid, ...; its warps draw them from a shared counter), stages the tile's labels with a 1-block halo in shared memory and
-// decides the tile's blocks of the phase class (eval_tile.cuh).  A tile is skipped when no
-// label present in it has changed since its last scan in this phase class and that scan
-// issued no merge request: its blocks would decide exactly as before (no move), so the
-// recorded counts are replayed instead.
+// Work layout: one persistent CTA of 1024 (or 512) threads per SM.  Under the sweep
+// schedule a phase walks a bitmap of the class's blocks that may be eligible, split
+// evenly over the warps of the grid (eval_sweep.cuh); under the queue schedule a phase pops
+// the queued blocks of its class, by tiles of kTileW x kTileH blocks (32 x 16, 32 x 8 or
+// 64 x 16 by unit) or from a worklist (eval_tile.cuh).
 //
 // Decisions: the energy difference of each candidate label k against the block's label a
 // is first computed in single precision in the well-conditioned form
@@ -52,7 +50,6 @@ constexpr int kTileW = RAPID_TILE_W, kTileH = RAPID_TILE_H;
 // blocks of one phase class in a tile, and 32-bit words of one bit each
 constexpr int kPhaseMax = ((kTileW + 2) / 3) * ((kTileH + 2) / 3);
 constexpr int kReqWords = (kPhaseMax + 31) / 32;
-static_assert(4 + kTileLabels + kReqWords <= kRecInts, "the tile record holds the request words");
 static_assert(kReqWords <= kQueueWords, "the frontier queue holds a tile's class lattice");
 
 #ifndef RAPID_THREADS
@@ -569,7 +566,6 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
     a.st.adj[k] = 0;
   }
   const long long nrec = (long long)a.ntiles * 9;
-  for (long long i = gtid; i < nrec; i += gstride) a.trec[i * kRecInts] = 0;
   if (sweep_schedule<kSched>(a)) {  // sweep schedule: every block may be eligible when the stage starts
     for (int i = gtid; i < a.cwb[9]; i += gstride) {
       a.cbits[i] = ~0u;
@@ -598,7 +594,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
         if (nq <= 4 * (int)(gridDim.x * blockDim.x))
           eval_queue<kBatch, kSched>(a, s_img, s_active, s_cnt, ph, g, slot, nq);
         else
-          eval_phase<kBatch, kSched>(a, s_img, s_tile0, s_active, s_pruned, s_valid_from, wts, &s_draw, ph, g, slot);
+          eval_phase<kBatch, kSched>(a, s_img, s_tile0, s_active, wts, &s_draw, ph, g, slot);
       }
 
       tm.lap(PROF_EVAL);
