@@ -339,6 +339,27 @@ rapid_status rapid_trainer_samples(rapid_trainer *t, int64_t first, int32_t coun
 rapid_status rapid_trainer_gradient(rapid_trainer *t, const float *weights, int64_t first, int32_t count,
                                     float pos_weight, float *grad_out, float *loss_out);
 
+/* Input generator (not part of the method: it makes the synthetic stand-in for the
+ * paper's whole-slide images at full size on the device).  Writes the counter-based
+ * synthetic H&E-like slide of H x W pixels into rgb_dev (device, interleaved RGB uint8,
+ * rows rgb_pitch_bytes apart) and, when regions_dev is not NULL, its ground-truth region
+ * ids (device int32, rows regions_pitch_bytes apart): Voronoi tissue cells (one per
+ * px_per_cell pixels, white_frac of them white background), nuclei (nucleus_density per
+ * pixel), fold bands covering about fold_frac of the area, Gaussian noise of sigma 6.
+ * The definition is in k_synth.cu; paper_1704_02083_gb300.synth.slide_gen gives the same
+ * bytes on the host for any window.  Stream-ordered on cuda_stream.  EINVAL on bad
+ * arguments, ERANGE beyond 8 seeds or 64 nuclei per 128 x 128 bucket, 1024 bands or 2^31
+ * ids. */
+typedef struct {
+  int64_t H, W;
+  uint64_t seed;
+  int32_t px_per_cell;
+  int32_t pad;
+  double white_frac, fold_frac, nucleus_density;
+} rapid_synth_params;
+rapid_status rapid_synth_slide(const rapid_synth_params *p, uint8_t *rgb_dev, int64_t rgb_pitch_bytes,
+                               int32_t *regions_dev, int64_t regions_pitch_bytes, void *cuda_stream);
+
 /* Whole slide.  The slide (device, H x W interleaved RGB, rows rgb_pitch_bytes apart; any
  * size) is cut into tiles by even row and column bands of at most max_tile pixels
  * (startRow = H i / n, Eq. parallel_spit, on both axes); the tiles, as views into the

@@ -55,6 +55,12 @@ class rapid_stage_counters(C.Structure):
                 ("section_ms", C.c_float * 5), ("pad2", C.c_float)]
 
 
+class rapid_synth_params(C.Structure):
+    _fields_ = [("H", C.c_int64), ("W", C.c_int64), ("seed", C.c_uint64), ("px_per_cell", C.c_int32),
+                ("pad", C.c_int32), ("white_frac", C.c_double), ("fold_frac", C.c_double),
+                ("nucleus_density", C.c_double)]
+
+
 class rapid_counters(C.Structure):
     _fields_ = [("num_stages", C.c_int32), ("M", C.c_int32), ("launches", C.c_int64),
                 ("stage", rapid_stage_counters * RAPID_MAX_STAGES)]
@@ -107,6 +113,7 @@ def lib() -> C.CDLL:
         "rapid_set_scorer": (i32, [P, P, C.c_float]),
         "rapid_set_keep_mask": (i32, [P, i32, i32, P, i64, i32]),
         "rapid_set_scorer_stages": (i32, [P, P, i32]),
+        "rapid_synth_slide": (i32, [C.POINTER(rapid_synth_params), P, i64, P, i64, P]),
         "rapid_set_classifier": (i32, [P, P]),
         "rapid_read_features": (i32, [P, i32, P]),
         "rapid_refine_slide": (i32, [P, P, i64, i64, i64, i32, i32, i32, P, i64, P, i64, pi64, pi32]),
@@ -304,6 +311,29 @@ def rapid_set_scorer(ctx: int, weights, threshold: float):
         return
     w = _f32(weights)
     _check(lib().rapid_set_scorer(ctx, w.ctypes.data, float(threshold)), "rapid_set_scorer")
+
+
+def rapid_synth_slide(params: rapid_synth_params, rgb_dev_ptr: int, rgb_pitch_bytes: int, regions_dev_ptr,
+                      regions_pitch_bytes: int, cuda_stream: int = 0):
+    """The counter-based synthetic slide into device buffers (see include/rapid.h)."""
+    _check(lib().rapid_synth_slide(C.byref(params), rgb_dev_ptr, rgb_pitch_bytes, regions_dev_ptr,
+                                   regions_pitch_bytes, cuda_stream), "rapid_synth_slide")
+
+
+def synth_slide_device(H: int, W: int, seed: int, regions: bool = False, px_per_cell: int = 8192,
+                       white_frac: float = 0.40, fold_frac: float = 0.05, nucleus_density: float = 1.0 / 400.0,
+                       stream=None):
+    """The counter-based synthetic slide made on the device (rapid_synth_slide): an H x W x 3
+    uint8 CUDA tensor, and its ground-truth region ids (int32) when `regions`."""
+    import torch
+
+    rgb = torch.empty((H, W, 3), dtype=torch.uint8, device="cuda")
+    reg = torch.empty((H, W), dtype=torch.int32, device="cuda") if regions else None
+    p = rapid_synth_params(H=H, W=W, seed=seed, px_per_cell=px_per_cell, pad=0, white_frac=white_frac,
+                           fold_frac=fold_frac, nucleus_density=nucleus_density)
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    rapid_synth_slide(p, rgb.data_ptr(), 3 * W, reg.data_ptr() if reg is not None else None, 4 * W, s)
+    return (rgb, reg) if regions else rgb
 
 
 def rapid_set_scorer_stages(ctx: int, on):

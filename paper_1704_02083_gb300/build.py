@@ -18,7 +18,7 @@ LIB = os.path.join(OUT_DIR, "librapid.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 UNITS = ["k_stage_s0.cu", "k_stage_s1.cu", "k_stage_s2.cu", "k_stage_s3.cu", "k_stage_s4.cu", "k_stage_s5.cu",
          "k_stage.cu", "k_prep.cu", "k_scorer.cu",
-         "rapid_api.cu", "rapid_static.cu"]
+         "rapid_api.cu", "rapid_static.cu", "k_synth.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-fmad=false", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
                      "-I" + INCLUDE]

@@ -289,3 +289,227 @@ def batch_workload(name: str, count: int | None = None):
 def workload_image(name: str) -> SynthImage:
     w = WORKLOADS[name]
     return he_image(w["H"], w["W"], w["n_cells"], w["seed"])
+
+
+# ---------------------------------------------------------------- counter-based slide generator
+# The whole-slide stand-in at full size (100000 x 80000, 24 GB of RGB) is generated on the
+# device (rapid_synth_slide) from the definition below, which this host function restates
+# pixel for pixel, so that both give the same bytes: every random quantity is a hash of
+# (seed, stream, index), never a stream position, and every geometric test is exact
+# integer arithmetic.  Any window of the slide can therefore be generated alone.
+#
+# hash: h(seed, s, i) = mix(mix(mix(seed) ^ s) ^ i) on unsigned 64-bit words, where mix is
+# the SplitMix64 output function (z += 0x9E3779B97F4A7C15; z = (z ^ z >> 30) *
+# 0xBF58476D1CE4E5B9; z = (z ^ z >> 27) * 0x94D049BB133111EB; z ^ z >> 31).
+#
+# * Buckets: B x B pixels (B = 128), bucket (bx, by) spans [B bx, min(B bx + B, W)) x ...
+#   (edge buckets are clipped); bucket index q = by * nbx + bx.
+# * Voronoi cells: kc = max(1, round(B^2 / px_per_cell)) seeds per bucket; seed id
+#   = q kc + j at (B bx + h(seed, 1, id) % bw_q, B by + h(seed, 2, id) % bh_q) (bw_q, bh_q the
+#   clipped bucket size).  A pixel belongs to the seed of least squared distance (ties: the
+#   smaller id); since every bucket holds a seed, the nearest lies within 2 buckets.
+# * Cell classes: u = h(seed, 3, id) % 10000: white below round(10000 white_frac), purple
+#   below that plus round(10000 (1 - white_frac) 0.4375), else pink; mean = base colour +
+#   h(seed, 4 + c, id) % 31 - 15 per channel c (white: % 11 - 5).
+# * Nuclei: kn = round(B^2 nucleus_density) per bucket, id = q kn + j, centre (B bx +
+#   h(seed, 10, id) % bw_q, B by + h(seed, 11, id) % bh_q), radius 3 + h(seed, 12, id) % 6,
+#   colour NUCLEUS + h(seed, 13 + c, id) % 21 - 10; kept when the centre's cell is not white.
+#   A pixel within the radius (squared distance <= r^2) of kept nuclei takes the largest id.
+# * Folds: nf = max(1, round(fold_frac H W / (50 * 0.65 * min(H, W)))) bands; band b: width
+#   20 + h(seed, 30, b) % 61, direction (ax, ay) = (h(seed, 31, b) % 2049 - 1024, h(seed, 32,
+#   b) % 2049 - 1024) ((1, 0) when both are 0), centre (h(seed, 33, b) % W, h(seed, 34, b) %
+#   H), length min(H, W) (300 + h(seed, 35, b) % 701) // 1000, colour FOLD + h(seed, 36 + c,
+#   b) % 21 - 10.  With d = p - centre and n2 = ax^2 + ay^2, a pixel is in the band when
+#   4 (ax dx + ay dy)^2 <= length^2 n2 and 4 (ay dx - ax dy)^2 <= width^2 n2; the largest b
+#   wins, over nuclei and cells.
+# * Noise: channel c of pixel (x, y) adds -30 + #{t in the discrete Gaussian table, t <= u},
+#   u = h(seed, 20, 3 (y W + x) + c) >> 32; the sum is clamped to [0, 255].
+# * Ground truth: cell id, then n_cells + nucleus id, then n_cells + n_nuclei + band id; ROI =
+#   purple cells and nuclei (folds are not ROI).
+GEN_BUCKET = 128
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def _mix(z):
+    z = (z + np.uint64(0x9E3779B97F4A7C15)) & _M64
+    z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _M64
+    z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _M64
+    return z ^ (z >> np.uint64(31))
+
+
+def gen_hash(seed: int, stream: int, idx):
+    """h(seed, stream, idx) of the counter-based generator (idx: int or integer array)."""
+    with np.errstate(over="ignore"):
+        k = _mix(_mix(np.uint64(seed)) ^ np.uint64(stream))
+        return _mix(k ^ np.asarray(idx, dtype=np.uint64))
+
+
+def gen_layout(H: int, W: int, px_per_cell: int = 8192, nucleus_density: float = 1.0 / 400.0,
+               fold_frac: float = 0.05):
+    """Bucket grid and counts of the counter-based slide generator."""
+    B = GEN_BUCKET
+    nbx, nby = -(-W // B), -(-H // B)
+    kc = max(1, int(round(B * B / px_per_cell)))
+    kn = int(round(B * B * nucleus_density))
+    nf = max(1, int(round(fold_frac * H * W / (50.0 * 0.65 * min(H, W)))))
+    return dict(B=B, nbx=nbx, nby=nby, kc=kc, kn=kn, nf=nf, n_cells=nbx * nby * kc, n_nuclei=nbx * nby * kn)
+
+
+def _bucket_dims(q, nbx, H, W, B):
+    bx, by = q % nbx, q // nbx
+    return bx, by, np.minimum(B, W - B * bx), np.minimum(B, H - B * by)
+
+
+def _cell_pos(seed, ids, kc, nbx, H, W, B):
+    """Seed positions of the cells with the given ids."""
+    q = ids // kc
+    bx, by, bw, bh = _bucket_dims(q, nbx, H, W, B)
+    x = B * bx + (gen_hash(seed, 1, ids) % bw.astype(np.uint64)).astype(np.int64)
+    y = B * by + (gen_hash(seed, 2, ids) % bh.astype(np.uint64)).astype(np.int64)
+    return x, y
+
+
+def _cells(seed, ids, kc, nbx, H, W, B, white_frac):
+    """Position, class and mean colour of the cells with the given ids."""
+    x, y = _cell_pos(seed, ids, kc, nbx, H, W, B)
+    u = (gen_hash(seed, 3, ids) % np.uint64(10000)).astype(np.int64)
+    n_white = int(round(white_frac * 10000))
+    n_purple = int(round((1.0 - white_frac) * 0.4375 * 10000))
+    cls = np.where(u < n_white, 2, np.where(u < n_white + n_purple, 1, 0))
+    base = np.array([PINK, PURPLE, WHITE], np.int64)[cls]
+    jit = np.stack([(gen_hash(seed, 4 + c, ids) % np.uint64(31)).astype(np.int64) - 15 for c in range(3)], -1)
+    jit_w = np.stack([(gen_hash(seed, 4 + c, ids) % np.uint64(11)).astype(np.int64) - 5 for c in range(3)], -1)
+    mean = base + np.where((cls == 2)[..., None], jit_w, jit)
+    return x, y, cls, mean
+
+
+def slide_gen(H: int, W: int, seed: int, x0: int = 0, y0: int = 0, h: int | None = None, w: int | None = None,
+              px_per_cell: int = 8192, white_frac: float = 0.40, fold_frac: float = 0.05,
+              nucleus_density: float = 1.0 / 400.0) -> SynthImage:
+    """The window [x0, x0 + w) x [y0, y0 + h) of the counter-based slide (see above)."""
+    h = H - y0 if h is None else h
+    w = W - x0 if w is None else w
+    if not (0 <= x0 and 0 <= y0 and w > 0 and h > 0 and x0 + w <= W and y0 + h <= H):
+        raise ValueError("window outside the slide")
+    lay = gen_layout(H, W, px_per_cell, nucleus_density, fold_frac)
+    B, nbx, nby, kc, kn, nf = lay["B"], lay["nbx"], lay["nby"], lay["kc"], lay["kn"], lay["nf"]
+    n_cells, n_nuc = lay["n_cells"], lay["n_nuclei"]
+    ys = np.arange(y0, y0 + h, dtype=np.int64)
+    xs = np.arange(x0, x0 + w, dtype=np.int64)
+    # Voronoi: candidate seeds of the buckets within 2 of each pixel's bucket (seed
+    # positions computed once per bucket of the window's neighbourhood)
+    cell = np.empty((h, w), np.int64)
+    gx0, gx1 = max(0, x0 // B - 2), min(nbx - 1, (x0 + w - 1) // B + 2)
+    gy0, gy1 = max(0, y0 // B - 2), min(nby - 1, (y0 + h - 1) // B + 2)
+    gq = (np.arange(gy0, gy1 + 1)[:, None] * nbx + np.arange(gx0, gx1 + 1)[None, :]).astype(np.int64)
+    spos = [_cell_pos(seed, gq * kc + j, kc, nbx, H, W, B) for j in range(kc)]
+    band = max(1, (1 << 20) // w)
+    for r0 in range(0, h, band):
+        yy = ys[r0:r0 + band][:, None]
+        xx = xs[None, :]
+        best_d = np.full((yy.shape[0], w), np.iinfo(np.int64).max, np.int64)
+        best_id = np.full((yy.shape[0], w), -1, np.int64)
+        pbx, pby = xx // B, yy // B
+        for dby in range(-2, 3):
+            for dbx in range(-2, 3):
+                qbx, qby = pbx + dbx, pby + dby
+                ok = (qbx >= 0) & (qbx < nbx) & (qby >= 0) & (qby < nby)
+                lx = np.clip(qbx - gx0, 0, gx1 - gx0)
+                ly = np.clip(qby - gy0, 0, gy1 - gy0)
+                q = np.where(ok, qby * nbx + qbx, 0)
+                for j in range(kc):
+                    ids = q * kc + j
+                    sx, sy = spos[j][0][ly, lx], spos[j][1][ly, lx]
+                    d = (sx - xx) ** 2 + (sy - yy) ** 2
+                    better = ok & ((d < best_d) | ((d == best_d) & (ids < best_id)))
+                    best_d = np.where(better, d, best_d)
+                    best_id = np.where(better, ids, best_id)
+        cell[r0:r0 + band] = best_id
+    _, _, ccls, cmean = _cells(seed, cell, kc, nbx, H, W, B, white_frac)
+    colour = cmean.copy()
+    regions = cell.copy()
+    roi = ccls == 1
+    # nuclei whose disc can reach the window, painted in ascending id order
+    qx0, qx1 = max(0, (x0 - 8) // B), min(nbx - 1, (x0 + w - 1 + 8) // B)
+    qy0, qy1 = max(0, (y0 - 8) // B), min(nby - 1, (y0 + h - 1 + 8) // B)
+    qs = np.array([qy * nbx + qx for qy in range(qy0, qy1 + 1) for qx in range(qx0, qx1 + 1)], np.int64)
+    nid = (qs[:, None] * kn + np.arange(kn, dtype=np.int64)[None, :]).ravel()
+    nid.sort()
+    if nid.size:
+        q = nid // kn
+        bx, by, bw, bh = _bucket_dims(q, nbx, H, W, B)
+        cx = B * bx + (gen_hash(seed, 10, nid) % bw.astype(np.uint64)).astype(np.int64)
+        cy = B * by + (gen_hash(seed, 11, nid) % bh.astype(np.uint64)).astype(np.int64)
+        rad = 3 + (gen_hash(seed, 12, nid) % np.uint64(6)).astype(np.int64)
+        ncol = np.array(NUCLEUS, np.int64)[None, :] + np.stack(
+            [(gen_hash(seed, 13 + c, nid) % np.uint64(21)).astype(np.int64) - 10 for c in range(3)], -1)
+        # the centre's cell (its own Voronoi search, as for any pixel)
+        centre = slide_cells_at(H, W, seed, cx, cy, px_per_cell, white_frac)
+        _, _, ncls, _ = _cells(seed, centre, kc, nbx, H, W, B, white_frac)
+        for t in np.nonzero(ncls != 2)[0]:
+            r = int(rad[t])
+            ya, yb = max(y0, int(cy[t]) - r), min(y0 + h, int(cy[t]) + r + 1)
+            xa, xb = max(x0, int(cx[t]) - r), min(x0 + w, int(cx[t]) + r + 1)
+            if ya >= yb or xa >= xb:
+                continue
+            gy, gx = np.mgrid[ya:yb, xa:xb]
+            inside = (gx - cx[t]) ** 2 + (gy - cy[t]) ** 2 <= r * r
+            sy, sx = gy[inside] - y0, gx[inside] - x0
+            colour[sy, sx] = ncol[t]
+            regions[sy, sx] = n_cells + nid[t]
+            roi[sy, sx] = True
+    # folds, painted in ascending band order
+    for b in range(nf):
+        fw = 20 + int(gen_hash(seed, 30, b) % np.uint64(61))
+        ax = int(gen_hash(seed, 31, b) % np.uint64(2049)) - 1024
+        ay = int(gen_hash(seed, 32, b) % np.uint64(2049)) - 1024
+        if ax == 0 and ay == 0:
+            ax = 1
+        fcx, fcy = int(gen_hash(seed, 33, b) % np.uint64(W)), int(gen_hash(seed, 34, b) % np.uint64(H))
+        flen = min(H, W) * (300 + int(gen_hash(seed, 35, b) % np.uint64(701))) // 1000
+        fcol = np.array(FOLD, np.int64) + np.array(
+            [int(gen_hash(seed, 36 + c, b) % np.uint64(21)) - 10 for c in range(3)], np.int64)
+        ext = (flen + fw) // 2 + 2  # the band lies within this distance of its centre
+        ya, yb = max(y0, fcy - ext), min(y0 + h, fcy + ext + 1)
+        xa, xb = max(x0, fcx - ext), min(x0 + w, fcx + ext + 1)
+        if ya >= yb or xa >= xb:
+            continue
+        n2 = ax * ax + ay * ay
+        for r0 in range(ya, yb, 256):
+            gy, gx = np.mgrid[r0:min(yb, r0 + 256), xa:xb]
+            dx, dy = gx.astype(np.int64) - fcx, gy.astype(np.int64) - fcy
+            along, across = ax * dx + ay * dy, ay * dx - ax * dy
+            inside = (4 * along * along <= flen * flen * n2) & (4 * across * across <= fw * fw * n2)
+            sy, sx = gy[inside] - y0, gx[inside] - x0
+            colour[sy, sx] = fcol
+            regions[sy, sx] = n_cells + n_nuc + b
+            roi[sy, sx] = False
+    # noise
+    pix = (ys[:, None] * W + xs[None, :])[..., None] * 3 + np.arange(3, dtype=np.int64)[None, None, :]
+    u = (gen_hash(seed, 20, pix) >> np.uint64(32)).astype(np.uint32)
+    noise = np.searchsorted(_NOISE_CDF, u, side="right").astype(np.int64) + _NOISE_LO
+    rgb = np.clip(colour + noise, 0, 255).astype(np.uint8)
+    return SynthImage(rgb=np.ascontiguousarray(rgb), regions=regions.astype(np.int64), roi=roi,
+                      n_regions=int(n_cells + n_nuc + nf))
+
+
+def slide_cells_at(H, W, seed, px, py, px_per_cell=8192, white_frac=0.40):
+    """Voronoi cell id of pixels (px, py) (integer arrays) of the counter-based slide."""
+    lay = gen_layout(H, W, px_per_cell)
+    B, nbx, nby, kc = lay["B"], lay["nbx"], lay["nby"], lay["kc"]
+    px, py = np.asarray(px, np.int64), np.asarray(py, np.int64)
+    best_d = np.full(px.shape, np.iinfo(np.int64).max, np.int64)
+    best_id = np.full(px.shape, -1, np.int64)
+    for dby in range(-2, 3):
+        for dbx in range(-2, 3):
+            qbx, qby = px // B + dbx, py // B + dby
+            ok = (qbx >= 0) & (qbx < nbx) & (qby >= 0) & (qby < nby)
+            q = np.where(ok, qby * nbx + qbx, 0)
+            for j in range(kc):
+                ids = q * kc + j
+                sx, sy = _cell_pos(seed, ids, kc, nbx, H, W, B)
+                d = (sx - px) ** 2 + (sy - py) ** 2
+                better = ok & ((d < best_d) | ((d == best_d) & (ids < best_id)))
+                best_d = np.where(better, d, best_d)
+                best_id = np.where(better, ids, best_id)
+    return best_id

@@ -75,7 +75,8 @@ def test_null_handles_are_refused(pkg):
     import test_abi
     takes_handle = {n for n in test_abi.declared_functions()
                     if n not in ("rapid_default_params", "rapid_status_string", "rapid_destroy",
-                                 "rapid_trainer_destroy", "rapid_trainer_create", "rapid_run_static")}
+                                 "rapid_trainer_destroy", "rapid_trainer_create", "rapid_run_static",
+                                 "rapid_synth_slide")}
     assert takes_handle <= set(calls), sorted(takes_handle - set(calls))
 
 
@@ -142,3 +143,21 @@ def test_valid_create_without_a_gpu_reports_ecuda(pkg):
     p = pkg.rapid_default_params()
     assert L.rapid_create(C.byref(p), None, C.byref(h)) == pkg.RAPID_ECUDA
     assert h.value is None
+
+
+def test_slide_generator_checks_its_arguments_before_any_cuda_call(pkg):
+    L = pkg.lib()
+    fake = C.c_void_p(256)
+    good = dict(H=512, W=768, seed=5, px_per_cell=8192, pad=0, white_frac=0.4, fold_frac=0.05,
+                nucleus_density=1 / 400)
+    for bad in (dict(H=0), dict(W=-1), dict(px_per_cell=0), dict(white_frac=1.5), dict(fold_frac=-0.1),
+                dict(nucleus_density=float("nan"))):
+        p = pkg.rapid_synth_params(**dict(good, **bad))
+        assert L.rapid_synth_slide(C.byref(p), fake, 3 * 768, None, 0, None) == pkg.RAPID_EINVAL, bad
+    p = pkg.rapid_synth_params(**good)
+    assert L.rapid_synth_slide(None, fake, 3 * 768, None, 0, None) == pkg.RAPID_EINVAL
+    assert L.rapid_synth_slide(C.byref(p), None, 3 * 768, None, 0, None) == pkg.RAPID_EINVAL
+    assert L.rapid_synth_slide(C.byref(p), fake, 3 * 768 - 1, None, 0, None) == pkg.RAPID_EINVAL
+    assert L.rapid_synth_slide(C.byref(p), fake, 3 * 768, fake, 4 * 768 - 4, None) == pkg.RAPID_EINVAL
+    dense = pkg.rapid_synth_params(**dict(good, px_per_cell=1024))  # 16 seeds per bucket
+    assert L.rapid_synth_slide(C.byref(dense), fake, 3 * 768, None, 0, None) == pkg.RAPID_ERANGE
