@@ -651,6 +651,51 @@ def measure(args, rank, world, local, dist, workload, prune, use_classifier, geo
     return out
 
 
+def slide_batches(H, W, max_tile, px_per_superpixel, max_batch=64, max_px=1 << 30) -> int:
+    """How many batches rapid_refine_slide makes of a slide's tiles (up to max_batch tiles
+    and max_px pixels each, at least one tile)."""
+    from paper_1704_02083_gb300 import synth
+    n, k, px = 0, 0, 0
+    for (_, _, h, w, _) in synth.slide_tiles(H, W, max_tile, px_per_superpixel):
+        if k == 0 or k == max_batch or px + h * w > max_px:
+            n, k, px = n + 1, 0, 0
+        k, px = k + 1, px + h * w
+    return n
+
+
+def slide_parity(workload: str, rgb, labels, stats):
+    """The sampled tiles of a slide against the oracle's records (tests/golden/<workload>.json,
+    written by make_golden.py from the host restatement of the generator and the oracle
+    alone): the tile's pixels, its labels (slide-wide ids minus the tile's first id) and the
+    statistics of its ids.  None when there is no record."""
+    import numpy as np
+
+    import paper_1704_02083_gb300 as pkg
+
+    gpath = os.path.join(ROOT, "tests", "golden", f"{workload}.json")
+    if not os.path.exists(gpath):
+        return None
+    g = json.load(open(gpath))
+    fields = ("n", "sum_r", "sum_g", "sum_b", "sum_x", "sum_y", "init_size")
+    st_all = stats.view(-1, pkg.SP_STATS_DTYPE.itemsize)
+
+    def sha(a):
+        return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+    ok = []
+    for rec in g["sampled"]:
+        r0, c0, h, w, base, M = rec["row0"], rec["col0"], rec["H"], rec["W"], rec["id_base"], rec["M"]
+        img = rgb[r0:r0 + h, c0:c0 + w].cpu().numpy()
+        lab = (labels[r0:r0 + h, c0:c0 + w].cpu().numpy().astype(np.int64) - base).astype("<i4")
+        st = st_all[base:base + M].cpu().numpy().copy().view(pkg.SP_STATS_DTYPE).reshape(-1)
+        st7 = np.stack([st[f] for f in fields], 1).astype("<i8")
+        ok.append(sha(img) == rec["image_sha256"] and sha(lab) == rec["labels_sha256"] and
+                  sha(st7) == rec["stats_sha256"])
+    tiles = ", ".join(str(r["tile"]) for r in g["sampled"])
+    return (f"bit-exact vs the oracle's records of sampled tiles {tiles} (pixels, labels, S)" if all(ok)
+            else f"MISMATCH vs the oracle's records (tiles {tiles}: {ok})")
+
+
 def run_slide(args, rank, world, local):
     """A whole slide through rapid_refine_slide: tiles of at most max_tile px as views into the
     slide in HBM, refined in batches; one step = the whole slide."""
@@ -669,17 +714,33 @@ def run_slide(args, rank, world, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     sd = synth.SLIDES[args.workload]
     H, W, params = sd["H"], sd["W"], dict(sd["params"])
-    img = synth.slide_image(H, W, sd["seed"])
     npx = H * W
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    rgb = torch.from_numpy(img.rgb).cuda()
+    gen_s, img = None, None
+    if sd.get("generator") == "counter":  # made on the device (the counter-based definition)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rgb = pkg.synth_slide_device(H, W, sd["seed"], px_per_cell=sd["px_per_cell"], white_frac=sd["white_frac"],
+                                     fold_frac=sd["fold_frac"], stream=stream)
+        torch.cuda.synchronize()
+        gen_s = time.perf_counter() - t0
+    else:
+        img = synth.slide_image(H, W, sd["seed"])
+        rgb = torch.from_numpy(img.rgb).cuda()
     labels = torch.empty((H, W), dtype=torch.int32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     ctx = pkg.Context(stream=stream, **params)
     ctx.set_profiling(True)
+    geometry = args.geometry or sd.get("geometry")
+    if geometry:  # a pinned launch geometry instead of tuning on the first batch
+        g_str, s_str = geometry.split(":")
+        ctx.set_stage_grids([int(x) for x in g_str.split(",")])
+        ctx.set_stage_shapes([int(x) for x in s_str.split(",")])
     kw = dict(max_tile=sd["max_tile"], px_per_superpixel=sd["px_per_superpixel"], labels=labels)
-    _, M, T = ctx.refine_slide(rgb, autotune=not args.no_autotune, **kw)  # first warm-up run tunes
+    _, M, T = ctx.refine_slide(rgb, autotune=not args.no_autotune and not geometry, **kw)  # first warm-up run tunes
+    stats = torch.empty(M * pkg.SP_STATS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    kw["stats"] = stats  # the statistics of every slide-wide id, with the labels
     for _ in range(max(0, args.warmup - 1)):
         ctx.refine_slide(rgb, **kw)
     ctx.sync()
@@ -727,7 +788,11 @@ def run_slide(args, rank, world, local):
 
     e2e = None
     if not args.no_e2e:  # pinned host slide -> HBM, refine, labels -> pinned host
-        pin = torch.from_numpy(img.rgb).pin_memory()
+        if img is not None:
+            pin = torch.from_numpy(img.rgb).pin_memory()
+        else:
+            pin = torch.empty((H, W, 3), dtype=torch.uint8).pin_memory()
+            pin.copy_(rgb)
         lab_host = torch.empty((H, W), dtype=torch.int32).pin_memory()
         times = []
         for it in range(args.warmup + args.steps):
@@ -749,6 +814,9 @@ def run_slide(args, rank, world, local):
         cpu = {"value": rgb_s.shape[0] * rgb_s.shape[1] / ts[0] / 1e6, "unit": UNIT, "cores": 1,
                "kind": "oracle", "sample": desc, **host_cpu()}
 
+    free_b, total_b = torch.cuda.mem_get_info()
+    dev_used_gb = (total_b - free_b) / 1e9  # the slide, its labels and the context's buffers
+    parity = slide_parity(args.workload, rgb, labels, stats) if rank == 0 else None
     peak, peak_kind = measured_peak()
     dom = max(range(nst), key=lambda i: stage_ms[i])
     launch_ms, launch_bytes = stage_ms[dom] / args.steps, stage_bytes[dom] / args.steps
@@ -762,9 +830,13 @@ def run_slide(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "H": H, "W": W, "tiles": T, "max_tile": sd["max_tile"],
                        "M_total": M, "px_per_superpixel": sd["px_per_superpixel"],
-                       "batches": -(-T // pkg.RAPID_MAX_BATCH), "levels": L, "ratio_C": C,
+                       "batches": slide_batches(H, W, sd["max_tile"], sd["px_per_superpixel"]),
+                       "levels": L, "ratio_C": C,
                        "init_block": params["init_block"], "predict": params["predict"],
                        "schedule": "frontier queue" if params.get("schedule", 0) == 1 else "sweeps",
+                       "generator": ("counter-based, on the device" if gen_s is not None else "host"),
+                       "generation_s": gen_s, "parity": parity,
+                       "device_memory_in_use_gb": dev_used_gb,
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"kernel": f"stage_kernel, stage {dom} (level {st_dom.level}, block side {st_dom.block}), "

@@ -363,7 +363,9 @@ rapid_status rapid_synth_slide(const rapid_synth_params *p, uint8_t *rgb_dev, in
 /* Whole slide.  The slide (device, H x W interleaved RGB, rows rgb_pitch_bytes apart; any
  * size) is cut into tiles by even row and column bands of at most max_tile pixels
  * (startRow = H i / n, Eq. parallel_spit, on both axes); the tiles, as views into the
- * slide, are refined on ctx in batches of up to RAPID_MAX_BATCH (each with
+ * slide, are refined on ctx in batches of up to RAPID_MAX_BATCH tiles and at most 2^30
+ * pixels (a batch's block and label indices are 32-bit; a larger tile forms a batch alone;
+ * each with
  * K = max(1, area / px_per_superpixel) and ctx's parameters), and every tile's labels are
  * written into labels_dev (device, H x W int32, rows labels_pitch_bytes apart) as
  * slide-wide ids: the tiles' superpixels numbered one after another, tile by tile in
@@ -458,6 +460,24 @@ rapid_status rapid_run_static(const rapid_params *p, const uint8_t *rgb_dev, int
                               void *cuda_stream);
 
 /* Human-readable name of a status.  Never NULL. */
+/* Race check (a debug mode): with on = 1 every label write of a phase also stamps its
+ * block with the phase, and a write counts a violation when its block is not of the
+ * phase's class, was already written in the phase, or has a block within distance 2
+ * written in the same phase -- the independence the 9-phase schedule relies on (two blocks
+ * deciding together never share a 3 x 3 window).  rapid_read_race_violations returns the
+ * count since the check was first turned on (synchronises); rapid_race_selftest runs the
+ * check on three scripted write sequences and returns their counts (expected 0, 2, 1).
+ * Costs one stamp per block of device memory and some atomics per move. */
+rapid_status rapid_set_race_check(rapid_ctx *ctx, int32_t on);
+rapid_status rapid_read_race_violations(rapid_ctx *ctx, int64_t *out);
+rapid_status rapid_race_selftest(int64_t *violations3);
+
+/* Test hook for failure handling: the n-th device allocation the library attempts from
+ * now on fails as if the device were out of memory (n = 1: the next one); n <= 0 turns it
+ * off.  Process-wide; the calls that meet the failure return RAPID_ENOMEM and the context
+ * stays destroyable.  Not for production use. */
+void rapid_debug_fail_alloc(int64_t n);
+
 const char *rapid_status_string(rapid_status s);
 
 /* Free everything the context owns.  NULL-safe.  Synchronises its stream first. */

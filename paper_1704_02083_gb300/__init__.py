@@ -113,6 +113,10 @@ def lib() -> C.CDLL:
         "rapid_set_scorer": (i32, [P, P, C.c_float]),
         "rapid_set_keep_mask": (i32, [P, i32, i32, P, i64, i32]),
         "rapid_set_scorer_stages": (i32, [P, P, i32]),
+        "rapid_debug_fail_alloc": (None, [i64]),
+        "rapid_set_race_check": (i32, [P, i32]),
+        "rapid_read_race_violations": (i32, [P, pi64]),
+        "rapid_race_selftest": (i32, [pi64]),
         "rapid_synth_slide": (i32, [C.POINTER(rapid_synth_params), P, i64, P, i64, P]),
         "rapid_set_classifier": (i32, [P, P]),
         "rapid_read_features": (i32, [P, i32, P]),
@@ -334,6 +338,28 @@ def synth_slide_device(H: int, W: int, seed: int, regions: bool = False, px_per_
     s = (stream or torch.cuda.current_stream()).cuda_stream
     rapid_synth_slide(p, rgb.data_ptr(), 3 * W, reg.data_ptr() if reg is not None else None, 4 * W, s)
     return (rgb, reg) if regions else rgb
+
+
+def rapid_set_race_check(ctx: int, on: bool):
+    _check(lib().rapid_set_race_check(ctx, 1 if on else 0), "rapid_set_race_check")
+
+
+def rapid_read_race_violations(ctx: int) -> int:
+    v = C.c_int64()
+    _check(lib().rapid_read_race_violations(ctx, C.byref(v)), "rapid_read_race_violations")
+    return v.value
+
+
+def rapid_race_selftest():
+    """Violations the race check finds on its three scripted write sequences."""
+    v = (C.c_int64 * 3)()
+    _check(lib().rapid_race_selftest(v), "rapid_race_selftest")
+    return list(v)
+
+
+def rapid_debug_fail_alloc(n: int):
+    """Test hook: the n-th device allocation of the library from now on fails (0 = off)."""
+    lib().rapid_debug_fail_alloc(int(n))
 
 
 def rapid_set_scorer_stages(ctx: int, on):
@@ -636,6 +662,13 @@ class Context:
 
     def set_scorer(self, weights, threshold: float = 0.3):
         rapid_set_scorer(self.h, weights, threshold)
+
+    def set_race_check(self, on: bool = True):
+        rapid_set_race_check(self.h, on)
+        return self
+
+    def race_violations(self) -> int:
+        return rapid_read_race_violations(self.h)
 
     def set_scorer_stages(self, on):
         rapid_set_scorer_stages(self.h, on)

@@ -223,6 +223,7 @@ __device__ __forceinline__ bool decide_block_at(const StageArgs &a, const ImageD
   // snapshot means and counts, never S).
   const BlockSums &bs = in.bs;
   im.lab[idx] = k;
+  if (a.wstamp) race_check(a.race, a.wstamp, im.blk0, im.nbx, im.nby, bx, by, g, (g - 1) % 9);
   atomic_add_i64(&s.N[lbl], -bs.w);
   atomic_add_i64(&s.R[lbl], -bs.r);
   atomic_add_i64(&s.G[lbl], -bs.g);

@@ -11,6 +11,53 @@ static inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t
 
 // Level image of factor f (Sec. 2.2): coarse cell (X, Y) holds the exact R, G, B sums of
 // full-res [fX, min(fX + f, W)) x [fY, min(fY + f, H)).
+//
+// The finest sum level is read from the image: a CTA takes f rows and kPyrCells cells of
+// them (f * kPyrCells pixels per row), stages those rows in shared memory with 16-byte loads
+// when the image rows allow it (16-byte aligned base and pitch), and each thread sums one
+// cell from shared memory.  Every coarser level (its factor a multiple of the previous one's:
+// all are powers of two) is summed from the previous level's cells, never from the image.
+constexpr int kPyrCells = 256;
+constexpr int kPyrMaxF = 16;  // finest factor staged in shared memory (larger: per-thread sums)
+
+__global__ void __launch_bounds__(kPyrCells) pyramid_rows_kernel(const unsigned char *img, long long pitch, int H,
+                                                                  int W, int f, int Wl, int4 *out, int vec) {
+  extern __shared__ __align__(16) unsigned char rows[];  // f rows of 3 f kPyrCells bytes
+  const int Y = blockIdx.y, X0 = blockIdx.x * kPyrCells;
+  const int x0 = X0 * f, y0 = Y * f;
+  const int nrow = min(f, H - y0);
+  const int span = min(f * kPyrCells, W - x0);  // pixels of this CTA's rows
+  const int bytes = 3 * span, stride = 3 * f * kPyrCells;
+  if (vec) {  // 16-byte loads; the last chunk may read up to 15 bytes past the row, within its pitch
+    const int chunks = (bytes + 15) / 16;
+    for (int t = threadIdx.x; t < nrow * chunks; t += blockDim.x) {
+      const int r = t / chunks, c = t % chunks;
+      const uint4 v = *reinterpret_cast<const uint4 *>(img + (long long)(y0 + r) * pitch + 3ll * x0 + 16 * c);
+      *reinterpret_cast<uint4 *>(rows + r * stride + 16 * c) = v;
+    }
+  } else {
+    for (int t = threadIdx.x; t < nrow * bytes; t += blockDim.x) {
+      const int r = t / bytes, c = t % bytes;
+      rows[r * stride + c] = img[(long long)(y0 + r) * pitch + 3ll * x0 + c];
+    }
+  }
+  __syncthreads();
+  const int X = X0 + threadIdx.x;
+  if (X >= Wl) return;
+  const int cx0 = threadIdx.x * f, cw = min(f, span - cx0);
+  int r = 0, g = 0, b = 0;
+  for (int yy = 0; yy < nrow; yy++) {
+    const unsigned char *row = rows + yy * stride + 3 * cx0;
+    for (int x = 0; x < cw; x++) {
+      r += row[3 * x];
+      g += row[3 * x + 1];
+      b += row[3 * x + 2];
+    }
+  }
+  out[(long long)Y * Wl + X] = make_int4(r, g, b, 0);
+}
+
+// Per-thread sums straight from the image (factors too large to stage their rows).
 __global__ void pyramid_kernel(const unsigned char *img, long long pitch, int H, int W, int f, int Wl, int Hl,
                                int4 *out) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -29,10 +76,46 @@ __global__ void pyramid_kernel(const unsigned char *img, long long pitch, int H,
   out[i] = make_int4(r, g, b, 0);
 }
 
+// Coarser level: cell (X, Y) = the sum of the finer level's cells [mX, mX + m) x [mY, mY + m)
+// (clipped to the finer level), m = the ratio of the two factors.
+__global__ void pyramid_merge_kernel(const int4 *fine, int Wf, int Hf, int m, int Wl, int Hl, int4 *out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)Wl * Hl) return;
+  const int X = (int)(i % Wl), Y = (int)(i / Wl);
+  const int x1 = min(X * m + m, Wf), y1 = min(Y * m + m, Hf);
+  int r = 0, g = 0, b = 0;
+  for (int y = Y * m; y < y1; y++)
+    for (int x = X * m; x < x1; x++) {
+      const int4 c = fine[(long long)y * Wf + x];
+      r += c.x;
+      g += c.y;
+      b += c.z;
+    }
+  out[i] = make_int4(r, g, b, 0);
+}
+
 cudaError_t launch_pyramid(const unsigned char *img, long long pitch, int H, int W, int f, int Wl, int Hl,
                            int4 *out, cudaStream_t s) {
+  if (f > kPyrMaxF || Hl > 65535) {
+    const long long n = (long long)Wl * Hl;
+    pyramid_kernel<<<blocks_for(n, 256), 256, 0, s>>>(img, pitch, H, W, f, Wl, Hl, out);
+    return cudaGetLastError();
+  }
+  const int vec = ((uintptr_t)img % 16 == 0 && pitch % 16 == 0) ? 1 : 0;
+  const size_t smem = (size_t)f * 3 * f * kPyrCells + 16;
+  if (smem > 48 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(pyramid_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  pyramid_rows_kernel<<<dim3((Wl + kPyrCells - 1) / kPyrCells, Hl), kPyrCells, smem, s>>>(img, pitch, H, W, f, Wl,
+                                                                                         out, vec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pyramid_merge(const int4 *fine, int Wf, int Hf, int m, int Wl, int Hl, int4 *out, cudaStream_t s) {
   const long long n = (long long)Wl * Hl;
-  pyramid_kernel<<<blocks_for(n, 256), 256, 0, s>>>(img, pitch, H, W, f, Wl, Hl, out);
+  pyramid_merge_kernel<<<blocks_for(n, 256), 256, 0, s>>>(fine, Wf, Hf, m, Wl, Hl, out);
   return cudaGetLastError();
 }
 

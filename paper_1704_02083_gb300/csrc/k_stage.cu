@@ -1,5 +1,6 @@
 // k_stage.cu — dispatch of the stage kernel over its evaluation-tile shapes (kShapes in
 // rapid_dev.cuh; one translation unit per shape).
+#include "../../include/rapid.h"
 #include "rapid_dev.cuh"
 
 namespace rapid {
@@ -38,4 +39,34 @@ cudaError_t launch_stage(const StageArgs &a, int grid, int block, cudaStream_t s
   }
 }
 
+// Three scripted write sequences through the race check on a 6 x 6 block grid, one phase
+// each (g = 1, 2, 3): class-0 blocks 3 apart (no violation); a class-0 block, then a block 2
+// to its right (wrong class, and within distance 2 of the first: two); the same block twice
+// (one).
+__global__ void race_selftest_kernel(int *wstamp, unsigned long long *out) {
+  for (int i = 0; i < 36; i++) wstamp[i] = 0;
+  const int A[4][2] = {{0, 0}, {3, 0}, {0, 3}, {3, 3}}, B[2][2] = {{0, 0}, {2, 0}}, Cw[2][2] = {{3, 3}, {3, 3}};
+  for (int i = 0; i < 4; i++) race_check(out + 0, wstamp, 0, 6, 6, A[i][0], A[i][1], 1, 0);
+  for (int i = 0; i < 2; i++) race_check(out + 1, wstamp, 0, 6, 6, B[i][0], B[i][1], 2, 0);
+  for (int i = 0; i < 2; i++) race_check(out + 2, wstamp, 0, 6, 6, Cw[i][0], Cw[i][1], 3, 0);
+}
+
 }  // namespace rapid
+
+extern "C" rapid_status rapid_race_selftest(int64_t *violations3) {
+  if (!violations3) return RAPID_EINVAL;
+  int *w = nullptr;
+  unsigned long long *v = nullptr;
+  rapid_status rs = RAPID_OK;
+  if (cudaMalloc(&w, 36 * sizeof(int)) != cudaSuccess || cudaMalloc(&v, 3 * sizeof(unsigned long long)) != cudaSuccess)
+    rs = RAPID_ENOMEM;
+  unsigned long long h[3] = {0, 0, 0};
+  if (rs == RAPID_OK && (cudaMemset(v, 0, sizeof h) != cudaSuccess ||
+                         (rapid::race_selftest_kernel<<<1, 1>>>(w, v), cudaGetLastError()) != cudaSuccess ||
+                         cudaMemcpy(h, v, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess))
+    rs = RAPID_ECUDA;
+  cudaFree(w);
+  cudaFree(v);
+  for (int i = 0; i < 3; i++) violations3[i] = (int64_t)h[i];
+  return rs;
+}

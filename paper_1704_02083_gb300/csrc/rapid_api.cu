@@ -4,6 +4,7 @@
 // (through the dispatcher k_stage.cu) and, for the learned scorer, k_scorer.cu.
 #include <algorithm>
 #include <climits>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -15,6 +16,7 @@
 namespace rapid {
 cudaError_t launch_pyramid(const unsigned char *img, long long pitch, int H, int W, int f, int Wl, int Hl,
                            int4 *out, cudaStream_t s);
+cudaError_t launch_pyramid_merge(const int4 *fine, int Wf, int Hf, int m, int Wl, int Hl, int4 *out, cudaStream_t s);
 cudaError_t launch_seed(const StageArgs &a, const ImageDesc *ims, const int *gx, const int *gy, int n,
                         cudaStream_t s, int *launches);
 cudaError_t launch_recompute(const StageArgs &a, const ImageDesc *ims, int n, cudaStream_t s, int *launches);
@@ -79,6 +81,10 @@ struct rapid_ctx {
   size_t wl_bytes_cap;
   int wl_cap;
   unsigned *d_cbits, *d_rbits;  // sweep schedule: per-class block bitmaps, sized for the largest stage
+  int *d_wstamp;  // race check: per block, the phase that last wrote it (rapid_set_race_check)
+  size_t wstamp_cap;
+  unsigned long long *d_race;  // race check: violations
+  int race_on;
   size_t cbits_cap, rbits_cap;
   int cwb[RAPID_MAX_STAGES][10];  // per stage: first word of each class's bitmaps (all images)
   // per (stage, image) descriptors
@@ -147,6 +153,27 @@ struct rapid_trainer {
   float *buf_y;
   int *buf_count;
 };
+
+// Every device allocation of the library goes through dev_malloc, so that a test can make
+// the n-th one fail (rapid_debug_fail_alloc) and check that each call reports RAPID_ENOMEM
+// and leaves the context destroyable.  The countdown is process-wide; 0 = off.
+static std::atomic<long long> g_fail_alloc_after{0};
+
+static cudaError_t dev_malloc(void **p, size_t bytes) {
+  long long n = g_fail_alloc_after.load();
+  while (n > 0) {
+    if (g_fail_alloc_after.compare_exchange_weak(n, n - 1)) {
+      if (n == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
+extern "C" void rapid_debug_fail_alloc(int64_t n) { g_fail_alloc_after.store(n > 0 ? n : 0); }
 
 static rapid_status cuda_fail(rapid_ctx *c) {
   if (c) c->sticky = RAPID_ECUDA;
@@ -241,7 +268,7 @@ extern "C" rapid_status rapid_create(const rapid_params *p, void *cuda_stream, r
   }
   ctx->coop_grid = ctx->nsm * per_sm;
   ctx->cl = ctl_layout(kMaxBatch);
-  if (cudaMalloc(&ctx->d_ctl_block, ctx->cl.total) != cudaSuccess) {
+  if (dev_malloc((void **)&ctx->d_ctl_block, ctx->cl.total) != cudaSuccess) {
     delete ctx;
     return RAPID_ENOMEM;
   }
@@ -296,6 +323,9 @@ static void free_image_buffers(rapid_ctx *ctx) {
   cudaFree(ctx->d_wl);
   ctx->d_wl = nullptr;
   ctx->wl_bytes_cap = 0;
+  cudaFree(ctx->d_wstamp);
+  ctx->d_wstamp = nullptr;
+  ctx->wstamp_cap = 0;
   cudaFree(ctx->d_cbits);
   ctx->d_cbits = nullptr;
   ctx->cbits_cap = 0;
@@ -336,6 +366,7 @@ extern "C" void rapid_destroy(rapid_ctx *ctx) {
   cudaFree(ctx->d_ctl_block);
   cudaFree(ctx->d_scorer);
   cudaFree(ctx->d_scorer_tmp);
+  cudaFree(ctx->d_race);
   for (int i = 0; i < RAPID_MAX_STAGES; i++)
     if (ctx->ev_ok[i]) {
       cudaEventDestroy(ctx->ev[i][0]);
@@ -387,7 +418,7 @@ static bool grow(T **pp, size_t *cap, size_t need) {
   cudaFree(*pp);
   *pp = nullptr;
   *cap = 0;
-  if (cudaMalloc((void **)pp, need ? need : 1) != cudaSuccess) return false;
+  if (dev_malloc((void **)pp, need ? need : 1) != cudaSuccess) return false;
   *cap = need;
   return true;
 }
@@ -401,7 +432,7 @@ static rapid_status ensure_label_arrays(rapid_ctx *ctx, int M) {
   ctx->d_label_block = nullptr;
   ctx->M_cap = 0;
   const size_t bytes = label_arrays_bytes(M);
-  if (cudaMalloc(&ctx->d_label_block, bytes) != cudaSuccess) return RAPID_ENOMEM;
+  if (dev_malloc((void **)&ctx->d_label_block, bytes) != cudaSuccess) return RAPID_ENOMEM;
   carve_label_arrays(ctx->d_label_block, bytes, M, &ctx->st, &ctx->mg);
   ctx->M_cap = M;
   return RAPID_OK;
@@ -572,6 +603,7 @@ extern "C" rapid_status rapid_set_images(rapid_ctx *ctx, int32_t n, const uint8_
   rs = ensure_label_arrays(ctx, ctx->M_total);
   if (rs != RAPID_OK) return rs;
   if (ctx->scorer_on && !grow(&ctx->d_mask, &ctx->mask_cap, lab_n)) return RAPID_ENOMEM;
+  if (ctx->race_on && !grow(&ctx->d_wstamp, &ctx->wstamp_cap, lab_n * sizeof(int))) return RAPID_ENOMEM;
   if (ctx->logger) {
     if (!grow(&ctx->d_feat, &ctx->feat_cap, lab_n * kScorerFeatures() * sizeof(float))) return RAPID_ENOMEM;
     if (!grow(&ctx->d_before, &ctx->before_cap, lab_n * sizeof(int))) return RAPID_ENOMEM;
@@ -636,6 +668,8 @@ static StageArgs stage_args(rapid_ctx *ctx, int s) {
   a.wl_cap = ctx->wl_cap;
   a.cbits = ctx->d_cbits;
   a.rbits = ctx->d_rbits;
+  a.wstamp = ctx->race_on ? ctx->d_wstamp : nullptr;
+  a.race = ctx->d_race;
   for (int c = 0; c < 10; c++) a.cwb[c] = ctx->cwb[s][c];
   return a;
 }
@@ -649,10 +683,15 @@ extern "C" rapid_status rapid_seed_grid(rapid_ctx *ctx, int32_t *M_out) {
   // level images (exact box sums, Sec. 2.2) and the extra box-sum levels for block sums
   for (int i = 0; i < ctx->nimg; i++) {
     const ImgHost &h = ctx->im[i];
-    for (int l = 0; l < ctx->nsf; l++) {
+    for (int l = 0; l < ctx->nsf; l++) {  // the finest level from the image, each coarser one from the last
       const int sf = ctx->sf[l];
-      CK(launch_pyramid(ctx->d_img + h.img_off, h.pitch, h.H, h.W, sf, ceil_div(h.W, sf), ceil_div(h.H, sf),
-                        ctx->d_pyr[l] + h.pyr_off[l], ctx->stream));
+      if (l == 0)
+        CK(launch_pyramid(ctx->d_img + h.img_off, h.pitch, h.H, h.W, sf, ceil_div(h.W, sf), ceil_div(h.H, sf),
+                          ctx->d_pyr[l] + h.pyr_off[l], ctx->stream));
+      else
+        CK(launch_pyramid_merge(ctx->d_pyr[l - 1] + h.pyr_off[l - 1], ceil_div(h.W, ctx->sf[l - 1]),
+                                ceil_div(h.H, ctx->sf[l - 1]), sf / ctx->sf[l - 1], ceil_div(h.W, sf),
+                                ceil_div(h.H, sf), ctx->d_pyr[l] + h.pyr_off[l], ctx->stream));
       ctx->launches++;
     }
   }
@@ -983,7 +1022,7 @@ extern "C" rapid_status rapid_set_scorer(rapid_ctx *ctx, const float *weights, f
   if (ctx->keep_on) return RAPID_EINVAL;          // one source of masks at a time
   for (int i = 0; i < RAPID_SCORER_PARAMS; i++)
     if (!std::isfinite(weights[i])) return RAPID_EINVAL;
-  if (!ctx->d_scorer && cudaMalloc(&ctx->d_scorer, scorer_dev_bytes()) != cudaSuccess) return RAPID_ENOMEM;
+  if (!ctx->d_scorer && dev_malloc((void **)&ctx->d_scorer, scorer_dev_bytes()) != cudaSuccess) return RAPID_ENOMEM;
   CK(scorer_upload(weights, ctx->d_scorer, &ctx->sdev, ctx->stream));
   ctx->scorer_thr = threshold;
   ctx->scorer_on = 1;
@@ -991,6 +1030,35 @@ extern "C" rapid_status rapid_set_scorer(rapid_ctx *ctx, const float *weights, f
     if (!grow(&ctx->d_mask, &ctx->mask_cap, ctx->lab_total)) return RAPID_ENOMEM;
     return build_descriptors(ctx);
   }
+  return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_set_race_check(rapid_ctx *ctx, int32_t on) {
+  if (!ctx || (on & ~1)) return RAPID_EINVAL;
+  if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  drop_graph(ctx);
+  if (!on) {
+    ctx->race_on = 0;
+    return RAPID_OK;
+  }
+  if (!ctx->d_race) {
+    if (dev_malloc((void **)&ctx->d_race, sizeof(unsigned long long)) != cudaSuccess) return RAPID_ENOMEM;
+    CK(cudaMemsetAsync(ctx->d_race, 0, sizeof(unsigned long long), ctx->stream));
+  }
+  if (ctx->image_set && !grow(&ctx->d_wstamp, &ctx->wstamp_cap, ctx->lab_total * sizeof(int))) return RAPID_ENOMEM;
+  ctx->race_on = 1;
+  return RAPID_OK;
+}
+
+extern "C" rapid_status rapid_read_race_violations(rapid_ctx *ctx, int64_t *out) {
+  if (!ctx || !out) return RAPID_EINVAL;
+  if (ctx->sticky != RAPID_OK) return ctx->sticky;
+  unsigned long long v = 0;
+  if (ctx->d_race) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(&v, ctx->d_race, sizeof v, cudaMemcpyDeviceToHost));
+  }
+  *out = (int64_t)v;
   return RAPID_OK;
 }
 
@@ -1060,7 +1128,7 @@ extern "C" rapid_status rapid_scorer_scores(rapid_ctx *ctx, int32_t i, const flo
   if (ctx->sticky != RAPID_OK) return ctx->sticky;
   if (ctx->cur < 0) return RAPID_ESTATE;
   if (i < 0 || i >= ctx->nimg) return RAPID_EINVAL;
-  if (!ctx->d_scorer_tmp && cudaMalloc(&ctx->d_scorer_tmp, scorer_dev_bytes()) != cudaSuccess) return RAPID_ENOMEM;
+  if (!ctx->d_scorer_tmp && dev_malloc((void **)&ctx->d_scorer_tmp, scorer_dev_bytes()) != cudaSuccess) return RAPID_ENOMEM;
   ScorerDev w;
   CK(scorer_upload(weights, ctx->d_scorer_tmp, &w, ctx->stream));
   StageArgs a = stage_args(ctx, ctx->cur);
@@ -1077,10 +1145,10 @@ extern "C" rapid_status rapid_trainer_create(int64_t capacity, float neg_rate, r
   if (!t) return RAPID_ENOMEM;
   std::memset(t, 0, sizeof *t);
   t->neg_rate = neg_rate;
-  bool ok = cudaMalloc(&t->buf_x, (size_t)capacity * kScorerPatchFloats * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&t->buf_inb, (size_t)capacity * sizeof(unsigned long long)) == cudaSuccess &&
-            cudaMalloc(&t->buf_y, (size_t)capacity * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&t->buf_count, sizeof(int)) == cudaSuccess &&
+  bool ok = dev_malloc((void **)&t->buf_x, (size_t)capacity * kScorerPatchFloats * sizeof(float)) == cudaSuccess &&
+            dev_malloc((void **)&t->buf_inb, (size_t)capacity * sizeof(unsigned long long)) == cudaSuccess &&
+            dev_malloc((void **)&t->buf_y, (size_t)capacity * sizeof(float)) == cudaSuccess &&
+            dev_malloc((void **)&t->buf_count, sizeof(int)) == cudaSuccess &&
             cudaMemset(t->buf_count, 0, sizeof(int)) == cudaSuccess;
   if (!ok) {
     rapid_trainer_destroy(t);
@@ -1182,9 +1250,9 @@ extern "C" rapid_status rapid_trainer_fit(rapid_trainer *t, int32_t epochs, int3
   int *horder = (int *)std::malloc((size_t)n * sizeof(int));
   rapid_status rs = RAPID_OK;
   const size_t nparts = (size_t)train_max_ctas();
-  if (!horder || cudaMalloc(&d, (4 * (size_t)nP + 1) * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&part, nparts * (nP + 1) * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&order, (size_t)n * sizeof(int)) != cudaSuccess)
+  if (!horder || dev_malloc((void **)&d, (4 * (size_t)nP + 1) * sizeof(float)) != cudaSuccess ||
+      dev_malloc((void **)&part, nparts * (nP + 1) * sizeof(float)) != cudaSuccess ||
+      dev_malloc((void **)&order, (size_t)n * sizeof(int)) != cudaSuccess)
     rs = RAPID_ENOMEM;
   float *w = d, *m = d + nP, *v = d + 2 * nP, *grad = d + 3 * nP, *loss = d + 4 * nP;
   float *part_loss = part + nparts * nP;
@@ -1259,9 +1327,9 @@ extern "C" rapid_status rapid_trainer_gradient(rapid_trainer *t, const float *we
   int *order = nullptr;
   int *horder = (int *)std::malloc((size_t)count * sizeof(int));
   rapid_status rs = RAPID_OK;
-  if (!horder || cudaMalloc(&d, (2 * (size_t)nP + 1) * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&part, nparts * (nP + 1) * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&order, (size_t)count * sizeof(int)) != cudaSuccess)
+  if (!horder || dev_malloc((void **)&d, (2 * (size_t)nP + 1) * sizeof(float)) != cudaSuccess ||
+      dev_malloc((void **)&part, nparts * (nP + 1) * sizeof(float)) != cudaSuccess ||
+      dev_malloc((void **)&order, (size_t)count * sizeof(int)) != cudaSuccess)
     rs = RAPID_ENOMEM;
   for (int i = 0; i < count && horder; i++) horder[i] = (int)(first + i);
   float *w = d, *grad = d + nP, *loss = d + 2 * nP;
@@ -1282,6 +1350,8 @@ extern "C" rapid_status rapid_trainer_gradient(rapid_trainer *t, const float *we
 }
 
 // ---------------------------------------------------------------- whole slides
+static constexpr long long kSlideBatchPixels = 1ll << 30;
+
 extern "C" rapid_status rapid_refine_slide(rapid_ctx *ctx, const uint8_t *rgb_dev, int64_t H, int64_t W,
                                            int64_t rgb_pitch_bytes, int32_t max_tile, int32_t px_per_superpixel,
                                            int32_t autotune, int32_t *labels_dev, int64_t labels_pitch_bytes,
@@ -1302,10 +1372,15 @@ extern "C" rapid_status rapid_refine_slide(rapid_ctx *ctx, const uint8_t *rgb_de
   long long id_base = 0, t = 0;
   bool tuned = false;
   while (rs == RAPID_OK && t < nr * nc) {
+    // a batch: up to kMaxBatch tiles and at most kSlideBatchPixels pixels (its block and label
+    // indices are 32-bit), at least one tile
     int n = 0;
+    long long batch_px = 0;
     for (; n < kMaxBatch && t < nr * nc; n++, t++) {
       const long long i = t / nc, j = t % nc;
       const long long r0 = H * i / nr, r1 = H * (i + 1) / nr, c0 = W * j / nc, c1 = W * (j + 1) / nc;
+      if (n > 0 && batch_px + (r1 - r0) * (c1 - c0) > kSlideBatchPixels) break;
+      batch_px += (r1 - r0) * (c1 - c0);
       ptrs[n] = rgb_dev + r0 * rgb_pitch_bytes + 3 * c0;
       hs[n] = (int32_t)(r1 - r0);
       ws[n] = (int32_t)(c1 - c0);
@@ -1489,7 +1564,7 @@ extern "C" rapid_status rapid_set_profiling(rapid_ctx *ctx, int32_t on) {
 extern "C" rapid_status rapid_simple_table(uint8_t *out256) {
   if (!out256) return RAPID_EINVAL;
   unsigned char *d = nullptr;
-  if (cudaMalloc(&d, 256) != cudaSuccess) return RAPID_ENOMEM;
+  if (dev_malloc((void **)&d, 256) != cudaSuccess) return RAPID_ENOMEM;
   cudaError_t e = launch_simple_table(d, 0);
   if (e == cudaSuccess) e = cudaMemcpy(out256, d, 256, cudaMemcpyDeviceToHost);
   cudaFree(d);

@@ -183,6 +183,8 @@ struct StageArgs {
   int wl_cap;         // entries one class can hold (its blocks over all images)
   // sweep schedule: per phase class, one bit per block of the class lattice (class_words
   // below), class-major over the images: class c's words are [cwb[c], cwb[c + 1])
+  int *wstamp;        // race check (null when off): per block of the stage, the phase that last wrote it
+  unsigned long long *race;  // race check: violations found
   unsigned *cbits;    // 1 = the block may be eligible (a superset of the eligible blocks)
   unsigned *rbits;    // 1 = the block requested a merge at its last evaluation
   int cwb[10];
@@ -291,6 +293,25 @@ __host__ __device__ inline bool simple_mask(unsigned m) {
   int runs = popc8(m & ~prev);
   int lone_corners = popc8(m & 0x55u & ~prev & ~next);
   return runs - lone_corners == 1;
+}
+
+// ---------------------------------------------------------------- race check
+// A phase may write only labels of blocks of its class (by % 3, bx % 3), each once, and
+// these are at least 3 apart (Chebyshev), so no two deciding blocks share a 3 x 3 window.
+// With the check on, every label write of a phase (a move) stamps its block (global index
+// idx) with the phase number g and counts a violation when the block is not of the class
+// `phase`, was already stamped in this phase, or finds a block within distance 2 stamped in
+// this phase (whichever of two conflicting writes comes second sees the first).
+__device__ inline void race_check(unsigned long long *race, int *wstamp, long long blk0, int nbx, int nby, int bx,
+                                  int by, int g, int phase) {
+  if ((by % 3) * 3 + bx % 3 != phase) atomicAdd(race, 1ull);
+  if (atomicExch(wstamp + blk0 + (long long)by * nbx + bx, g) == g) atomicAdd(race, 1ull);
+  for (int dy = -2; dy <= 2; dy++)
+    for (int dx = -2; dx <= 2; dx++) {
+      const int x = bx + dx, y = by + dy;
+      if ((dx == 0 && dy == 0) || x < 0 || y < 0 || x >= nbx || y >= nby) continue;
+      if (atomicAdd(wstamp + blk0 + (long long)y * nbx + x, 0) == g) atomicAdd(race, 1ull);
+    }
 }
 
 // ---------------------------------------------------------------- grid barrier

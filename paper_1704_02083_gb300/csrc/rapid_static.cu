@@ -25,6 +25,7 @@
 namespace rapid {
 cudaError_t launch_pyramid(const unsigned char *img, long long pitch, int H, int W, int f, int Wl, int Hl,
                            int4 *out, cudaStream_t s);
+cudaError_t launch_pyramid_merge(const int4 *fine, int Wf, int Hf, int m, int Wl, int Hl, int4 *out, cudaStream_t s);
 cudaError_t launch_seed(const StageArgs &a, const ImageDesc *ims, const int *gx, const int *gy, int n,
                         cudaStream_t s, int *launches);
 cudaError_t launch_recompute(const StageArgs &a, const ImageDesc *ims, int n, cudaStream_t s, int *launches);
@@ -282,8 +283,12 @@ extern "C" rapid_status rapid_run_static(const rapid_params *p, const uint8_t *r
   // Start from a clean control block: barrier, error word, request counts, counters.
   CKS(cudaMemsetAsync(ctl, 0, cl.total, stream));
   CKS(cudaMemcpyAsync(d_desc, desc, (size_t)nst * sizeof(ImageDesc), cudaMemcpyHostToDevice, stream));
-  for (int l = 0; l < nsf; l++)
-    CKS(launch_pyramid(rgb_dev, rgb_pitch_bytes, H, W, sf[l], cdiv(W, sf[l]), cdiv(H, sf[l]), pyr[l], stream));
+  for (int l = 0; l < nsf; l++)  // the finest level from the image, each coarser one from the last
+    if (l == 0)
+      CKS(launch_pyramid(rgb_dev, rgb_pitch_bytes, H, W, sf[l], cdiv(W, sf[l]), cdiv(H, sf[l]), pyr[l], stream));
+    else
+      CKS(launch_pyramid_merge(pyr[l - 1], cdiv(W, sf[l - 1]), cdiv(H, sf[l - 1]), sf[l] / sf[l - 1], cdiv(W, sf[l]),
+                               cdiv(H, sf[l]), pyr[l], stream));
   Schedule sch;
   std::memset(&sch, 0, sizeof sch);
   sch.n = nst;

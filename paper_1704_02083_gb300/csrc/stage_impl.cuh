@@ -566,6 +566,12 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
     a.st.adj[k] = 0;
   }
   const long long nrec = (long long)a.ntiles * 9;
+  if (a.wstamp) {  // race check: no block written in this launch yet
+    const long long nb = (long long)(kBatch ? a.imgs[a.nimg - 1].blk0 : 0) +
+                         (long long)(kBatch ? a.imgs[a.nimg - 1].nbx : a.img0.nbx) *
+                             (kBatch ? a.imgs[a.nimg - 1].nby : a.img0.nby);
+    for (long long i = gtid; i < nb; i += gstride) a.wstamp[i] = 0;
+  }
   if (sweep_schedule<kSched>(a)) {  // sweep schedule: every block may be eligible when the stage starts
     for (int i = gtid; i < a.cwb[9]; i += gstride) {
       a.cbits[i] = ~0u;

@@ -248,7 +248,30 @@ SLIDES = {
     "slide16k_l3": dict(H=16384, W=12288, seed=5, max_tile=8192, px_per_superpixel=4096,
                         params=dict(num_levels=3, ratio_C=4, init_block=32, final_grain=1, size_mode=2,
                                     predict=1, reuse=1)),
+    # The whole-slide workload at its full size: 100000 x 80000 (24 GB of RGB), made on the
+    # device by the counter-based generator (slide_gen restates it on the host), 40% white,
+    # folds over about 5%, one Voronoi cell per 8192 px, one superpixel per 16384 px (about
+    # 488k), tiles of at most 8192^2 (Eq. parallel_spit on both axes: 13 x 10 tiles); the
+    # oracle's records cover the sampled tiles.
+    "slide100k_l3": dict(H=100000, W=80000, seed=5, max_tile=8192, px_per_superpixel=16384, generator="counter",
+                         px_per_cell=8192, white_frac=0.40, fold_frac=0.05, sample_tiles=(0, 65, 129),
+                         geometry="152,152,152,152,152,152:4,4,4,4,4,4",
+                         params=dict(num_levels=3, ratio_C=4, init_block=32, final_grain=1, size_mode=2,
+                                     predict=1, reuse=1)),
 }
+
+
+def slide_tiles(H: int, W: int, max_tile: int, px_per_superpixel: int):
+    """The tiles of a slide as rapid_refine_slide cuts it: even row and column bands of at
+    most max_tile px (Eq. parallel_spit on both axes), row-major; per tile (row0, col0,
+    height, width, K)."""
+    nr, nc = -(-H // max_tile), -(-W // max_tile)
+    out = []
+    for t in range(nr * nc):
+        i, j = divmod(t, nc)
+        r0, r1, c0, c1 = H * i // nr, H * (i + 1) // nr, W * j // nc, W * (j + 1) // nc
+        out.append((r0, c0, r1 - r0, c1 - c0, max(1, (r1 - r0) * (c1 - c0) // px_per_superpixel)))
+    return out
 # The same batch and slide refined with the queue schedule.
 for _d in (BATCHES, SLIDES):
     for _name in list(_d):

@@ -48,6 +48,8 @@ def _null_calls(pkg):
         "rapid_set_scorer": (None, None, C.c_float(0.5)),
         "rapid_set_keep_mask": (None, 0, 0, buf, 16, 0),
         "rapid_set_scorer_stages": (None, None, 0),
+        "rapid_set_race_check": (None, 1),
+        "rapid_read_race_violations": (None, C.byref(i64)),
         "rapid_set_classifier": (None, None),
         "rapid_read_features": (None, 0, buf),
         "rapid_scorer_features": (None, 0, buf),
@@ -76,7 +78,7 @@ def test_null_handles_are_refused(pkg):
     takes_handle = {n for n in test_abi.declared_functions()
                     if n not in ("rapid_default_params", "rapid_status_string", "rapid_destroy",
                                  "rapid_trainer_destroy", "rapid_trainer_create", "rapid_run_static",
-                                 "rapid_synth_slide")}
+                                 "rapid_synth_slide", "rapid_debug_fail_alloc", "rapid_race_selftest")}
     assert takes_handle <= set(calls), sorted(takes_handle - set(calls))
 
 

@@ -1,5 +1,6 @@
 """The two exact shortcuts of the stage kernel: single-precision decisions with a certified
-error bound (binary64 when undecided) and skipping tiles whose inputs did not change.
+error bound (binary64 when undecided) and skipping decisions whose inputs did not change
+(skip_tiles: unchanged blocks under the sweep schedule, unqueued tiles under the queue one).
 Both must leave labels, statistics and every oracle counter unchanged, and the
 single-precision decisions must never disagree with binary64."""
 import numpy as np
@@ -51,6 +52,33 @@ def test_filter_never_disagrees_with_binary64(name, rgb, params):
     assert fallbacks <= evaluated
     if name != "flat-ish":  # exact ties are common there and go to binary64 by design
         assert fallbacks < 0.05 * evaluated, (fallbacks, evaluated)
+
+
+EXTREMES = [
+    ("lam_pos0_0", dict(lambda_pos0=0.0)),
+    ("lam_pos0_1e6", dict(lambda_pos0=1e6)),
+    ("lam_b_0", dict(lambda_b=0.0)),
+    ("lam_b_1e4", dict(lambda_b=1e4)),
+    ("both_large", dict(lambda_pos0=1e6, lambda_b=1e4)),
+]
+
+
+@pytest.mark.parametrize("name,extra", EXTREMES, ids=[e[0] for e in EXTREMES])
+def test_filter_at_parameter_extremes(name, extra):
+    """The certified single-precision decisions where float magnitudes and the bound's
+    widening are most stressed: position weights of 0 and 10^6, boundary weights of 0 and
+    10^4, and coarse blocks (initial block 512 on a 2048 x 1536 image, blocks of 2^18
+    pixels): no disagreement with binary64, and the run equal to the binary64-only run."""
+    rgb = synth.he_image(2048, 1536, 80, 12).rgb
+    params = dict(num_levels=3, ratio_C=4, init_block=512, final_grain=8, K=48, size_mode=2, predict=1,
+                  max_sweeps=24, **extra)
+    stages, _ = gpu_counters(rgb, verify_filter=1, **params)
+    assert sum(s.filter_mismatches for s in stages) == 0
+    assert sum(s.evaluated for s in stages) > 0
+    ref = gpu_run(rgb, use_filter=0, **params)
+    got = gpu_run(rgb, use_filter=1, **params)
+    for x, y in zip(got, ref):
+        np.testing.assert_array_equal(x, y, err_msg=name)
 
 
 def test_tiles_are_skipped_on_long_stages():

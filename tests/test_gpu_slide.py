@@ -98,3 +98,37 @@ def test_slide_tile_against_oracle():
     tile = np.ascontiguousarray(img.rgb[0:100, 0:86])
     rlab = oracle_run(tile, K=max(1, 100 * 86 // 512), **PARAMS)[0]
     np.testing.assert_array_equal(lab[0:100, 0:86], rlab)
+
+
+def test_counter_slide_on_the_device_tiles_against_the_oracle():
+    """The whole-slide workload's pipeline at a small size: the slide made on the device by
+    the counter-based generator, refined by rapid_refine_slide with the full-size workload's
+    schedule; sampled tiles, each generated alone on the host from the same definition, against
+    the oracle (labels, and the statistics of their slide-wide ids)."""
+    import torch
+
+    import paper_1704_02083_gb300 as pkg
+
+    sd = synth.SLIDES["slide100k_l3"]
+    H, W, max_tile, pps = 2600, 2100, 1024, 16384
+    params = dict(sd["params"])
+    rgb = pkg.synth_slide_device(H, W, 13)
+    with pkg.Context(stream=torch.cuda.current_stream(), **params) as ctx:
+        stats = torch.zeros((20000 * pkg.SP_STATS_DTYPE.itemsize,), dtype=torch.uint8, device="cuda")
+        labels, M, T = ctx.refine_slide(rgb, max_tile=max_tile, px_per_superpixel=pps, stats=stats)
+        torch.cuda.synchronize()
+    tiles = synth.slide_tiles(H, W, max_tile, pps)
+    assert T == len(tiles) == 9
+    lab = labels.cpu().numpy()
+    st = stats.cpu().numpy()[: M * pkg.SP_STATS_DTYPE.itemsize].view(pkg.SP_STATS_DTYPE)
+    bases = np.cumsum([0] + [_seed_count(h, w, K, s0=32) for (_, _, h, w, K) in tiles])
+    assert bases[-1] == M
+    for t in (0, 4, 8):
+        r0, c0, h, w, K = tiles[t]
+        host = synth.slide_gen(H, W, 13, x0=c0, y0=r0, h=h, w=w)
+        np.testing.assert_array_equal(rgb[r0:r0 + h, c0:c0 + w].cpu().numpy(), host.rgb)
+        rlab, rst, _, _, _ = oracle_run(host.rgb, K=K, **params)
+        np.testing.assert_array_equal(lab[r0:r0 + h, c0:c0 + w] - bases[t], rlab, err_msg=f"tile {t}")
+        got = np.stack([st[bases[t]:bases[t + 1]][f] for f in ("n", "sum_r", "sum_g", "sum_b", "sum_x", "sum_y",
+                                                                 "init_size")], 1)
+        np.testing.assert_array_equal(got, rst, err_msg=f"tile {t}")
