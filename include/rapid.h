@@ -116,11 +116,13 @@ typedef struct rapid_stage_counters {
   int64_t fp64_fallbacks;  /* evaluations the single-precision bound could not decide */
   int64_t filter_mismatches; /* with verify_filter: single-precision decisions that differ
                               from binary64 (must be 0) */
-  int64_t tiles_scanned;   /* tile-phase scans performed ... */
-  int64_t tiles_skipped;   /* ... and skipped because nothing they depend on changed (queue
-                              schedule: because none of their blocks of the phase class was
-                              queued; its sparse phases take listed blocks, not tiles, and
-                              count neither) */
+  int64_t tiles_scanned;   /* sweep schedule: blocks visited by the bitmap walk (their bit
+                              was set); queue schedule: tile-phase scans ... */
+  int64_t tiles_skipped;   /* sweep schedule: blocks that passed the tests and skipped the
+                              decision because nothing in their window changed since their
+                              previous visit; queue schedule: tiles skipped because none of
+                              their blocks of the phase class was queued (its sparse phases
+                              take listed blocks, not tiles, and count neither) */
   int64_t merge_searches;  /* merge-target searches that scanned the label map ... */
   int64_t merge_cache_hits; /* ... and requests answered by a still-valid earlier failure */
   float kernel_ms;         /* device time of the stage's refinement launch when profiling is
@@ -459,7 +461,6 @@ rapid_status rapid_run_static(const rapid_params *p, const uint8_t *rgb_dev, int
                               rapid_sp_stats *stats_dev, int64_t stats_capacity, int32_t *M_out,
                               void *cuda_stream);
 
-/* Human-readable name of a status.  Never NULL. */
 /* Race check (a debug mode): with on = 1 every label write of a phase also stamps its
  * block with the phase, and a write counts a violation when its block is not of the
  * phase's class, was already written in the phase, or has a block within distance 2
@@ -478,6 +479,7 @@ rapid_status rapid_race_selftest(int64_t *violations3);
  * stays destroyable.  Not for production use. */
 void rapid_debug_fail_alloc(int64_t n);
 
+/* Human-readable name of a status.  Never NULL. */
 const char *rapid_status_string(rapid_status s);
 
 /* Free everything the context owns.  NULL-safe.  Synchronises its stream first. */

@@ -44,9 +44,12 @@ def test_package_never_reaches_the_oracle():
 
 def test_oracle_includes_nothing_of_the_library():
     for p in _sources(ORACLE, (".c", ".h")):
-        incs = re.findall(r'#\s*include\s*[<"]([^">]+)[">]', open(p).read())
-        local = [i for i in incs if not i.startswith(("std", "math", "string"))]
+        src = open(p).read()
+        local = re.findall(r'#\s*include\s*"([^"]+)"', src)  # quoted: this project's own headers
         assert local in ([], ["rapid_oracle.h"]), (p, local)
+        system = re.findall(r'#\s*include\s*<([^>]+)>', src)  # C library and OpenMP only
+        assert all(i.split(".")[0] in ("stdint", "stdio", "stdlib", "string", "math", "omp", "stddef", "limits")
+                   for i in system), (p, system)
     for p in _sources(ORACLE, (".py",)):
         code = _code(p)
         assert "paper_1704_02083_gb300" not in code and "librapid" not in code, p

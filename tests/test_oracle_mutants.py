@@ -81,9 +81,9 @@ MUTANTS = [
            "int32_t py = phase / 3, px = phase % 3, M = st->M;",
            "int32_t px = phase / 3, py = phase % 3, M = st->M;", (BF,)),
     Mutant("size_rule_reads_live_counts", "the size rule reads the phase-start counts",
-           "if (r == 1) { mv[nmv].blk = blk; mv[nmv].a = st->lab[blk]; mv[nmv].k = k; nmv++; }",
-           "if (r == 1) { mv[nmv].blk = blk; mv[nmv].a = st->lab[blk]; mv[nmv].k = k; nmv++;"
-           " int64_t bb[6]; block_sums(st, bx, by, bb); N0[st->lab[blk]] -= bb[0]; }",
+           "r[j] = (int8_t)decide(st, bx, by, cR, cG, cB, mX, mY, N0, &kk[j], &e, &v);",
+           "r[j] = (int8_t)decide(st, bx, by, cR, cG, cB, mX, mY, N0, &kk[j], &e, &v);"
+           " if (r[j] == 1) { int64_t bb[6]; block_sums(st, bx, by, bb); N0[st->lab[blk]] -= bb[0]; }",
            (BF, INV)),
     Mutant("evaluated_counts_topology_failures", "a block counts as evaluated once it passes E_topo",
            "if (!st->lut[neighbour_mask(st, bx, by, a)]) return 0;\n  (*eval)++;",
