@@ -38,8 +38,9 @@ L2_FLUSH_BYTES = 256 << 20
 SAMPLE_SIDE = 1024  # CPU legs: a 1024 x 1024 tile of the same generator and parameters
 
 
-# evaluation-tile shapes of the stage kernel, by index (blocks per tile, threads per CTA)
-TILE_NAMES = ["32x16", "32x8", "64x16", "32x16/512t", "32x8/512t", "64x16/512t"]
+# builds of the stage kernel, by index: the queue schedule's evaluation-tile shape (blocks per
+# tile), the threads per CTA, and the sweep schedule's bitmap walk (warp or CTA)
+TILE_NAMES = ["32x16/cta", "32x8/warp", "64x16/cta", "32x16/512t/cta", "32x8/512t/warp", "64x16/512t/cta"]
 
 
 def parse():

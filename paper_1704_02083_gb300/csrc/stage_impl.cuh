@@ -47,6 +47,11 @@ namespace RAPID_SHAPE_NS {
 
 // Evaluation tiles of this unit: kTileW x kTileH blocks, one warp each.
 constexpr int kTileW = RAPID_TILE_W, kTileH = RAPID_TILE_H;
+// the sweep schedule's walk of this build: the CTA walk (1) or the warp walk (0)
+#ifndef RAPID_SWEEP_CTA
+#error "define RAPID_SWEEP_CTA (0 or 1) before including stage_impl.cuh"
+#endif
+constexpr bool kSweepCta = RAPID_SWEEP_CTA != 0;
 // blocks of one phase class in a tile, and 32-bit words of one bit each
 constexpr int kPhaseMax = ((kTileW + 2) / 3) * ((kTileH + 2) / 3);
 constexpr int kReqWords = (kPhaseMax + 31) / 32;
