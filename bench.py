@@ -252,7 +252,7 @@ def kernel_source_sha256(csrc=None):
     csrc = csrc or os.path.join(ROOT, "paper_1704_02083_gb300", "csrc")
     h = hashlib.sha256()
     for name in ("stage_impl.cuh", "eval_tile.cuh", "eval_sweep.cuh", "rapid_dev.cuh", "k_stage_s0.cu",
-                 "k_stage_s1.cu", "k_stage_s2.cu"):
+                 "k_stage_s1.cu", "k_stage_s2.cu", "k_stage_s3.cu", "k_stage_s4.cu", "k_stage_s5.cu"):
         for line in open(os.path.join(csrc, name), encoding="utf-8"):
             code = line.split("//", 1)[0].rstrip()
             if code:
