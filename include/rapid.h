@@ -219,13 +219,16 @@ rapid_status rapid_read_image_counters(rapid_ctx *ctx, int32_t i, rapid_counters
 /* Launch geometry.  Results never depend on it (a phase's decisions are independent and
  * merges are ordered by block index), only the time does.
  * rapid_set_stage_grids: CTAs of each stage's launch for stages 0 .. n-1 (0 = the full
- *   co-resident grid, larger values are capped to it; the others reset to 0).
+ *   co-resident grid, larger values are capped to it; the others reset to 0).  A single
+ *   image's stage of 2 to 16 CTAs runs as one thread-block cluster, whose hardware barrier
+ *   replaces the grid barrier, where the device can co-schedule such a cluster (else, and
+ *   for batches, as a cooperative launch).
  * rapid_set_stage_shapes: evaluation-tile shape of each stage, an index into
  *   {32 x 16, 32 x 8, 64 x 16} blocks with 1024 threads per CTA (0, 1, 2) or with 512 threads
  *   per CTA (3, 4, 5) (default 0; the others reset to 0).
  * rapid_autotune: time the whole schedule on the context's current images once per tile
- *   shape (full grid), then once per grid size (the full grid halved down to one CTA) with
- *   the chosen shapes; keep per stage the fastest and write them to grids_out and
+ *   shape (full grid), then once per grid size (the full grid halved down to one CTA, and
+ *   the cluster sizes 16 and 8) with the chosen shapes; keep per stage the fastest and write them to grids_out and
  *   shapes_out (RAPID_MAX_STAGES entries each, either may be NULL).  Synchronises; the
  *   context's results afterwards are those of a normal run.
  * EINVAL on a negative grid or an unknown shape, ESTATE without images. */

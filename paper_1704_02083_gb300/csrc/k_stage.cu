@@ -3,9 +3,12 @@
 #include "../../include/rapid.h"
 #include "rapid_dev.cuh"
 
+#include <mutex>
+#include <vector>
+
 namespace rapid {
 #define RAPID_SHAPE_DECL(NS)                                  \
-  const void *stage_kernel_ptr_##NS(bool batch, bool frontier); \
+  const void *stage_kernel_ptr_##NS(bool batch, bool frontier, bool cluster); \
   cudaError_t launch_stage_##NS(const StageArgs &a, int grid, int block, cudaStream_t s);
 RAPID_SHAPE_DECL(s0)
 RAPID_SHAPE_DECL(s1)
@@ -19,12 +22,77 @@ int stage_block_threads(int shape) { return kShapes[(shape >= 0 && shape < kNumS
 
 const void *stage_kernel_ptr(bool batch, bool frontier, int shape) {
   switch (shape) {
-    case 1: return stage_kernel_ptr_s1(batch, frontier);
-    case 2: return stage_kernel_ptr_s2(batch, frontier);
-    case 3: return stage_kernel_ptr_s3(batch, frontier);
-    case 4: return stage_kernel_ptr_s4(batch, frontier);
-    case 5: return stage_kernel_ptr_s5(batch, frontier);
-    default: return stage_kernel_ptr_s0(batch, frontier);
+    case 1: return stage_kernel_ptr_s1(batch, frontier, false);
+    case 2: return stage_kernel_ptr_s2(batch, frontier, false);
+    case 3: return stage_kernel_ptr_s3(batch, frontier, false);
+    case 4: return stage_kernel_ptr_s4(batch, frontier, false);
+    case 5: return stage_kernel_ptr_s5(batch, frontier, false);
+    default: return stage_kernel_ptr_s0(batch, frontier, false);
+  }
+}
+
+// Cluster support per (kernel, device): the largest cluster size found to fit (16, 8 or 0).
+namespace {
+struct ClusterFit {
+  const void *fn;
+  int device, block, max_size;
+};
+std::mutex g_cluster_mu;
+std::vector<ClusterFit> g_cluster_fit;
+
+int cluster_fit(const void *fn, int block) {
+  for (int size : {kMaxCluster, 8}) {
+    if (size > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(size);
+    cfg.blockDim = dim3(block);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = size;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (n >= 1) return size;
+  }
+  return 0;
+}
+}  // namespace
+
+bool cluster_launch_ok(const void *fn, int grid, int block, cudaStream_t s) {
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  std::lock_guard<std::mutex> lock(g_cluster_mu);
+  for (const ClusterFit &c : g_cluster_fit)
+    if (c.fn == fn && c.device == device && c.block == block) return grid <= c.max_size;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return false;
+  }
+  g_cluster_fit.push_back({fn, device, block, cluster_fit(fn, block)});
+  return grid <= g_cluster_fit.back().max_size;
+}
+
+const void *stage_cluster_kernel_ptr(bool frontier, int shape) {
+  switch (shape) {
+    case 1: return stage_kernel_ptr_s1(false, frontier, true);
+    case 2: return stage_kernel_ptr_s2(false, frontier, true);
+    case 3: return stage_kernel_ptr_s3(false, frontier, true);
+    case 4: return stage_kernel_ptr_s4(false, frontier, true);
+    case 5: return stage_kernel_ptr_s5(false, frontier, true);
+    default: return stage_kernel_ptr_s0(false, frontier, true);
   }
 }
 

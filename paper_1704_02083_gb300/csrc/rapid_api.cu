@@ -267,6 +267,11 @@ extern "C" rapid_status rapid_create(const rapid_params *p, void *cuda_stream, r
     return RAPID_ECUDA;
   }
   ctx->coop_grid = ctx->nsm * per_sm;
+  // which stage kernels can run as one thread-block cluster (decided now, outside any graph
+  // capture, and remembered)
+  for (int sh = 0; sh < kNumShapes; sh++)
+    for (int fr = 0; fr < 2; fr++)
+      cluster_launch_ok(stage_cluster_kernel_ptr(fr != 0, sh), 2, stage_block_threads(sh), ctx->stream);
   ctx->cl = ctl_layout(kMaxBatch);
   if (dev_malloc((void **)&ctx->d_ctl_block, ctx->cl.total) != cudaSuccess) {
     delete ctx;
@@ -921,9 +926,10 @@ extern "C" rapid_status rapid_set_stage_grids(rapid_ctx *ctx, const int32_t *gri
 // ordered by block index), only its time does: coarse stages with few tiles lose more to
 // the grid barrier than they gain from more SMs, and the best tile shape depends on the
 // stage.  First the whole schedule runs once per tile shape on the full grid, then once per
-// grid size (the full co-resident grid, then halvings down to one CTA) with the chosen
-// shapes; every stage is timed with events and keeps its fastest setting (ties to the
-// earlier candidate).  Each candidate runs twice, the first run warming up.
+// grid size (the full co-resident grid, its halvings down to one CTA, and 16 and 8 CTAs,
+// which run as one thread-block cluster) with the chosen shapes; every stage is timed with
+// events and keeps its fastest setting (ties to the earlier candidate).  Each candidate runs
+// twice, the first run warming up.
 static rapid_status time_stages(rapid_ctx *ctx, float *ms) {
   for (int rep = 0; rep < 2; rep++) {
     rapid_status rs = run_sequence(ctx);
@@ -964,7 +970,14 @@ extern "C" rapid_status rapid_autotune(rapid_ctx *ctx, int32_t *grids_out, int32
   }
   for (int s = 0; s < RAPID_MAX_STAGES; s++) ctx->stage_shape[s] = best_shape[s];
   if (rs == RAPID_OK) rs = build_descriptors(ctx);
-  for (int g = ctx->coop_grid / 2; g >= 1 && rs == RAPID_OK; g /= 2) {
+  // grid candidates: the halvings of the full grid, and the cluster sizes 16 and 8 (a grid of
+  // at most kMaxCluster CTAs runs as one thread-block cluster where the device allows it)
+  int cand[40], nc = 0;
+  for (int g = ctx->coop_grid / 2; g >= 1; g /= 2) cand[nc++] = g;
+  for (int g : {kMaxCluster, 8})
+    if (g < ctx->coop_grid && std::find(cand, cand + nc, g) == cand + nc) cand[nc++] = g;
+  for (int ci = 0; ci < nc && rs == RAPID_OK; ci++) {
+    const int g = cand[ci];
     for (int s = 0; s < RAPID_MAX_STAGES; s++) ctx->stage_grid[s] = g;
     rs = time_stages(ctx, ms);
     for (int s = 0; s < ctx->nstages && rs == RAPID_OK; s++)

@@ -344,7 +344,23 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
 // acquire-release add whose last arriver opens a separate flag.)  Every wait is bounded by
 // ctl.spin_ns (and an iteration cap); on give-up the CTA records DERR_TIMEOUT and the whole
 // grid returns false, so no kernel can hang.
+//
+// A kernel launched as one thread-block cluster (kCluster: the single-image kernels built
+// for it) meets at the cluster's hardware
+// barrier instead: every thread arrives with release and waits with acquire semantics at
+// cluster scope, which orders the global-memory accesses of all the cluster's threads as
+// the counter does for a grid.  The wait cannot time out and every CTA passes the same
+// barriers (all control flow between barriers is uniform over the grid), so it returns true.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+template <bool kCluster = false>
 __device__ inline bool grid_sync(const DevCtl &c, unsigned &epoch) {
+  if constexpr (kCluster) {
+    cluster_barrier();
+    epoch++;
+    return true;
+  }
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -549,8 +565,17 @@ cudaError_t launch_adam(float *w, float *m, float *v, float *grad, float lr, flo
 
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_stage(const StageArgs &a, int grid, int block, cudaStream_t s, int shape);
+// Largest grid that runs as one thread-block cluster (the non-portable cluster size limit).
+constexpr int kMaxCluster = 16;
+// Whether stage kernel fn (block threads per CTA) can run as one cluster of `grid` CTAs on
+// the current device: decided once per kernel and device (cluster sizes 16 and 8 are
+// queried) and remembered; while the stream is being captured an unknown kernel counts as
+// not (a cooperative launch is always correct).
+bool cluster_launch_ok(const void *fn, int grid, int block, cudaStream_t s);
 int stage_block_threads(int shape);
 const void *stage_kernel_ptr(bool batch, bool frontier, int shape);
+// the single-image kernel of a shape built for a launch as one thread-block cluster
+const void *stage_cluster_kernel_ptr(bool frontier, int shape);
 
 // Carve the per-label arrays of M labels from `base` (256-byte aligned pieces); returns the
 // bytes used, or 0 when they do not fit in `cap` bytes.  label_arrays_bytes(M) is the size.

@@ -539,7 +539,7 @@ struct Timer {
 // one image, whose descriptor the kernel reads from its parameters.  kSched: the sweep
 // schedule alone, the queue schedule alone (such a kernel carries only the code of its
 // schedule), or either by a.frontier (used for batches under the sweep schedule).
-template <bool kBatch, int kSched>
+template <bool kBatch, int kSched, bool kCluster = false>
 __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
   constexpr int kImgs = kBatch ? kMaxBatch : 1;
   __shared__ WarpTile wts[kThreads / 32];
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
     for (long long i = gtid; i < nrec * kQueueWords; i += gstride) a.qbits[i] = ~0u;
     if (gtid < 9) a.wl_count[gtid] = 0;  // blocks queued from the start are not listed
   }
-  if (!grid_sync(a.ctl, epoch)) return;
+  if (!grid_sync<kCluster>(a.ctl, epoch)) return;
   Timer tm(a.ctl.prof);
   int g = 0;
   for (int sweep = 0; sweep < a.max_sweeps; sweep++) {
@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
       }
 
       tm.lap(PROF_EVAL);
-      if (!grid_sync(a.ctl, epoch)) return;
+      if (!grid_sync<kCluster>(a.ctl, epoch)) return;
       tm.lap(PROF_SYNC1);
       const int gp = g & 1;
       if (blockIdx.x == 0 && threadIdx.x == 0) {  // slots of the next phase; last read a phase ago
@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
       const int rq = ld_volatile_i32(a.mg.req_count + gp);
       if (rq > 0) merge_targets<kBatch>(a, s_img, s_label0, rq, g);
       tm.lap(PROF_COMMIT);
-      if (!grid_sync(a.ctl, epoch)) return;
+      if (!grid_sync<kCluster>(a.ctl, epoch)) return;
       tm.lap(PROF_SYNC2);
       if (rq > 0) {
         const int nf = ld_volatile_i32(a.mg.found_count + gp);
@@ -633,10 +633,10 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
             merge_apply<kBatch, kSched>(a, s_img, s_label0, s_acc, nacc, g, slot);
           } else {
             if (blockIdx.x == 0) merge_walk_big(a, nf);
-            if (!grid_sync(a.ctl, epoch)) return;
+            if (!grid_sync<kCluster>(a.ctl, epoch)) return;
             merge_apply<kBatch, kSched>(a, s_img, s_label0, a.mg.acc, ld_volatile_i32(a.mg.acc_count), g, slot);
           }
-          if (!grid_sync(a.ctl, epoch)) return;
+          if (!grid_sync<kCluster>(a.ctl, epoch)) return;
         }
         tm.lap(PROF_MERGE);
       }
@@ -667,19 +667,43 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(StageArgs a) {
 
 }  // namespace RAPID_SHAPE_NS
 
-const void *RAPID_CAT(stage_kernel_ptr_, RAPID_SHAPE_NS)(bool batch, bool frontier) {
+const void *RAPID_CAT(stage_kernel_ptr_, RAPID_SHAPE_NS)(bool batch, bool frontier, bool cluster) {
   using namespace RAPID_SHAPE_NS;
+  if (cluster) return frontier ? (const void *)stage_kernel<false, kSchedQueue, true>
+                               : (const void *)stage_kernel<false, kSchedSweeps, true>;
   // (a batch under the sweep schedule runs the kernel that reads the schedule at run time:
   // measured 5% faster there than the sweeps-only build, 1042 against 1102 ms on 64 tiles)
   if (batch) return frontier ? (const void *)stage_kernel<true, kSchedQueue> : (const void *)stage_kernel<true, kSchedRuntime>;
   return frontier ? (const void *)stage_kernel<false, kSchedQueue> : (const void *)stage_kernel<false, kSchedSweeps>;
 }
 
+// A single image's stage of at most kMaxCluster CTAs runs as one thread-block cluster (the
+// kernel built with the cluster's hardware barrier) when the device can co-schedule such a
+// cluster; otherwise, for larger grids and for batches, as a cooperative launch (barriers
+// through a counter in global memory).
 cudaError_t RAPID_CAT(launch_stage_, RAPID_SHAPE_NS)(const StageArgs &a, int grid, int block, cudaStream_t s) {
   StageArgs copy = a;
   void *args[] = {&copy};
-  return cudaLaunchCooperativeKernel(RAPID_CAT(stage_kernel_ptr_, RAPID_SHAPE_NS)(a.nimg > 1, a.frontier != 0),
-                                     dim3(grid), dim3(block), args, 0, s);
+  if (a.nimg == 1 && grid >= 2 && grid <= kMaxCluster) {
+    const void *fc = RAPID_CAT(stage_kernel_ptr_, RAPID_SHAPE_NS)(false, a.frontier != 0, true);
+    if (cluster_launch_ok(fc, grid, block, s)) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(grid);
+      cfg.blockDim = dim3(block);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = grid;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelExC(&cfg, fc, args);
+    }
+  }
+  const void *fn = RAPID_CAT(stage_kernel_ptr_, RAPID_SHAPE_NS)(a.nimg > 1, a.frontier != 0, false);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, s);
 }
 
 }  // namespace rapid

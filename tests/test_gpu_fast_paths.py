@@ -127,3 +127,42 @@ def test_autotune_picks_valid_grids_and_keeps_results():
     np.testing.assert_array_equal(lab, ref[0])
     np.testing.assert_array_equal(st, ref[1])
     np.testing.assert_array_equal(cnt, ref[2])
+
+
+@pytest.mark.parametrize("schedule", [0, 1], ids=["sweeps", "queue"])
+def test_cluster_launches_change_nothing(schedule):
+    """A single image's grids of 2 to 16 CTAs run as one thread-block cluster (hardware
+    cluster barriers in place of the grid barrier): every stage at cluster sizes 16, 12, 8
+    and 2 with every tile shape equals the full-grid run and the oracle; a batch at the same
+    small grids (cooperative launches) through a captured graph and its replay equals its
+    full-grid run."""
+    import torch
+
+    import paper_1704_02083_gb300 as pkg
+
+    for name, rgb, params in CASES[:3]:
+        p = dict(params, schedule=schedule)
+        ref = _run_with_grids(rgb, None, **p)
+        for grids in ([16] * 8, [12, 16, 8, 16, 12, 8, 16, 2], [2] * 8):
+            got = _run_with_grids(rgb, grids, **p)
+            for x, y in zip(got[:3], ref[:3]):
+                np.testing.assert_array_equal(x, y, err_msg=f"{name} grids={grids}")
+        np.testing.assert_array_equal(ref[0], oracle_run(rgb, **p)[0])
+    imgs = [CASES[0][1], CASES[2][1], synth.he_image(70, 90, 4, 15).rgb]
+    params = dict(num_levels=2, ratio_C=4, init_block=16, size_mode=2, predict=1, schedule=schedule)
+    K = [200, 40, 20]
+    out = []
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for grids in (None, [16, 8, 16, 12, 16, 16, 16, 16]):
+            with pkg.Context(stream=stream, **params) as ctx:
+                ctx.set_graph(True)
+                ctx.set_images([torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in imgs], K)
+                if grids is not None:
+                    ctx.set_stage_grids(grids)
+                for rep in range(2):  # capture, then replay
+                    ctx.run()
+                    out.append([ctx.image_labels(i) for i in range(len(imgs))])
+    for run in out[1:]:
+        for a, b in zip(run, out[0]):
+            np.testing.assert_array_equal(a, b)
