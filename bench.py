@@ -636,6 +636,7 @@ def measure(args, rank, world, local, dist, workload, prune, use_classifier, geo
                          "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
                          "traffic": traffic, "alg_bytes_per_launch": launch_bytes, "launch_ms": launch_ms,
+                         "kernel_source_sha256": kernel_source_sha256()[:16],
                          "share_of_step": launch_ms / (total_ms / args.steps),
                          "all_stage_launches": {"launches_per_step": nst,
                                                 "ms_per_step": all_ms / args.steps,

@@ -156,7 +156,7 @@ __device__ __forceinline__ void conv_layer_tc(const __nv_bfloat16 *in, int gin, 
 // Scores of one kOut x kOut tile of image im's blocks: features (with a 3-block halo) in
 // shared memory, two tensor-core layers, the last layer per thread.  Writes the sigmoid
 // score (if score != null) and the pruning mask (score >= threshold).
-__global__ void __launch_bounds__(kScoreThreads) score_kernel(StageArgs a, ImageDesc im, int L, ScorerDev W,
+__global__ void __launch_bounds__(kScoreThreads, 4) score_kernel(StageArgs a, ImageDesc im, int L, ScorerDev W,
                                                               float threshold, float *score, unsigned char *mask) {
   __shared__ __align__(16) __nv_bfloat16 s_f[kG0 * kG0 * kCh];
   __shared__ __align__(16) __nv_bfloat16 s_h1[kG1 * kG1 * kHid];
